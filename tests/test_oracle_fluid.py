@@ -1,0 +1,349 @@
+"""Pins of the oracle's explicit finite-volume compressible Navier-Stokes step
+(the equations of Sec. 2.1) against exact invariances, a manufactured smooth
+solution differentiated by sympy, the exact Riemann solution of Sod's problem
+and the linear decay rates of a shear wave and of an isobaric temperature
+wave."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2301_09349_gb300 import cases as C
+
+PER = (C.BC_PERIODIC,) * 6
+
+
+def _uniform(g, rho=1.0, u=(1.0, 0.0, 0.0), T=1.0):
+    R = 1.0 / (g.gamma * g.Mach ** 2)
+    U = np.zeros((g.ncomp, g.ncells))
+    U[0] = rho
+    for d in range(g.dim):
+        U[1 + d] = rho * u[d]
+    U[-1] = rho * R * T / (g.gamma - 1) + 0.5 * rho * sum(u[d] ** 2 for d in range(g.dim))
+    return U
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("mach", [0.3, 2.0])
+def test_freestream_is_steady_under_all_bcs(oracle, dim, mach):
+    n = (12, 10, 8)[:dim]
+    g = C.small_grid(dim, n, h=0.2, Mach=mach)
+    U = _uniform(g)
+    L = oracle.rhs(g, U)
+    assert np.abs(L).max() == 0.0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_uniform_state_steady_periodic(oracle, dim):
+    g = C.small_grid(dim, (8, 7, 6)[:dim], h=0.3, bc=PER)
+    U = _uniform(g, rho=1.7, u=(0.3, -0.4, 0.2), T=1.3)
+    assert np.abs(oracle.rhs(g, U)).max() == 0.0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_periodic_conservation(oracle, dim):
+    g = C.small_grid(dim, (12, 10, 8)[:dim], h=0.2, bc=PER, Re=50.0)
+    U = C.random_state(g, seed=31, amp=0.05).reshape(g.ncomp, -1)
+    L = oracle.rhs(g, U)
+    scale = np.abs(L).sum(1)
+    assert np.all(np.abs(L.sum(1)) <= 1e-12 * scale)
+    # and over a full SSP-RK2 step
+    dt, Us = oracle.predictor(g, U)
+    np.testing.assert_allclose(Us.sum(1), U.sum(1), rtol=1e-13)
+
+
+def _perm_state(g, U, axes):
+    """transpose grid axes (a permutation of 0..dim-1 in x,y,z order) and the
+    momentum components with them"""
+    dim = g.dim
+    Ug = U.reshape((g.ncomp,) + tuple(reversed(g.n[:dim])))
+    # storage axes are (comp, z, y, x): axis for coordinate d is 1 + dim-1-d
+    new_axes = [0] + [1 + dim - 1 - axes[dim - 1 - a] for a in range(dim)]
+    V = np.transpose(Ug, new_axes).copy()
+    M = V[1:1 + dim].copy()
+    for d in range(dim):
+        V[1 + d] = M[axes[d]]
+    return V
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_rotation_and_mirror_symmetry(oracle, dim):
+    n = (10, 10, 10)[:dim]
+    g = C.small_grid(dim, n, h=0.25, bc=PER, Re=40.0)
+    U = C.random_state(g, seed=32, amp=0.05).reshape(g.ncomp, -1)
+    L = oracle.rhs(g, U)
+    perms = [(1, 0)] if dim == 2 else [(1, 2, 0), (2, 0, 1), (1, 0, 2)]
+    for axes in perms:
+        Up = _perm_state(g, U, axes)
+        Lp = oracle.rhs(g, Up)
+        np.testing.assert_allclose(Lp.reshape(Up.shape), _perm_state(g, L, axes), rtol=0,
+                                   atol=1e-12 * np.abs(L).max())
+    # mirror y -> -y with v negated
+    Ug = U.reshape((g.ncomp,) + tuple(reversed(n)))
+    ax_y = 1 + dim - 2
+    Um = np.flip(Ug, axis=ax_y).copy()
+    Um[2] *= -1
+    Lm = oracle.rhs(g, Um).reshape(Um.shape)
+    Lg = np.flip(L.reshape(Ug.shape), axis=ax_y).copy()
+    Lg[2] *= -1
+    np.testing.assert_allclose(Lm, Lg, rtol=0, atol=1e-12 * np.abs(L).max())
+
+
+def test_3d_uniform_in_z_reduces_to_2d(oracle):
+    g2 = C.small_grid(2, (12, 10), h=0.2, bc=PER, Re=60.0)
+    g3 = C.small_grid(3, (12, 10, 5), h=0.2, bc=PER, Re=60.0)
+    U2 = C.random_state(g2, seed=33, amp=0.05).reshape(4, 10, 12)
+    U3 = np.zeros((5, 5, 10, 12))
+    U3[0:3] = U2[0:3][:, None]
+    U3[4] = U2[3][None]
+    L2 = oracle.rhs(g2, U2).reshape(4, 10, 12)
+    L3 = oracle.rhs(g3, U3).reshape(5, 5, 10, 12)
+    for k in range(5):
+        np.testing.assert_allclose(L3[[0, 1, 2, 4], k], L2, rtol=0, atol=1e-13 * np.abs(L2).max())
+    assert np.abs(L3[3]).max() == 0.0
+
+
+def test_dt_closed_form_free_stream(oracle):
+    for dim in (2, 3):
+        g = C.small_grid(dim, (8, 8, 8)[:dim], h=0.1, Re=200.0, Mach=0.5)
+        U = _uniform(g)
+        c = 1.0 / g.Mach
+        nu = max(4.0 / 3.0, g.gamma / g.Pr) * (1.0 / g.Re)
+        s = (1.0 + dim * c) / g.h + dim * 2 * nu / g.h ** 2
+        assert oracle.dt(g, U) == pytest.approx(g.cfl / s, rel=1e-14)
+
+
+def test_ghost_cells(oracle):
+    g = C.small_grid(2, (6, 5), h=0.5, Mach=0.5,
+                     bc=(C.BC_FREESTREAM, C.BC_ZEROGRAD, C.BC_SLIP, C.BC_PERIODIC, 0, 0))
+    U = C.random_state(g, seed=34).reshape(4, 5, 6)
+    P = oracle.fill_ghosts(g, U)
+    assert P.shape == (4, 9, 10)
+    inner = P[:, 2:7, 2:8]
+    np.testing.assert_array_equal(inner, U)
+    p_inf = 1 / (g.gamma * g.Mach ** 2)
+    Uinf = np.array([1.0, 1.0, 0.0, p_inf / (g.gamma - 1) + 0.5])
+    np.testing.assert_array_equal(P[:, :, 0:2], np.broadcast_to(Uinf[:, None, None], (4, 9, 2)))
+    # zero gradient at x+ (rows inside in y)
+    for q in (8, 9):
+        np.testing.assert_array_equal(P[:, 2:7, q], U[:, :, 5])
+    # slip at y-: mirrored rows with v negated
+    for q, src in ((1, 0), (0, 1)):
+        np.testing.assert_array_equal(P[[0, 1, 3], q, 2:8], U[[0, 1, 3], src, :])
+        np.testing.assert_array_equal(P[2, q, 2:8], -U[2, src, :])
+    # periodic at y+
+    np.testing.assert_array_equal(P[:, 7, 2:8], U[:, 0, :])
+    np.testing.assert_array_equal(P[:, 8, 2:8], U[:, 1, :])
+    # corner: zero-gradient in x composed with slip in y
+    np.testing.assert_array_equal(P[2, 1, 9], -U[2, 0, 5])
+
+
+# ---------------------------------------------------------------------------
+# manufactured smooth solution: FV operator vs the exact flux divergence
+# ---------------------------------------------------------------------------
+
+def _mms_exact(dim, g):
+    sp = pytest.importorskip("sympy")
+    x, y, z = sp.symbols("x y z", real=True)
+    X = [x, y, z][:dim]
+    k = 2 * sp.pi
+    if dim == 2:
+        rho = 1 + sp.Rational(1, 5) * sp.sin(k * x) * sp.cos(k * y)
+        vel = [sp.Rational(1, 2) + sp.Rational(1, 5) * sp.cos(k * x + k * y),
+               sp.Rational(1, 5) * sp.sin(k * x) * sp.sin(k * y) - sp.Rational(1, 10)]
+        p0 = 1 / (g.gamma * g.Mach ** 2)
+        p = p0 * (1 + sp.Rational(1, 10) * sp.cos(k * x) * sp.sin(k * y))
+    else:
+        rho = 1 + sp.Rational(1, 5) * sp.sin(k * x) * sp.cos(k * y) * sp.cos(k * z)
+        vel = [sp.Rational(1, 2) + sp.Rational(1, 5) * sp.cos(k * x + k * z),
+               sp.Rational(1, 5) * sp.sin(k * y) * sp.sin(k * x) - sp.Rational(1, 10),
+               sp.Rational(1, 5) * sp.cos(k * z + k * y)]
+        p0 = 1 / (g.gamma * g.Mach ** 2)
+        p = p0 * (1 + sp.Rational(1, 10) * sp.cos(k * x) * sp.sin(k * y) * sp.cos(k * z))
+    gam = sp.nsimplify(g.gamma)
+    R = 1 / (gam * sp.nsimplify(g.Mach) ** 2)
+    T = p / (rho * R)
+    S = sp.nsimplify(g.sutherland_S)
+    mu = (1 / sp.nsimplify(g.Re)) * T ** sp.Rational(3, 2) * (1 + S) / (T + S)
+    cp = gam * R / (gam - 1)
+    lam = mu * cp / sp.nsimplify(g.Pr)
+    E = p / (gam - 1) + rho * sum(v ** 2 for v in vel) / 2
+    div = sum(sp.diff(vel[m], X[m]) for m in range(dim))
+    cons = [rho] + [rho * v for v in vel] + [E]
+    Lexpr = [0] * (dim + 2)
+    for d in range(dim):
+        tau = [mu * (sp.diff(vel[d], X[m]) + sp.diff(vel[m], X[d])) - (sp.Rational(2, 3) * mu * div if m == d else 0)
+               for m in range(dim)]
+        flux = [rho * vel[d]] + [rho * vel[m] * vel[d] + (p if m == d else 0) - tau[m] for m in range(dim)]
+        flux += [(E + p) * vel[d] - sum(vel[m] * tau[m] for m in range(dim)) - lam * sp.diff(T, X[d])]
+        for c in range(dim + 2):
+            Lexpr[c] = Lexpr[c] - sp.diff(flux[c], X[d])
+    fU = sp.lambdify(X, cons, "numpy")
+    fL = sp.lambdify(X, Lexpr, "numpy")
+    return fU, fL
+
+
+@pytest.mark.parametrize("dim,ns,emax,rmin", [(2, (16, 32, 64), 2e-2, 1.7),
+                                               (3, (8, 16, 32), 6e-2, 1.55)])
+def test_manufactured_solution_second_order(oracle, dim, ns, emax, rmin):
+    # the limiter clips at smooth extrema, so the observed order approaches 2
+    # from below (3D at 64^3 measures 1.68-1.83 per component)
+    errs = []
+    fU = fL = None
+    for n in ns:
+        g = C.small_grid(dim, (n,) * dim, h=1.0 / n, lo=(0.0,) * dim, bc=PER, Re=50.0, Mach=0.5)
+        if fU is None:
+            fU, fL = _mms_exact(dim, g)
+        ax = [(np.arange(n) + 0.5) / n for _ in range(dim)]
+        mesh = np.meshgrid(*ax, indexing="ij")
+        pts = [m.transpose(tuple(reversed(range(dim)))).ravel() for m in mesh]
+        U = np.stack([np.broadcast_to(np.asarray(v, dtype=float), pts[0].shape) for v in fU(*pts)])
+        Lx = np.stack([np.broadcast_to(np.asarray(v, dtype=float), pts[0].shape) for v in fL(*pts)])
+        L = oracle.rhs(g, U)
+        errs.append(np.abs(L - Lx).mean(1) / np.abs(Lx).mean(1))
+    errs = np.array(errs)
+    rates = np.log2(errs[:-1] / errs[1:])
+    assert np.all(errs[-1] < emax), errs
+    assert np.all(rates[-1] > rmin), rates
+    assert np.all(rates > 1.0), rates
+
+
+# ---------------------------------------------------------------------------
+# Sod's shock tube: exact Riemann solution (textbook construction)
+# ---------------------------------------------------------------------------
+
+def _exact_riemann(rl, ul, pl, rr, ur, pr, gam, xi):
+    cl, cr = math.sqrt(gam * pl / rl), math.sqrt(gam * pr / rr)
+
+    def f(p, rk, pk, ck):
+        if p > pk:
+            A, B = 2 / ((gam + 1) * rk), (gam - 1) / (gam + 1) * pk
+            return (p - pk) * math.sqrt(A / (p + B))
+        return 2 * ck / (gam - 1) * ((p / pk) ** ((gam - 1) / (2 * gam)) - 1)
+
+    lo_, hi_ = 1e-8, 10 * max(pl, pr)
+    for _ in range(200):
+        pm = 0.5 * (lo_ + hi_)
+        if f(pm, rl, pl, cl) + f(pm, rr, pr, cr) + (ur - ul) > 0:
+            hi_ = pm
+        else:
+            lo_ = pm
+    ps = 0.5 * (lo_ + hi_)
+    us = 0.5 * (ul + ur) + 0.5 * (f(ps, rr, pr, cr) - f(ps, rl, pl, cl))
+    out = np.zeros((3, len(xi)))
+    for i, s in enumerate(xi):
+        if s <= us:  # left of contact
+            if ps > pl:
+                rs = rl * (ps / pl + (gam - 1) / (gam + 1)) / ((gam - 1) / (gam + 1) * ps / pl + 1)
+                sl = ul - cl * math.sqrt((gam + 1) / (2 * gam) * ps / pl + (gam - 1) / (2 * gam))
+                out[:, i] = (rl, ul, pl) if s < sl else (rs, us, ps)
+            else:
+                rs = rl * (ps / pl) ** (1 / gam)
+                cs = cl * (ps / pl) ** ((gam - 1) / (2 * gam))
+                if s < ul - cl:
+                    out[:, i] = (rl, ul, pl)
+                elif s > us - cs:
+                    out[:, i] = (rs, us, ps)
+                else:
+                    u = 2 / (gam + 1) * (cl + (gam - 1) / 2 * ul + s)
+                    c = 2 / (gam + 1) * (cl + (gam - 1) / 2 * (ul - s))
+                    r = rl * (c / cl) ** (2 / (gam - 1))
+                    out[:, i] = (r, u, pl * (c / cl) ** (2 * gam / (gam - 1)))
+        else:
+            if ps > pr:
+                rs = rr * (ps / pr + (gam - 1) / (gam + 1)) / ((gam - 1) / (gam + 1) * ps / pr + 1)
+                sr = ur + cr * math.sqrt((gam + 1) / (2 * gam) * ps / pr + (gam - 1) / (2 * gam))
+                out[:, i] = (rr, ur, pr) if s > sr else (rs, us, ps)
+            else:
+                rs = rr * (ps / pr) ** (1 / gam)
+                cs = cr * (ps / pr) ** ((gam - 1) / (2 * gam))
+                if s > ur + cr:
+                    out[:, i] = (rr, ur, pr)
+                elif s < us + cs:
+                    out[:, i] = (rs, us, ps)
+                else:
+                    u = 2 / (gam + 1) * (-cr + (gam - 1) / 2 * ur + s)
+                    c = 2 / (gam + 1) * (cr - (gam - 1) / 2 * (ur - s))
+                    r = rr * (c / cr) ** (2 / (gam - 1))
+                    out[:, i] = (r, u, pr * (c / cr) ** (2 * gam / (gam - 1)))
+    return out
+
+
+def _sod_run(oracle, n, tend=0.2):
+    bc = (C.BC_ZEROGRAD, C.BC_ZEROGRAD, C.BC_PERIODIC, C.BC_PERIODIC, 0, 0)
+    g = C.small_grid(2, (n, 2), h=1.0 / n, lo=(0.0, 0.0), bc=bc, Re=0.0, Mach=1.0)
+    x = (np.arange(n) + 0.5) / n
+    left = x < 0.5
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    U = np.zeros((4, 2, n))
+    U[0] = rho
+    U[3] = p / (g.gamma - 1)
+    U = U.reshape(4, -1)
+    t = 0.0
+    while t < tend - 1e-14:
+        dt = min(oracle.dt(g, U), tend - t)
+        _, U = oracle.predictor(g, U, dt_fixed=dt)
+        t += dt
+    ex = _exact_riemann(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, g.gamma, (x - 0.5) / tend)
+    return np.abs(U.reshape(4, 2, n)[0, 0] - ex[0]).mean()
+
+
+def test_sod_converges_to_exact_riemann_solution(oracle):
+    e = [_sod_run(oracle, n) for n in (100, 200, 400)]
+    assert e[0] > e[1] > e[2], e
+    assert e[2] < 6e-3, e
+    assert e[0] / e[2] > 2.0, e
+
+
+# ---------------------------------------------------------------------------
+# linear viscous and conductive decay rates (low Mach)
+# ---------------------------------------------------------------------------
+
+def _mode_amplitude(f, n):
+    x = (np.arange(n) + 0.5) / n
+    return 2 * np.mean(f * np.sin(2 * np.pi * x))
+
+
+def test_shear_wave_decay_rate(oracle):
+    n, Re, A = 128, 20.0, 1e-3
+    g = C.small_grid(2, (n, 2), h=1.0 / n, lo=(0.0, 0.0), bc=PER, Re=Re, Mach=0.1)
+    x = (np.arange(n) + 0.5) / n
+    U = _uniform(g, u=(0.0, 0.0, 0.0)).reshape(4, 2, n)
+    U[2] = A * np.sin(2 * np.pi * x)[None, :]
+    U = U.reshape(4, -1)
+    U[3] += 0.5 * U[2] ** 2
+    t, tend = 0.0, 0.2
+    while t < tend - 1e-14:
+        dt = min(oracle.dt(g, U), tend - t)
+        _, U = oracle.predictor(g, U, dt_fixed=dt)
+        t += dt
+    a = _mode_amplitude(U.reshape(4, 2, n)[2, 0], n)
+    rate = -math.log(a / A) / tend
+    nu = 1.0 / Re
+    assert rate == pytest.approx(nu * (2 * np.pi) ** 2, rel=0.02)
+
+
+def test_isobaric_temperature_wave_decay_rate(oracle):
+    n, Re, a0 = 128, 20.0, 1e-3
+    g = C.small_grid(2, (n, 2), h=1.0 / n, lo=(0.0, 0.0), bc=PER, Re=Re, Mach=0.05)
+    x = (np.arange(n) + 0.5) / n
+    T = 1.0 + a0 * np.sin(2 * np.pi * x)
+    R = 1.0 / (g.gamma * g.Mach ** 2)
+    rho = 1.0 / T                    # p = rho R T uniform
+    U = np.zeros((4, 2, n))
+    U[0] = rho[None]
+    U[3] = R / (g.gamma - 1)
+    U = U.reshape(4, -1)
+    t, tend = 0.0, 0.2
+    while t < tend - 1e-14:
+        dt = min(oracle.dt(g, U), tend - t)
+        _, U = oracle.predictor(g, U, dt_fixed=dt)
+        t += dt
+    V = U.reshape(4, 2, n)[:, 0]
+    p = (g.gamma - 1) * (V[3] - 0.5 * (V[1] ** 2 + V[2] ** 2) / V[0])
+    Tn = p / (V[0] * R)
+    a = _mode_amplitude(Tn - Tn.mean(), n)
+    rate = -math.log(a / a0) / tend
+    alpha = (1.0 / Re) / g.Pr        # lambda / (rho c_p) at T = 1, rho = 1
+    assert rate == pytest.approx(alpha * (2 * np.pi) ** 2, rel=0.03)
