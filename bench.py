@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Benchmark of the IBM step (3D heated sphere, 256^3 FP32).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = the whole hot path: fluid stage 1 (L(U^n), dt), fluid stage 2
+(SSP-RK2 predictor), interpolation + direct forcing at the markers,
+spreading + forced update, force/heat sums.  The markers are at rest, so the
+bins and the quadrature weights are built once at set-up.
+
+With N > 1 (torchrun, one process per GPU) every rank runs its own
+independent sphere case (Mach x wall-temperature variants): weak scaling,
+no collective on the data path.  Rank 0 prints one JSON line.
+
+--impl reference times the FP64 CPU oracle on this host's cores on a slab
+sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2301_09349_gb300 import cases as C  # noqa: E402
+
+METRIC = "cell-updates/s + marker-updates/s per IBM step at 1 GB300; % HBM roofline"
+UNIT = "cell-updates/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=10)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=256, help="grid cells per axis")
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="target seconds of oracle work for the cpu_baseline")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def case_for(rank: int, world: int, n: int) -> C.Case:
+    variants = C.sphere_variants(n)
+    return variants[0] if world == 1 else variants[rank % len(variants)]
+
+
+def workload_name(c: C.Case, n_kept: int) -> str:
+    return ("3D heated sphere %d^3 FP32, Ma %.1f, T_w %.1f, Re 300, %d Fibonacci markers "
+            "(%d after one-per-cell dedup)" % (c.grid.n[0], c.grid.Mach, c.Tw[0], len(c.X), n_kept))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def source_hash(path: str) -> str:
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; otherwise None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            t = json.load(f)
+        ent = t[kernel]
+        src = os.path.join(ROOT, ent["source"])
+        if source_hash(src) != ent["source_sha256_16"]:
+            return None
+        return float(ent["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % os.getpid())
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--id=" + gpu_id, "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on host cores (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_slab(c: C.Case, nz: int):
+    """A z-slab of the workload: same spacing, x-y extent, BCs and physics;
+    nz planes centred on the body; markers kept where their support fits."""
+    import dataclasses
+    g = c.grid
+    nz = max(8, min(nz, g.n[2]))
+    z0 = -0.5 * nz * g.h
+    gs = dataclasses.replace(g, n=(g.n[0], g.n[1], nz), lo=(g.lo[0], g.lo[1], z0))
+    cz = np.floor((c.X[:, 2] - z0) / g.h)
+    sel = (cz >= 2) & (cz <= nz - 3)
+    return gs, c.X[sel], c.Tw[sel]
+
+
+def oracle_rate(c: C.Case, target_s: float, steps: int, warmup: int, threads: int):
+    """Time `steps` oracle steps (after `warmup`) on a slab sized so that the
+    whole run takes about target_s seconds.  Returns (cells/s, details)."""
+    from oracle import oracle as O
+    O.build()
+    O.set_threads(threads)
+    g = c.grid
+    # calibrate the per-cell cost on a 16-plane slab
+    gs, X, Tw = oracle_slab(c, 16)
+    U = C.initial_state(gs, c.seed).astype(np.float32).astype(np.float64)
+    run = O.Run(gs, X, Tw)
+    t = time.perf_counter()
+    run.step(U)
+    per_cell = (time.perf_counter() - t) / gs.ncells
+    nz = int(target_s / max(steps + warmup, 1) / (per_cell * g.n[0] * g.n[1]))
+    gs, X, Tw = oracle_slab(c, nz)
+    U = C.initial_state(gs, c.seed).astype(np.float32).astype(np.float64)
+    run = O.Run(gs, X, Tw)
+    for _ in range(warmup):
+        U = run.step(U)
+    t = time.perf_counter()
+    for _ in range(steps):
+        U = run.step(U)
+    el = time.perf_counter() - t
+    rate = gs.ncells * steps / el
+    sample = ("z-slab %dx%dx%d of the %s case (%d markers), %d timed step(s)"
+              % (gs.n[0], gs.n[1], gs.n[2], "x".join(map(str, g.n[: g.dim])), len(run.X), steps))
+    return rate, {"seconds": el, "sample": sample, "cells": gs.ncells,
+                  "markers": len(run.X), "ms_per_step": 1e3 * el / steps}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    c = case_for(0, 1, args.n)
+    threads = os.cpu_count() or 1
+    target = max(60.0, min(150.0, 1.2 * (args.steps + args.warmup)))
+    rate, det = oracle_rate(c, target, args.steps, args.warmup, threads)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": det["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(c, det["markers"]) + "; " + det["sample"]},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": det["sample"]},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the CUDA path
+# ---------------------------------------------------------------------------
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2301_09349_gb300 import build, ibm
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    c = case_for(rank, world, args.n)
+    g = c.grid
+    stream = torch.cuda.Stream()
+    grid = ibm.Grid(g, max_markers=len(c.X), stream=stream)
+    n_kept = grid.set_markers(c.X, c.Tw)
+    grid.set_state(C.initial_state(g, c.seed).astype(np.float32))
+    N = g.ncells
+
+    grid.step(args.warmup)
+    grid.sync()
+
+    uuid = str(torch.cuda.get_device_properties(local).uuid)
+    gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    clocks = ClockSampler(gpu_id)
+    time.sleep(0.3)
+    ibm.ibm_profile(grid.h, True)
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    grid.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    prof = ibm.ibm_profile_read(grid.h)
+    ibm.ibm_profile(grid.h, False)
+    clk = clocks.stop()
+    grid.sync()
+
+    # end to end through the C ABI with host buffers: per step the wall
+    # temperatures go up from page-locked memory, the step runs, and the
+    # force/heat result comes back (a synchronizing read)
+    Tw_pin = torch.empty(n_kept, dtype=torch.float64, pin_memory=True).numpy()
+    _, _, idx = grid.markers()
+    Tw_pin[:] = c.Tw[idx]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ibm.ibm_set_wall_temperature(grid.h, Tw_pin)
+        ibm.ibm_step(grid.h, 1)
+        res = ibm.ibm_forces_and_nusselt(grid.h)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+
+    times = torch.tensor([ms, e2e_s * 1e3, float(N), float(n_kept)], dtype=torch.float64,
+                         device="cuda")
+    if dist is not None:
+        mx = times.clone()
+        dist.all_reduce(mx[:2], op=dist.ReduceOp.MAX)
+        sm = times.clone()
+        dist.all_reduce(sm[2:], op=dist.ReduceOp.SUM)
+        times = torch.cat([mx[:2], sm[2:]])
+    ms_max, e2e_ms_max, cells_all, markers_all = [float(x) for x in times.cpu()]
+
+    if rank == 0:
+        steps = args.steps
+        value = cells_all * steps / (ms_max * 1e-3)
+        marker_rate = markers_all * steps / (ms_max * 1e-3)
+        nc = g.ncomp
+        bpe = g.fp_bytes
+        alg = {"stage1": 2 * nc * bpe * N, "stage2": 3 * nc * bpe * N}
+        peak, peak_kind = measured_peaks()
+        kernels = {}
+        total_ms = sum(v[0] for v in prof.values())
+        for name, (kms, nl) in prof.items():
+            if nl == 0:
+                continue
+            ent = {"launches": nl, "ms_per_launch": kms / nl, "share": kms / total_ms}
+            if name in alg:
+                ent["GB_per_s"] = alg[name] / (kms / nl * 1e-3) / 1e9
+            kernels[name] = ent
+        dom = max(("stage1", "stage2"), key=lambda k: prof[k][0])
+        dms = prof[dom][0] / prof[dom][1]
+        achieved = alg[dom] / (dms * 1e-3) / 1e9
+        traffic = traffic_for(dom)
+        # the whole step against the same roofline (100 B per cell-step)
+        step_bytes = (alg["stage1"] + alg["stage2"]) * steps
+        step_frac = step_bytes / (ms / 1e3 if world == 1 else ms_max / 1e3) / 1e9 / peak
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded free stream + 1e-3 density noise; Fibonacci markers)",
+            "config": {"workload": workload_name(c, n_kept),
+                       "grid": list(g.n), "markers_in": len(c.X), "markers_kept": n_kept,
+                       "cases_per_rank": "one independent sphere case per GPU",
+                       "l2": "inputs larger than L2 (each state array %.0f MB > 129 MB)"
+                             % (nc * bpe * N / 1e6)},
+            "marker_updates_per_s": marker_rate,
+            "hbm_roofline_frac_step": step_frac,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
+                                        if peak_kind == "measured" else "fallback 6.8 TB/s",
+                         "algorithmic_bytes_per_launch": alg[dom]},
+            "kernels": kernels,
+            "gpu_launches": int(sum(v[1] for v in prof.values())) * world,
+            "e2e": {"value": cells_all * steps / (e2e_ms_max * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * n_kept, "d2h_bytes_per_step": 64,
+                    "path": "ibm_set_wall_temperature(pinned host) + ibm_step + "
+                            "ibm_forces_and_nusselt per step"},
+            "clocks": clk,
+            "result": {"Cd": res["Cd"], "Cl": res["Cl"], "Nu": res["Nu"]},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            threads = os.cpu_count() or 1
+            rate, det = oracle_rate(c, args.cpu_seconds, 1, 0, threads)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads,
+                                    "kind": "oracle", "sample": det["sample"]}
+        print(json.dumps(line), flush=True)
+    grid.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,94 @@
+// Device-side definitions shared by the library's kernels (internal header).
+//
+// Grid parameters are passed to every kernel by value in one POD struct; the
+// physics follows Sec. 2.1 of the paper (perfect gas, Sutherland viscosity,
+// Newtonian stress, Fourier heat flux) in units rho_inf = U_inf = T_inf = 1.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ibmk {
+
+// error bits recorded on the device, decoded by the host at sync points
+enum : int {
+    ERR_NONFINITE = 1,      // non-finite or non-positive density/pressure
+    ERR_NOCONV = 2,         // quadrature CG did not converge
+    ERR_MARKER_RANGE = 4,   // a (moving) marker left the admissible region
+    ERR_CAPACITY = 8,       // a quadrature row exceeded its storage
+    ERR_TIMEOUT = 16,       // a bounded wait gave up
+};
+
+enum : int { BC_FREESTREAM = 0, BC_ZEROGRAD = 1, BC_SLIP = 2, BC_PERIODIC = 3 };
+
+struct GridParams {
+    int dim;
+    int n[3];
+    long long N;          // cells
+    double lo[3];
+    double h, inv_h;
+    double gamma, Pr, Re, Mach, S, cfl;
+    double R, cv, cp;     // gas constant r = 1/(gamma Ma^2), c_v, c_p
+    double mu_inf;        // 1/Re, or 0 when inviscid
+    double kvisc;         // max(4/3, gamma/Pr) for the viscous step limit
+    double p_inf;         // free-stream pressure
+    int bc[6];
+    int tile[3];
+    int ntile[3];
+    int n_tiles;
+    int cells_per_tile;
+    int energy_reading;
+};
+
+// The 1D regularised 3-point delta of Sec. 2.2 (Pinelli et al.); r in cells.
+__device__ __forceinline__ double phi_d(double r) {
+    double a = fabs(r);
+    if (a <= 0.5) return (1.0 + sqrt(1.0 - 3.0 * a * a)) * (1.0 / 3.0);
+    if (a <= 1.5) {
+        double b = 1.0 - a;
+        return (5.0 - 3.0 * a - sqrt(1.0 - 3.0 * b * b)) * (1.0 / 6.0);
+    }
+    return 0.0;
+}
+
+// Owner cell floor((X - lo)/h) per axis, rounded exactly as IEEE double
+// subtraction and division (no contraction), so every implementation that
+// evaluates the same two IEEE operations bins identically.
+__device__ __forceinline__ int owner_cell(double x, double lo, double h) {
+    return (int)floor(__ddiv_rn(__dsub_rn(x, lo), h));
+}
+
+__device__ __forceinline__ double cell_center(const GridParams &g, int d, int i) {
+    return g.lo[d] + (i + 0.5) * g.h;
+}
+
+// Interior source index of an index along one axis under that axis's face
+// boundary conditions.  Slip mirrors and toggles `flip` for the axis;
+// freestream sets `fs`.  Matches the boundary description of ibm.h.
+__device__ __forceinline__ int map_axis(int idx, int n, int bc_lo, int bc_hi, int axis, int &flip,
+                                        int &fs) {
+    if (idx >= 0 && idx < n) return idx;
+    int bc = idx < 0 ? bc_lo : bc_hi;
+    if (bc == BC_FREESTREAM) { fs = 1; return idx < 0 ? 0 : n - 1; }
+    if (bc == BC_ZEROGRAD) return idx < 0 ? 0 : n - 1;
+    if (bc == BC_SLIP) {
+        flip ^= (1 << axis);
+        int s = idx < 0 ? -1 - idx : 2 * n - 1 - idx;
+        return s < 0 ? 0 : (s >= n ? n - 1 : s);
+    }
+    int m = idx % n;
+    return m < 0 ? m + n : m;
+}
+
+// key of a cell for the marker bins: tile id * cells_per_tile + cell in tile
+__device__ __forceinline__ unsigned cell_key(const GridParams &g, int cx, int cy, int cz) {
+    int tx = cx / g.tile[0], ty = cy / g.tile[1], tz = cz / g.tile[2];
+    int lx = cx - tx * g.tile[0], ly = cy - ty * g.tile[1], lz = cz - tz * g.tile[2];
+    unsigned tid = (unsigned)(tx + g.ntile[0] * (ty + g.ntile[1] * tz));
+    unsigned cin = (unsigned)(lx + g.tile[0] * (ly + g.tile[1] * lz));
+    return tid * (unsigned)g.cells_per_tile + cin;
+}
+
+__device__ __forceinline__ void record_error(int *err, int bits) { atomicOr(err, bits); }
+
+}  // namespace ibmk

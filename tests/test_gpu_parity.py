@@ -1,0 +1,323 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances.  FP64 grids: the two sides evaluate the same formulas with
+different rounding order, so states agree to ~1e-13 relative (gate 1e-11).
+FP32 grids: the per-step gate is relative L2 <= 1e-5 per conserved component
+(FP32 rounding of the state, 6e-8, amplified by the flux cancellation of a
+nearly uniform stream); the long-run gate is 1e-3.  For the flux operator
+alone, the relative error of L is ~ eps_32 |F| / |dF| where dF is the flux
+difference across a cell; with 5 % perturbations that is <= 1e-4.
+Integer work (owner cells, bins) is compared bit for bit.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2301_09349_gb300 import cases as C
+from paper_2301_09349_gb300 import ibm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup(oracle):
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2301_09349_gb300 import build
+    build.build()
+    oracle.set_threads(os.cpu_count() or 1)
+
+
+def rel_l2(a, b):
+    """relative L2 error per conserved quantity: density, momentum (the whole
+    vector field, so a component that is nearly zero in the free stream is
+    measured against the momentum it belongs to) and total energy"""
+    a = np.asarray(a, dtype=np.float64).reshape(a.shape[0], -1)
+    b = np.asarray(b, dtype=np.float64).reshape(b.shape[0], -1)
+    nc = a.shape[0]
+    groups = [[0], list(range(1, nc - 1)), [nc - 1]]
+    return np.array([np.linalg.norm(a[gr] - b[gr]) / max(np.linalg.norm(b[gr]), 1e-300)
+                     for gr in groups])
+
+
+def incr_rel(Ug, Uo, U0):
+    """relative L2 error of the increment U^{n+1} - U^n (a stricter view)"""
+    return rel_l2(np.asarray(Ug, dtype=np.float64) - U0, np.asarray(Uo) - U0)
+
+
+def cast(U, g):
+    return U.astype(np.float32 if g.fp_bytes == 4 else np.float64)
+
+
+# ---------------------------------------------------------------------------
+# flux operator
+# ---------------------------------------------------------------------------
+
+MIXED_BC = (C.BC_FREESTREAM, C.BC_ZEROGRAD, C.BC_SLIP, C.BC_SLIP, C.BC_ZEROGRAD, C.BC_SLIP)
+
+
+@pytest.mark.parametrize("dim,n,fp,tol", [
+    (2, (37, 29), 8, 1e-12), (2, (37, 29), 4, 1e-4),
+    (3, (21, 19, 13), 4, 1e-4), (3, (21, 19, 13), 8, 1e-12),
+])
+@pytest.mark.parametrize("bc", ["mixed", "periodic"])
+def test_rhs_matches_oracle(oracle, dim, n, fp, tol, bc):
+    bcs = MIXED_BC if bc == "mixed" else (C.BC_PERIODIC,) * 6
+    g = C.small_grid(dim, n, h=0.1, fp_bytes=fp, bc=bcs, Re=80.0, Mach=0.4)
+    U = cast(C.random_state(g, seed=41, amp=0.05), g)
+    grid = ibm.Grid(g)
+    L = grid.rhs(torch.from_numpy(U)).cpu().numpy()
+    Lo = oracle.rhs(g, U.astype(np.float64)).reshape(L.shape)
+    err = rel_l2(L, Lo)
+    assert np.all(err < tol), err
+
+
+def test_rhs_inviscid_supersonic(oracle):
+    g = C.small_grid(3, (17, 12, 10), h=0.05, fp_bytes=8, Re=0.0, Mach=2.0)
+    U = C.random_state(g, seed=42, amp=0.1)
+    grid = ibm.Grid(g)
+    L = grid.rhs(torch.from_numpy(U)).cpu().numpy()
+    err = rel_l2(L, oracle.rhs(g, U).reshape(L.shape))
+    assert np.all(err < 1e-12), err
+
+
+# ---------------------------------------------------------------------------
+# marker bins and quadrature
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,n,tile,count", [
+    (2, (77, 45), (16, 16, 1), 500), (2, (77, 45), (8, 4, 1), 500), (3, (37, 29, 23), (8, 8, 8), 2000),
+    (3, (37, 29, 23), (4, 8, 2), 700),
+])
+def test_bins_bit_exact(oracle, dim, n, tile, count):
+    g = C.small_grid(dim, n, h=0.1, fp_bytes=4, tile=tile)
+    X = C.random_markers(g, count, seed=43)
+    grid = ibm.Grid(g, max_markers=count)
+    nk = grid.set_markers(X, np.ones(count), dedup=False)
+    assert nk == count
+    tile_off, perm, keys = grid.bins()
+    rc, to, po, ko = oracle.bin_markers(g, X)
+    np.testing.assert_array_equal(tile_off, to)
+    np.testing.assert_array_equal(perm, po)
+    np.testing.assert_array_equal(keys, ko)
+
+
+def test_sphere_dedup_bins_and_quadrature_full_size(oracle):
+    c = C.heated_sphere(n=256)
+    grid = ibm.Grid(c.grid, max_markers=len(c.X))
+    nk = grid.set_markers(c.X, c.Tw)
+    rc, keep = oracle.dedup(c.grid, c.X)
+    assert nk == len(keep)
+    X, eps, idx = grid.markers()
+    np.testing.assert_array_equal(idx, keep)
+    np.testing.assert_array_equal(X, c.X[keep])
+    tile_off, perm, keys = grid.bins()
+    rc, to, po, ko = oracle.bin_markers(c.grid, c.X[keep])
+    np.testing.assert_array_equal(tile_off, to)
+    np.testing.assert_array_equal(perm, po)
+    np.testing.assert_array_equal(keys, ko)
+    rc, eo, it, res = oracle.quadrature(c.grid, c.X[keep])
+    assert np.max(np.abs(eps - eo) / eo) < 1e-7
+
+
+def test_isolated_marker_weight_is_2_pow_d():
+    for dim in (2, 3):
+        g = C.small_grid(dim, (12, 12, 12)[:dim], h=0.25, fp_bytes=8)
+        X = C.random_markers(g, 1, seed=44)
+        grid = ibm.Grid(g, max_markers=1)
+        grid.set_markers(X, np.ones(1))
+        _, eps, _ = grid.markers()
+        assert abs(eps[0] - 2.0 ** dim) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# interpolation / spreading operators
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,fp,tol", [(2, 8, 1e-13), (3, 8, 1e-13), (2, 4, 2e-6), (3, 4, 2e-6)])
+def test_interp_spread_adjoint_and_parity(oracle, dim, fp, tol):
+    g = C.small_grid(dim, (33, 27, 19)[:dim], h=0.2, fp_bytes=fp)
+    X = C.random_markers(g, 60, seed=45)
+    grid = ibm.Grid(g, max_markers=60)
+    nk = grid.set_markers(X, np.ones(60))
+    Xk, eps, idx = grid.markers()
+    rng = np.random.Generator(np.random.PCG64(46))
+    u = cast(rng.standard_normal((2, g.ncells)), g)
+    F = rng.standard_normal((nk, 2))
+    Iu = grid.interpolate(torch.from_numpy(u)).cpu().numpy()
+    SF = grid.spread(torch.from_numpy(F)).cpu().numpy().reshape(2, -1)
+    np.testing.assert_allclose(Iu, oracle.interp(g, Xk, u.astype(np.float64)), rtol=tol, atol=tol)
+    np.testing.assert_allclose(SF, oracle.spread(g, Xk, eps, F), rtol=tol, atol=tol)
+    lhs = np.sum(eps[:, None] * F * Iu)
+    rhs = np.sum(u.astype(np.float64) * SF)
+    assert abs(lhs - rhs) <= 10 * tol * np.sum(np.abs(eps[:, None] * F * Iu))
+    # partition of unity: I(S(1)) = 1
+    ones = torch.ones((nk, 1), dtype=torch.float64)
+    back = grid.interpolate(grid.spread(ones)).cpu().numpy()
+    assert np.max(np.abs(back - 1.0)) < (1e-9 if fp == 8 else 1e-6)
+
+
+def test_zero_forcing_body_at_rest_in_fluid_at_wall_temperature():
+    g = C.small_grid(3, (24, 24, 24), h=0.125, fp_bytes=8, bc=(C.BC_PERIODIC,) * 6)
+    R = 1.0 / (g.gamma * g.Mach ** 2)
+    U = np.zeros(g.shape())
+    U[0] = 1.2
+    U[-1] = 1.2 * R * 1.4 / (g.gamma - 1)
+    X = C.fibonacci_sphere_markers(300, radius=0.6)
+    grid = ibm.Grid(g, max_markers=300)
+    grid.set_markers(X, np.full(300, 1.4))
+    grid.set_state(U)
+    grid.step(1)
+    rho, F, Q = grid.marker_forcing()
+    assert np.abs(F).max() < 1e-9 and np.abs(Q).max() < 1e-8
+    np.testing.assert_allclose(grid.get_state().cpu().numpy(), U, rtol=1e-13, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# full IBM steps
+# ---------------------------------------------------------------------------
+
+def _compare_run(oracle, case, steps, tol, dt_fixed=0.0, energy_reading=0, tol_force=None):
+    g = case.grid
+    U0 = cast(C.initial_state(g, case.seed), g)
+    grid = ibm.Grid(g, max_markers=len(case.X), energy_reading=energy_reading)
+    nk = grid.set_markers(case.X, case.Tw, motion=case.motion)
+    grid.set_state(U0)
+    run = oracle.Run(g, case.X, case.Tw, motion=case.motion, energy_reading=energy_reading)
+    assert nk == len(run.X)
+    U = U0.astype(np.float64)
+    worst = 0.0
+    for s in range(steps):
+        grid.step(1, dt_fixed)
+        dtg, tg, ns = grid.time()
+        Ug = grid.get_state().cpu().numpy()
+        Uo = run.step(U, dt_fixed=dtg if g.fp_bytes == 4 else dt_fixed)
+        assert abs(dtg - run.dt) <= 1e-6 * run.dt
+        assert abs(dtg - oracle.dt(g, U)) <= 2e-6 * dtg
+        err = rel_l2(Ug, Uo)
+        worst = max(worst, err.max())
+        assert np.all(err < tol), (s, err)
+        # continue both from their own states (the GPU keeps its own)
+        U = Uo
+    rho, F, Q = grid.marker_forcing()
+    Fo = run.G / run.dt
+    Qo = run.H / run.dt
+    tf = tol_force if tol_force is not None else tol
+    assert np.linalg.norm(F - Fo) <= tf * max(np.linalg.norm(Fo), 1e-30)
+    assert np.linalg.norm(Q - Qo) <= tf * max(np.linalg.norm(Qo), 1e-30)
+    fg = grid.forces()
+    fo = run.forces()
+    assert abs(fg["Cd"] - fo[2]) <= tf * abs(fo[2]) + 1e-12
+    assert abs(fg["heat_rate"] - fo[1]) <= tf * abs(fo[1]) + 1e-12
+    return worst
+
+
+def test_cylinder_fp64_matches_oracle(oracle):
+    c = C.heated_cylinder()
+    worst = _compare_run(oracle, c, 20, 1e-11)
+    assert worst < 1e-11
+
+
+def test_cylinder_fp64_energy_reading_total(oracle):
+    c = C.heated_cylinder()
+    _compare_run(oracle, c, 3, 1e-11, energy_reading=1)
+
+
+def test_sphere_fp32_per_step(oracle):
+    c = C.heated_sphere(n=64, n_markers=3000)
+    _compare_run(oracle, c, 5, 1e-5, tol_force=1e-3)
+
+
+def test_supersonic_cold_sphere_fp32(oracle):
+    c = C.heated_sphere(n=48, mach=2.0, Tw=0.5, n_markers=2000)
+    _compare_run(oracle, c, 5, 1e-5, tol_force=1e-3)
+
+
+def test_moving_cylinder_fp32(oracle):
+    c = C.oscillating_cylinder(scale_div=4)
+    _compare_run(oracle, c, 5, 1e-5, tol_force=2e-3)
+
+
+def test_fluid_only_step_no_markers(oracle):
+    g = C.small_grid(3, (30, 22, 17), h=0.1, fp_bytes=4, Re=100.0, Mach=0.5)
+    U0 = cast(C.random_state(g, seed=47, amp=0.02), g)
+    grid = ibm.Grid(g)
+    grid.set_state(U0)
+    grid.step(1)
+    Ug = grid.get_state().cpu().numpy()
+    dt, Uo = oracle.predictor(g, U0.astype(np.float64))
+    assert np.all(rel_l2(Ug, Uo.reshape(Ug.shape)) < 1e-6)
+    assert np.all(incr_rel(Ug, Uo.reshape(Ug.shape), U0.astype(np.float64)) < 1e-3)
+
+
+def test_deterministic_bitwise():
+    c = C.heated_sphere(n=48, n_markers=2000)
+    outs = []
+    for _ in range(2):
+        U0 = C.initial_state(c.grid, c.seed).astype(np.float32)
+        grid = ibm.Grid(c.grid, max_markers=len(c.X))
+        grid.set_markers(c.X, c.Tw)
+        grid.set_state(U0)
+        grid.step(3)
+        outs.append((grid.get_state().cpu().numpy(), grid.forces()["Cd"]))
+        grid.close()
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    assert outs[0][1] == outs[1][1]
+
+
+@pytest.mark.parametrize("mach,Tw", [(0.3, 1.5)])
+def test_full_size_sphere_one_step(oracle, mach, Tw):
+    """The benchmark workload (256^3, 20000 markers -> dedup) for one step,
+    compared element by element with the oracle."""
+    c = C.heated_sphere(n=256, mach=mach, Tw=Tw)
+    _compare_run(oracle, c, 1, 1e-5, tol_force=1e-3)
+
+
+def test_long_run_1000_steps(oracle):
+    c = C.heated_sphere(n=40, n_markers=2000)
+    g = c.grid
+    U0 = C.initial_state(g, c.seed).astype(np.float32)
+    grid = ibm.Grid(g, max_markers=len(c.X))
+    grid.set_markers(c.X, c.Tw)
+    grid.set_state(U0)
+    run = oracle.Run(g, c.X, c.Tw)
+    U = U0.astype(np.float64)
+    for _ in range(1000):
+        U = run.step(U)
+    grid.step(1000)
+    Ug = grid.get_state().cpu().numpy()
+    err = rel_l2(Ug, U.reshape(Ug.shape))
+    assert np.all(err < 1e-3), err
+
+
+# ---------------------------------------------------------------------------
+# error reporting (host-made faults only)
+# ---------------------------------------------------------------------------
+
+def test_errors_are_reported():
+    g = C.small_grid(2, (32, 32), h=0.1, fp_bytes=8)
+    grid = ibm.Grid(g, max_markers=4)
+    with pytest.raises(ibm.IbmError) as e:
+        grid.step(1)
+    assert e.value.status == 7
+    X = np.array([[g.lo[0] + 1.5 * g.h, 0.0]])
+    with pytest.raises(ibm.IbmError) as e:
+        grid.set_markers(X, np.ones(1))
+    assert e.value.status == 1
+    with pytest.raises(ibm.IbmError) as e:
+        grid.set_markers(C.random_markers(g, 20, seed=1), np.ones(20), dedup=False)
+    assert e.value.status == 5
+    with pytest.raises(ibm.IbmError) as e:
+        ibm.ibm_backward(grid.h, 1.0, 0.0, 0, 2)
+    assert e.value.status == 8
+    U = C.random_state(g, seed=48)
+    U[0, 5, 5] = np.nan
+    grid.set_state(U)
+    grid.step(2)
+    with pytest.raises(ibm.IbmError) as e:
+        grid.sync()
+    assert e.value.status == 3
