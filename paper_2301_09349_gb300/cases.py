@@ -181,11 +181,21 @@ def heated_cylinder(scale: int = 1, seed: int = 1) -> Case:
     return Case("heated_cylinder_128x64", g, X, np.full(len(X), 1.1), None, None, 200, seed)
 
 
-def heated_sphere(n: int = 256, mach: float = 0.3, Tw: float = 1.5, n_markers: int = 20000,
-                  seed: int = 2) -> Case:
-    """3D heated sphere: n^3 over [-3,5]x[-4,4]^2, Fibonacci markers on r = 0.5,
-    Re 300, FP32 (Sec. 4 stand-in).  n = 256 is the full workload."""
+def markers_at_cell_spacing(h: float, D: float = 1.0) -> int:
+    """Fibonacci marker count whose mean spacing on a sphere of diameter D is
+    one cell: surface area / h^2 (the paper's sphere has 12119 markers for
+    pi D^2 / h^2 = 12868 at h = D/64, Sec. 4.1)."""
+    return int(round(math.pi * D * D / (h * h)))
+
+
+def heated_sphere(n: int = 256, mach: float = 0.3, Tw: float = 1.5,
+                  n_markers: Optional[int] = None, seed: int = 2) -> Case:
+    """3D heated sphere: n^3 over [-3,5]x[-4,4]^2, Fibonacci markers on r = 0.5
+    at a spacing of about one cell (3217 at n = 256), Re 300, FP32 (Sec. 4
+    stand-in).  n = 256 is the full workload."""
     h = 8.0 / n
+    if n_markers is None:
+        n_markers = markers_at_cell_spacing(h)
     g = GridDesc(dim=3, n=(n, n, n), lo=(-3.0, -4.0, -4.0), h=h, fp_bytes=4,
                  Re=300.0, Mach=mach, bc=_bc_for(3, mach), tile=(8, 8, 8))
     X = fibonacci_sphere_markers(n_markers)
@@ -206,10 +216,11 @@ def oscillating_cylinder(scale_div: int = 1, seed: int = 3) -> Case:
 
 
 def adjoint_sphere(seed: int = 5) -> Case:
-    """3D sphere 128^3 over [-3,5]x[-4,4]^2, 5000 Fibonacci markers, Ma 0.5, Re 100."""
+    """3D sphere 128^3 over [-3,5]x[-4,4]^2, Fibonacci markers at one-cell
+    spacing (804), Ma 0.5, Re 100."""
     g = GridDesc(dim=3, n=(128, 128, 128), lo=(-3.0, -4.0, -4.0), h=1.0 / 16.0, fp_bytes=4,
                  Re=100.0, Mach=0.5, bc=_bc_for(3, 0.5), tile=(8, 8, 8))
-    X = fibonacci_sphere_markers(5000)
+    X = fibonacci_sphere_markers(markers_at_cell_spacing(g.h))
     return Case("adjoint_sphere_128^3", g, X, np.full(len(X), 1.5), None, None, 500, seed)
 
 

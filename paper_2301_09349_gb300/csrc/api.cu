@@ -163,7 +163,7 @@ void layout(ibm_grid *g, const ibm_grid_desc &d, int cap, char *base, size_t *to
     void *U1 = c.take<char>(sb);
     void *L = c.take<char>(sb);
     const size_t nbm = fluid_blockmax_count(gp, d.fp_bytes);
-    float *blockmax = c.take<float>(nbm);
+    double *blockmax = c.take<double>(nbm);
     unsigned *counter = c.take<unsigned>(4);
     double *scal = c.take<double>(8);
     int *err = c.take<int>(4);

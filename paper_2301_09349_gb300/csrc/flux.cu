@@ -187,9 +187,9 @@ __device__ __forceinline__ void direction_pass(const GridParams &g, const T *__r
     __syncthreads();
 }
 
-__device__ __forceinline__ float warp_max(float v) {
+__device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
@@ -197,14 +197,14 @@ __device__ __forceinline__ float warp_max(float v) {
 template <int DIM, typename T, int MODE>
 __global__ void __launch_bounds__(NT)
 stage_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ Lp,
-             T *__restrict__ out, float *__restrict__ blockmax, unsigned *__restrict__ counter,
+             T *__restrict__ out, double *__restrict__ blockmax, unsigned *__restrict__ counter,
              double *__restrict__ dt_ptr, int *__restrict__ err, double dt_fixed) {
     using B = Box<DIM, T>;
     constexpr int NC = DIM + 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sW = reinterpret_cast<T *>(smem_raw);
     T *sF = sW + B::NW * B::PN;
-    __shared__ float s_red[NT / 32];
+    __shared__ double s_red[NT / 32];
     __shared__ int s_flag;
 
     const int tid = threadIdx.x;
@@ -272,7 +272,7 @@ stage_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ 
 
     // ---- outputs
     const T inv_h = (T)g.inv_h;
-    float smax = 0.0f;
+    double smax = 0.0;
     int bad = 0;
 #pragma unroll
     for (int i = 0; i < B::CPT; ++i) {
@@ -309,9 +309,9 @@ stage_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ 
 #pragma unroll
             for (int d = 0; d < DIM; ++d) s += (fabs(sW[(1 + d) * B::PN + q]) + c) * inv_h;
             s += T(2 * DIM) * nu * inv_h * inv_h;
-            const float sf = (float)s;
-            if (!(rho > T(0) && p > T(0) && sf <= FLT_MAX)) bad = 1;
-            else smax = fmaxf(smax, sf);
+            const double sd = (double)s;
+            if (!(rho > T(0) && p > T(0) && sd <= DBL_MAX)) bad = 1;
+            else smax = fmax(smax, sd);
         }
     }
 
@@ -324,8 +324,8 @@ stage_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ 
         const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
         const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
         if (tid == 0) {
-            float m = s_red[0];
-            for (int w = 1; w < NT / 32; ++w) m = fmaxf(m, s_red[w]);
+            double m = s_red[0];
+            for (int w = 1; w < NT / 32; ++w) m = fmax(m, s_red[w]);
             blockmax[bid] = m;
             if (bad) record_error(err, ERR_NONFINITE);
             __threadfence();
@@ -335,19 +335,19 @@ stage_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ 
         __syncthreads();
         if (s_flag) {
             __threadfence();
-            float m = 0.0f;
-            for (unsigned b = tid; b < nblocks; b += NT) m = fmaxf(m, __ldcg(blockmax + b));
+            double m = 0.0;
+            for (unsigned b = tid; b < nblocks; b += NT) m = fmax(m, __ldcg(blockmax + b));
             m = warp_max(m);
             if ((tid & 31) == 0) s_red[tid >> 5] = m;
             __syncthreads();
             if (tid == 0) {
-                float mm = s_red[0];
-                for (int w = 1; w < NT / 32; ++w) mm = fmaxf(mm, s_red[w]);
+                double mm = s_red[0];
+                for (int w = 1; w < NT / 32; ++w) mm = fmax(mm, s_red[w]);
                 double dtv;
                 if (dt_fixed > 0.0) {
                     dtv = dt_fixed;
-                } else if (mm > 0.0f && mm <= FLT_MAX) {
-                    dtv = g.cfl / (double)mm;
+                } else if (mm > 0.0 && mm <= DBL_MAX) {
+                    dtv = g.cfl / mm;
                 } else {
                     dtv = 0.0;
                     record_error(err, ERR_NONFINITE);

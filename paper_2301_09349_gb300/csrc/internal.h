@@ -14,7 +14,7 @@ namespace ibmk {
 // last block) dt = cfl / max s, or dt_fixed when > 0, written to *dt.
 // Stage 2: out = U/2 + (U1 + dt L(U1))/2 with U1 = U + dt Lprev built on load.
 struct FluidBuffers {
-    float *blockmax;        // one per CTA of the stage-1 grid
+    double *blockmax;       // one per CTA of the stage-1 grid
     unsigned *counter;      // last-block ticket (zero between launches)
     double *dt;             // device step size
     int *err;               // device error word
