@@ -214,6 +214,36 @@ ibm_status ibm_profile(ibm_grid *g, int enable);
  * arrays hold IBM_PROF_GROUPS entries (either may be NULL).  Resets. */
 ibm_status ibm_profile_read(ibm_grid *g, double *ms, long long *launches);
 
+/* ---- allocation-free stage 1 ------------------------------------------- */
+
+/* Largest stage-1 launch (thread blocks) ibm_rhs_dt_noalloc serves.  A 3D
+ * FP32 grid uses one block per 8x8x8 cells (65536 blocks = 2^25 cells), a
+ * 3D FP64 grid one per 8x8x4, a 2D grid one per 16x16. */
+#define IBM_NOALLOC_MAX_CTAS 65536
+
+/* Fluid stage 1 for callers that cannot allocate device memory: writes
+ * L = L(U) (as ibm_rhs) and the stable step size *dt = cfl / max_j s_j(U)
+ * (as ibm_step computes it), with no handle and no workspace.  There is no
+ * counterpart in the paper: this is a packaging of the scheme for hosts that
+ * own all device memory (a plug-in that may not call cudaMalloc) or loops
+ * that cannot afford an allocation.
+ *  - desc: grid description (host); U, L: (dim+2)*N device elements of the
+ *    grid's type; dt: one device double; stream: a cudaStream_t.
+ *  - Scratch (block maxima, a ticket counter, an error word) lives in one
+ *    static device array of 65536 doubles + 256 bytes (about 512 KiB) that
+ *    every GPU loading the library holds until the process exits.  The first
+ *    call on a device resolves that array's device address (once per device,
+ *    with that device current); make that first call before any stream
+ *    capture.
+ *  - Every call shares the array: calls that overlap on the GPU (other
+ *    streams, other host threads) race and must be serialised by the caller.
+ *  - A non-finite or non-positive state gives *dt = 0.  No device memory is
+ *    allocated or freed.  Errors: IBM_ERR_ARG (invalid description, null
+ *    buffer, or a grid needing more than IBM_NOALLOC_MAX_CTAS blocks; the
+ *    message is ibm_last_error(NULL)), IBM_ERR_CUDA.  Asynchronous. */
+ibm_status ibm_rhs_dt_noalloc(const ibm_grid_desc *desc, const void *U, void *L, double *dt,
+                              void *stream);
+
 #ifdef __cplusplus
 }
 #endif

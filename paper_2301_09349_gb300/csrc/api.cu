@@ -300,6 +300,11 @@ ibm_status rebuild_markers(ibm_grid *g, int warm) {
 
 }  // namespace
 
+namespace ibmk {
+GridParams params_from_desc(const ibm_grid_desc &d) { return make_params(d); }
+void set_handle_free_error(const char *msg) { g_create_error = msg; }
+}  // namespace ibmk
+
 extern "C" {
 
 size_t ibm_workspace_bytes(const ibm_grid_desc *desc, int max_markers) {

@@ -79,6 +79,7 @@ SIGNATURES = [
     ("ibm_spread", ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp]),
     ("ibm_profile", ctypes.c_int, [_vp, ctypes.c_int]),
     ("ibm_profile_read", ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    ("ibm_rhs_dt_noalloc", ctypes.c_int, [ctypes.POINTER(GridDescC), _vp, _vp, _vp, _vp]),
 ]
 
 PROF_GROUPS = ["stage1", "stage2", "markers", "interp_force", "spread_apply", "finish"]
@@ -279,6 +280,13 @@ def ibm_profile_read(h) -> dict:
     n = (ctypes.c_longlong * len(PROF_GROUPS))()
     _check(lib().ibm_profile_read(h, ms, n), h)
     return {name: (ms[i], n[i]) for i, name in enumerate(PROF_GROUPS)}
+
+
+def ibm_rhs_dt_noalloc(desc: GridDescC, U_ptr: int, L_ptr: int, dt_ptr: int, stream_ptr: int):
+    """Stage 1 without handle or workspace (scratch in a static device array;
+    overlapping calls race)."""
+    _check(lib().ibm_rhs_dt_noalloc(ctypes.byref(desc), _vp(U_ptr), _vp(L_ptr), _vp(dt_ptr),
+                                    _vp(stream_ptr)), None)
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,71 @@
+"""The allocation-free stage-1 entry point, ibm_rhs_dt_noalloc, against the
+regular entry points.
+
+It serves callers that may not allocate device memory (a plug-in inside a
+host that owns the device-memory budget, or a loop that cannot afford a
+cudaMalloc): its scratch lives in a static device array.  Its L must equal
+ibm_rhs's and its step size the one ibm_step computes from the same state,
+within the FP32 operator tolerance used by the parity tests (1e-4 relative
+for L; the step size is a max-reduction of identical values, so 1e-12).
+Two calls in a row check that the shared scratch is reset between calls.
+This file is collected last on purpose.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2301_09349_gb300 import cases as C
+from paper_2301_09349_gb300 import ibm
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    a = a.reshape(a.shape[0], -1).astype(np.float64)
+    b = b.reshape(b.shape[0], -1).astype(np.float64)
+    return max(np.linalg.norm(a[c] - b[c]) / np.linalg.norm(b[c]) for c in range(a.shape[0]))
+
+
+def test_noalloc_stage1_matches_regular_entry_points():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2301_09349_gb300 import build
+    build.build()
+    L = ibm.lib()
+    g = C.small_grid(3, (45, 38, 29), h=0.1, fp_bytes=4, Re=150.0, Mach=0.4)
+    desc = ibm.make_desc(g)
+    stream = torch.cuda.current_stream()
+    grid = ibm.Grid(g)
+    for call, seed in enumerate((51, 52)):
+        U = torch.from_numpy(C.random_state(g, seed=seed, amp=0.03).astype(np.float32)).cuda()
+        Lna = torch.empty_like(U)
+        dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        st = L.ibm_rhs_dt_noalloc(ctypes.byref(desc), ctypes.c_void_p(U.data_ptr()),
+                                  ctypes.c_void_p(Lna.data_ptr()), ctypes.c_void_p(dt.data_ptr()),
+                                  ctypes.c_void_p(stream.cuda_stream))
+        assert st == 0, ibm.ibm_last_error(None)
+        torch.cuda.synchronize()
+        L_ref = grid.rhs(U)
+        grid.set_state(U)
+        grid.step(1)
+        dt_ref, _, _ = grid.time()
+        err = _rel(Lna.cpu().numpy(), L_ref.cpu().numpy())
+        assert err < 1e-4, (call, err)
+        assert abs(dt.item() - dt_ref) <= 1e-12 * dt_ref, (call, dt.item(), dt_ref)
+    grid.close()
+
+
+def test_noalloc_rejects_oversized_grids():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    L = ibm.lib()
+    g = C.small_grid(3, (1024, 512, 72), h=0.1, fp_bytes=4)   # 73728 blocks of 8^3
+    desc = ibm.make_desc(g)
+    st = L.ibm_rhs_dt_noalloc(ctypes.byref(desc), ctypes.c_void_p(256), ctypes.c_void_p(256),
+                              ctypes.c_void_p(256), None)
+    assert st == ibm.IBM_OK + 1
+    assert "IBM_NOALLOC_MAX_CTAS" in ibm.ibm_last_error(None)
