@@ -217,8 +217,9 @@ ibm_status ibm_profile_read(ibm_grid *g, double *ms, long long *launches);
 /* ---- allocation-free stage 1 ------------------------------------------- */
 
 /* Largest stage-1 launch (thread blocks) ibm_rhs_dt_noalloc serves.  A 3D
- * FP32 grid uses one block per 8x8x8 cells (65536 blocks = 2^25 cells), a
- * 3D FP64 grid one per 8x8x4, a 2D grid one per 16x16. */
+ * FP32 grid uses one block per 32x8 column chunk of 8 to 32 planes (2048
+ * blocks at 256^3), a 3D FP64 grid one per 8x8x4 cells, a 2D grid one per
+ * 16x16 cells. */
 #define IBM_NOALLOC_MAX_CTAS 65536
 
 /* Fluid stage 1 for callers that cannot allocate device memory: writes

@@ -49,15 +49,23 @@ struct Box {
     static constexpr size_t SMEM = sizeof(T) * (size_t)(NW * PN + NC * NFMAX);
 };
 
+// Arithmetic helpers.  FP32 uses the hardware approximations (MUFU
+// reciprocal / reciprocal square root, ~2 ulp), which are far inside the
+// FP32 parity tolerance; FP64 keeps correctly rounded division and sqrt.
+template <typename T> __device__ __forceinline__ T fdiv(T a, T b);
+template <> __device__ __forceinline__ float fdiv<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double fdiv<double>(double a, double b) { return a / b; }
+
+// sqrt of a positive argument
+template <typename T> __device__ __forceinline__ T psqrt(T x);
+template <> __device__ __forceinline__ float psqrt<float>(float x) { return x * rsqrtf(x); }
+template <> __device__ __forceinline__ double psqrt<double>(double x) { return sqrt(x); }
+
 template <typename T>
 __device__ __forceinline__ T van_leer(T a, T b) {
     T ab = a * b;
-    return ab > T(0) ? T(2) * ab / (a + b) : T(0);
+    return ab > T(0) ? fdiv<T>(T(2) * ab, a + b) : T(0);
 }
-
-template <typename T> __device__ __forceinline__ T tsqrt(T x);
-template <> __device__ __forceinline__ float tsqrt<float>(float x) { return sqrtf(x); }
-template <> __device__ __forceinline__ double tsqrt<double>(double x) { return sqrt(x); }
 
 // Numerical flux through the face between box cells a and a + s_D.
 template <int DIM, typename T, int D>
@@ -68,7 +76,7 @@ __device__ __forceinline__ void face_flux(const GridParams &g, const T *__restri
     constexpr int NC = DIM + 2;
     const int b = a + s;
     const T gam = (T)g.gamma;
-    const T gm1 = (T)(g.gamma - 1.0);
+    const T inv_gm1 = (T)(1.0 / (g.gamma - 1.0));
 
     // MUSCL reconstruction of (rho, u.., p) with the van Leer limiter
     T wl[NC], wr[NC];
@@ -88,11 +96,11 @@ __device__ __forceinline__ void face_flux(const GridParams &g, const T *__restri
         keL += wl[1 + m] * wl[1 + m];
         keR += wr[1 + m] * wr[1 + m];
     }
-    const T EL = wl[NC - 1] / gm1 + T(0.5) * wl[0] * keL;
-    const T ER = wr[NC - 1] / gm1 + T(0.5) * wr[0] * keR;
+    const T EL = wl[NC - 1] * inv_gm1 + T(0.5) * wl[0] * keL;
+    const T ER = wr[NC - 1] * inv_gm1 + T(0.5) * wr[0] * keR;
     const T unL = wl[1 + D], unR = wr[1 + D];
-    const T cL = tsqrt<T>(gam * wl[NC - 1] / wl[0]);
-    const T cR = tsqrt<T>(gam * wr[NC - 1] / wr[0]);
+    const T cL = psqrt<T>(fdiv<T>(gam * wl[NC - 1], wl[0]));
+    const T cR = psqrt<T>(fdiv<T>(gam * wr[NC - 1], wr[0]));
     const T sL = fabs(unL) + cL, sR = fabs(unR) + cR;
     const T smax = sL > sR ? sL : sR;
     F[0] = T(0.5) * (wl[0] * unL + wr[0] * unR) - T(0.5) * smax * (wr[0] - wl[0]);
@@ -115,7 +123,7 @@ __device__ __forceinline__ void face_flux(const GridParams &g, const T *__restri
     const T *Tc = sW + (DIM + 2) * B::PN;
     const T Tf = T(0.5) * (Tc[a] + Tc[b]);
     const T Sv = (T)g.S;
-    const T mu = (T)g.mu_inf * Tf * tsqrt<T>(Tf) * (T(1) + Sv) / (Tf + Sv);
+    const T mu = fdiv<T>((T)g.mu_inf * Tf * psqrt<T>(Tf) * (T(1) + Sv), Tf + Sv);
     const T lam = mu * (T)(g.cp / g.Pr);
     T grad[DIM][DIM];
 #pragma unroll
@@ -216,36 +224,53 @@ stage_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ 
     const T invR = (T)(1.0 / g.R);
 
     // ---- load tile + halo, build U1 on the fly in stage 2, to primitives
+    // Tiles whose halo lies inside the domain index directly; the others map
+    // every halo index through the boundary conditions.
+    const bool interior = ox >= 2 && oy >= 2 && ox + B::BX + 2 <= g.n[0] &&
+                          oy + B::BY + 2 <= g.n[1] &&
+                          (DIM == 2 || (oz >= 2 && oz + B::BZ + 2 <= g.n[2]));
+    const T p_inf_E = (T)(g.p_inf / (g.gamma - 1.0) + 0.5);
     for (int q = tid; q < B::PN; q += NT) {
         const int lx = q % B::PX;
         const int r = q / B::PX;
         const int ly = r % B::PY;
         const int lz = r / B::PY;
-        int flip = 0, fs = 0;
-        const int sx = map_axis(ox + lx - 2, g.n[0], g.bc[0], g.bc[1], 0, flip, fs);
-        const int sy = map_axis(oy + ly - 2, g.n[1], g.bc[2], g.bc[3], 1, flip, fs);
-        const int sz = DIM == 3 ? map_axis(oz + lz - 2, g.n[2], g.bc[4], g.bc[5], 2, flip, fs) : 0;
         T u[NC];
-        if (fs) {
-            u[0] = T(1);
-            u[1] = T(1);
-#pragma unroll
-            for (int d = 1; d < DIM; ++d) u[1 + d] = T(0);
-            u[NC - 1] = (T)(g.p_inf / (g.gamma - 1.0) + 0.5);
-        } else {
-            const long long j = sx + (long long)g.n[0] * (sy + (long long)g.n[1] * sz);
+        if (interior) {
+            const long long j = (ox + lx - 2) +
+                                (long long)g.n[0] * ((oy + ly - 2) + (long long)g.n[1] * (oz + lz - 2 * (DIM == 3)));
 #pragma unroll
             for (int c = 0; c < NC; ++c) {
                 T v = __ldg(U + c * N + j);
                 if (MODE == 2) v = v + dt * __ldg(Lp + c * N + j);
                 u[c] = v;
             }
+        } else {
+            int flip = 0, fs = 0;
+            const int sx = map_axis(ox + lx - 2, g.n[0], g.bc[0], g.bc[1], 0, flip, fs);
+            const int sy = map_axis(oy + ly - 2, g.n[1], g.bc[2], g.bc[3], 1, flip, fs);
+            const int sz = DIM == 3 ? map_axis(oz + lz - 2, g.n[2], g.bc[4], g.bc[5], 2, flip, fs) : 0;
+            if (fs) {
+                u[0] = T(1);
+                u[1] = T(1);
 #pragma unroll
-            for (int d = 0; d < DIM; ++d)
-                if ((flip >> d) & 1) u[1 + d] = -u[1 + d];
+                for (int d = 1; d < DIM; ++d) u[1 + d] = T(0);
+                u[NC - 1] = p_inf_E;
+            } else {
+                const long long j = sx + (long long)g.n[0] * (sy + (long long)g.n[1] * sz);
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    T v = __ldg(U + c * N + j);
+                    if (MODE == 2) v = v + dt * __ldg(Lp + c * N + j);
+                    u[c] = v;
+                }
+#pragma unroll
+                for (int d = 0; d < DIM; ++d)
+                    if ((flip >> d) & 1) u[1 + d] = -u[1 + d];
+            }
         }
         const T rho = u[0];
-        const T inv = T(1) / rho;
+        const T inv = fdiv<T>(T(1), rho);
         T ke = 0;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
@@ -298,13 +323,13 @@ stage_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ 
         if (MODE == 1) {
             const int q = (cx + 2) + B::PX * (cy + 2) + (DIM == 3 ? B::PX * B::PY * (cz + 2) : 0);
             const T rho = sW[q], p = sW[(DIM + 1) * B::PN + q], Tt = sW[(DIM + 2) * B::PN + q];
-            const T c = tsqrt<T>((T)g.gamma * p / rho);
+            const T c = psqrt<T>(fdiv<T>((T)g.gamma * p, rho));
             T mu = T(0);
             if (g.mu_inf > 0.0) {
                 const T Sv = (T)g.S;
-                mu = (T)g.mu_inf * Tt * tsqrt<T>(Tt) * (T(1) + Sv) / (Tt + Sv);
+                mu = fdiv<T>((T)g.mu_inf * Tt * psqrt<T>(Tt) * (T(1) + Sv), Tt + Sv);
             }
-            const T nu = (T)g.kvisc * mu / rho;
+            const T nu = fdiv<T>((T)g.kvisc * mu, rho);
             T s = T(0);
 #pragma unroll
             for (int d = 0; d < DIM; ++d) s += (fabs(sW[(1 + d) * B::PN + q]) + c) * inv_h;
@@ -388,7 +413,7 @@ template <int MODE>
 cudaError_t dispatch(const GridParams &g, int fp_bytes, const void *U, const void *Lp, void *out,
                      const FluidBuffers &fb, double dt_fixed, cudaStream_t s) {
     if (g.dim == 3) {
-        if (fp_bytes == 4) return launch_one<3, float, MODE>(g, U, Lp, out, fb, dt_fixed, s);
+        if (fp_bytes == 4) return launch_zmarch(MODE, g, U, Lp, out, fb, dt_fixed, s);
         return launch_one<3, double, MODE>(g, U, Lp, out, fb, dt_fixed, s);
     }
     if (fp_bytes == 4) return launch_one<2, float, MODE>(g, U, Lp, out, fb, dt_fixed, s);
@@ -399,7 +424,8 @@ cudaError_t dispatch(const GridParams &g, int fp_bytes, const void *U, const voi
 
 size_t fluid_blockmax_count(const GridParams &g, int fp_bytes) {
     dim3 d;
-    if (g.dim == 3) d = fp_bytes == 4 ? stage_grid<3, float>(g) : stage_grid<3, double>(g);
+    if (g.dim == 3 && fp_bytes == 4) return zmarch_blocks(g);
+    if (g.dim == 3) d = stage_grid<3, double>(g);
     else d = fp_bytes == 4 ? stage_grid<2, float>(g) : stage_grid<2, double>(g);
     return (size_t)d.x * d.y * d.z;
 }

@@ -28,6 +28,10 @@ cudaError_t launch_stage2(const GridParams &g, int fp_bytes, const void *U, cons
 // L(U) only (no step size), for the diagnostic ibm_rhs
 cudaError_t launch_rhs(const GridParams &g, int fp_bytes, const void *U, void *L,
                        const FluidBuffers &fb, cudaStream_t s);
+// the z-marching form used for 3D FP32 grids (flux_zm.cu); mode 0/1/2 as above
+cudaError_t launch_zmarch(int mode, const GridParams &g, const void *U, const void *Lp, void *out,
+                          const FluidBuffers &fb, double dt_fixed, cudaStream_t s);
+size_t zmarch_blocks(const GridParams &g);
 
 // ---- markers (markers.cu) --------------------------------------------------
 struct MarkerBuffers {

@@ -227,22 +227,45 @@ __global__ void motion_kernel(const GridParams g, int ns, const double *__restri
 // interpolation + forcing
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ double warp_sum(double v) {
+// The 1D kernel evaluated in the field precision R: float on FP32 grids
+// (weights within ~1e-7 relative), double on FP64 grids.
+template <typename R> __device__ __forceinline__ R phi_r(R r);
+template <> __device__ __forceinline__ float phi_r<float>(float r) {
+    const float a = fabsf(r);
+    if (a <= 0.5f) return (1.0f + sqrtf(1.0f - 3.0f * a * a)) * (1.0f / 3.0f);
+    if (a <= 1.5f) {
+        const float b = 1.0f - a;
+        return (5.0f - 3.0f * a - sqrtf(1.0f - 3.0f * b * b)) * (1.0f / 6.0f);
+    }
+    return 0.0f;
+}
+template <> __device__ __forceinline__ double phi_r<double>(double r) { return phi_d(r); }
+
+// Offset in cells from a marker coordinate xi = (X - lo)/h to the centre of
+// cell c on one axis.  Every kernel evaluates the weights through this one
+// expression, so interpolation and spreading use identical weights.
+__device__ __forceinline__ double cell_offset(int c, double xi) { return ((double)c + 0.5) - xi; }
+
+template <typename R>
+__device__ __forceinline__ R warp_sum_r(R v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// support-cell weight Phi_k(j) for lane l of 3^DIM (offsets in z,y,x order)
-template <int DIM>
-__device__ __forceinline__ double lane_weight(const GridParams &g, const double *Xk, const int *ck,
-                                              int l, int *cell) {
+template <typename R> __device__ __forceinline__ R rdiv(R a, R b);
+template <> __device__ __forceinline__ float rdiv<float>(float a, float b) { return __fdividef(a, b); }
+template <> __device__ __forceinline__ double rdiv<double>(double a, double b) { return a / b; }
+
+// Phi_k(j) for the support cell `l` of 3^DIM (offsets in z, y, x order)
+template <int DIM, typename R>
+__device__ __forceinline__ R lane_weight(const double *xi, const int *ck, int l, int *cell) {
     const int o[3] = {l % 3 - 1, (l / 3) % 3 - 1, DIM == 3 ? l / 9 - 1 : 0};
-    double w = 1.0;
+    R w = R(1);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         cell[d] = ck[d] + o[d];
-        w *= phi_d((cell_center(g, d, cell[d]) - Xk[d]) * g.inv_h);
+        w *= phi_r<R>((R)cell_offset(cell[d], xi[d]));
     }
     if (DIM == 2) cell[2] = 0;
     return w;
@@ -252,9 +275,11 @@ template <int DIM, typename T>
 __global__ void __launch_bounds__(256)
 interp_force_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuffers m,
                     const int *__restrict__ perm) {
+    using R = T;
     constexpr int NF = DIM + 2;   // rho, rho u.., rho e
     constexpr int NS = DIM == 3 ? 27 : 9;
-    extern __shared__ __align__(16) double sS[];
+    extern __shared__ __align__(16) unsigned char smem_if[];
+    R *sS = reinterpret_cast<R *>(smem_if);
     const int bx = g.tile[0] + 2, by = g.tile[1] + 2, bz = DIM == 3 ? g.tile[2] + 2 : 1;
     const int bn = bx * by * bz;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -266,27 +291,28 @@ interp_force_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuf
                   tz = t / (g.ntile[0] * g.ntile[1]);
         const int ox = tx * g.tile[0] - 1, oy = ty * g.tile[1] - 1,
                   oz = DIM == 3 ? tz * g.tile[2] - 1 : 0;
+        // stage rho, rho u.., rho e of the tile grown by one cell
         for (int q = threadIdx.x; q < bn; q += blockDim.x) {
             const int lx = q % bx, ly = (q / bx) % by, lz = q / (bx * by);
             const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
             const bool in = gx >= 0 && gy >= 0 && gz >= 0 && gx < g.n[0] && gy < g.n[1] &&
                             (DIM == 2 || gz < g.n[2]);
-            double v[NF];
+            R v[NF];
             if (in) {
                 const long long j = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
-                const double rho = (double)U[j];
-                double ke = 0.0;
+                const R rho = U[j];
+                R ke = R(0);
 #pragma unroll
                 for (int d = 0; d < DIM; ++d) {
-                    const double md = (double)U[(1 + d) * N + j];
+                    const R md = U[(1 + d) * N + j];
                     v[1 + d] = md;
                     ke += md * md;
                 }
                 v[0] = rho;
-                v[NF - 1] = (double)U[(DIM + 1) * N + j] - 0.5 * ke / rho;
+                v[NF - 1] = U[(DIM + 1) * N + j] - R(0.5) * rdiv<R>(ke, rho);
             } else {
 #pragma unroll
-                for (int f = 0; f < NF; ++f) v[f] = 0.0;
+                for (int f = 0; f < NF; ++f) v[f] = R(0);
             }
 #pragma unroll
             for (int f = 0; f < NF; ++f) sS[f * bn + q] = v[f];
@@ -295,32 +321,33 @@ interp_force_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuf
         const int p0 = m.tile_off[t], p1 = m.tile_off[t + 1];
         for (int p = p0 + warp; p < p1; p += nwarps) {
             const int k = perm[p];
-            double Xk[3] = {0, 0, 0};
+            double xi[3] = {0, 0, 0};
             int ck[3] = {0, 0, 0};
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
-                Xk[d] = m.X[(long long)k * DIM + d];
-                ck[d] = owner_cell(Xk[d], g.lo[d], g.h);
+                const double X = m.X[(long long)k * DIM + d];
+                ck[d] = owner_cell(X, g.lo[d], g.h);
+                xi[d] = (X - g.lo[d]) * g.inv_h;
             }
-            double acc[NF];
+            R acc[NF];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) acc[f] = 0.0;
+            for (int f = 0; f < NF; ++f) acc[f] = R(0);
             if (lane < NS) {
                 int cell[3];
-                const double w = lane_weight<DIM>(g, Xk, ck, lane, cell);
+                const R w = lane_weight<DIM, R>(xi, ck, lane, cell);
                 const int li = (cell[0] - ox) + bx * ((cell[1] - oy) + by * (cell[2] - oz));
 #pragma unroll
                 for (int f = 0; f < NF; ++f) acc[f] = w * sS[f * bn + li];
             }
 #pragma unroll
-            for (int f = 0; f < NF; ++f) acc[f] = warp_sum(acc[f]);
+            for (int f = 0; f < NF; ++f) acc[f] = warp_sum_r<R>(acc[f]);
             if (lane == 0) {
-                const double rk = acc[0];
+                const double rk = (double)acc[0];
                 m.rhoL[k] = rk;
 #pragma unroll
                 for (int d = 0; d < DIM; ++d)
-                    m.G[(long long)k * DIM + d] = rk * m.Ub[(long long)k * DIM + d] - acc[1 + d];
-                m.H[k] = rk * g.cv * m.Tw[k] - acc[NF - 1];
+                    m.G[(long long)k * DIM + d] = rk * m.Ub[(long long)k * DIM + d] - (double)acc[1 + d];
+                m.H[k] = rk * g.cv * m.Tw[k] - (double)acc[NF - 1];
             }
         }
         __syncthreads();
@@ -332,8 +359,9 @@ interp_force_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuf
 // ---------------------------------------------------------------------------
 
 // Visit, in a fixed order, every marker whose support contains cell c:
-// neighbour owner cells (z, y, x offsets ascending), then sorted bin order.
-template <int DIM, typename F>
+// neighbour owner cells (z, y, x offsets ascending), then sorted bin order
+// (ascending marker index within a cell).  Global-memory form.
+template <int DIM, typename R, typename F>
 __device__ __forceinline__ bool gather_markers(const GridParams &g, const MarkerBuffers &m,
                                                const unsigned *__restrict__ keys,
                                                const int *__restrict__ perm, const int c[3],
@@ -357,10 +385,12 @@ __device__ __forceinline__ bool gather_markers(const GridParams &g, const Marker
                 const int end = m.tile_off[tc + 1];
                 for (int p = lo; p < end && keys[p] == key; ++p) {
                     const int k = perm[p];
-                    double w = 1.0;
+                    R w = R(1);
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d)
-                        w *= phi_d((cell_center(g, d, c[d]) - m.X[(long long)k * DIM + d]) * g.inv_h);
+                    for (int d = 0; d < DIM; ++d) {
+                        const double xi = (m.X[(long long)k * DIM + d] - g.lo[d]) * g.inv_h;
+                        w *= phi_r<R>((R)cell_offset(c[d], xi));
+                    }
                     visit(k, w);
                     any = true;
                 }
@@ -368,48 +398,181 @@ __device__ __forceinline__ bool gather_markers(const GridParams &g, const Marker
     return any;
 }
 
+constexpr int SP_T = 256;
+constexpr int SP_MAXC = 1024;   // staged candidates per band tile
+
+template <typename R>
+size_t spread_smem_bytes(const GridParams &g) {
+    const size_t bn = (size_t)(g.tile[0] + 2) * (g.tile[1] + 2) * (g.dim == 3 ? g.tile[2] + 2 : 1);
+    return SP_MAXC * (3 * sizeof(double) + 4 * sizeof(R) + sizeof(int)) + 2 * bn * sizeof(int);
+}
+
+// Forced update of one band cell (App. B, Eqs. u_centralF2 and e_centralF2;
+// f.u dropped): momentum += dt f, internal energy += dt q, rho unchanged.
+template <int DIM, typename T, typename R>
+__device__ __forceinline__ void apply_forcing(const GridParams &g, T *__restrict__ U, long long j,
+                                              const R *f, R qh) {
+    const long long N = g.N;
+    const double rho = (double)U[j];
+    double ke0 = 0.0, ke1 = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const double m0 = (double)U[(1 + d) * N + j];
+        const double m1 = m0 + (double)f[d];
+        ke0 += m0 * m0;
+        ke1 += m1 * m1;
+        U[(1 + d) * N + j] = (T)m1;
+    }
+    const double E = (double)U[(DIM + 1) * N + j];
+    const double En = g.energy_reading == 1 ? E + (double)qh
+                                            : (E - 0.5 * ke0 / rho + (double)qh) + 0.5 * ke1 / rho;
+    U[(DIM + 1) * N + j] = (T)En;
+}
+
 template <int DIM, typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(SP_T)
 spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m,
                     const unsigned *__restrict__ keys, const int *__restrict__ perm) {
-    const long long N = g.N;
+    using R = T;
+    constexpr int NT3 = DIM == 3 ? 27 : 9;
+    extern __shared__ __align__(16) unsigned char smem_sp[];
+    const int bx = g.tile[0] + 2, by = g.tile[1] + 2, bz = DIM == 3 ? g.tile[2] + 2 : 1;
+    const int bn = bx * by * bz;
+    double *s_xi = reinterpret_cast<double *>(smem_sp);   // [3][SP_MAXC]
+    R *s_g = reinterpret_cast<R *>(s_xi + 3 * SP_MAXC);    // [3][SP_MAXC]  eps~ G
+    R *s_h = s_g + 3 * SP_MAXC;                            // [SP_MAXC]     eps~ H
+    int *s_cell = reinterpret_cast<int *>(s_h + SP_MAXC);  // [SP_MAXC]     owner cell in box
+    int *s_head = s_cell + SP_MAXC;                        // [bn]
+    int *s_len = s_head + bn;                              // [bn]
+    __shared__ int s_cnt[NT3 + 1], s_start[NT3], s_warp[33];
+    const int tid = threadIdx.x;
     const int n_band = m.counts[1];
     const int cpt = g.cells_per_tile;
     for (int it = blockIdx.x; it < n_band; it += gridDim.x) {
         const int t = m.band_list[it];
         const int tx = t % g.ntile[0], ty = (t / g.ntile[0]) % g.ntile[1],
                   tz = t / (g.ntile[0] * g.ntile[1]);
-        for (int q = threadIdx.x; q < cpt; q += blockDim.x) {
-            const int c[3] = {tx * g.tile[0] + q % g.tile[0],
-                              ty * g.tile[1] + (q / g.tile[0]) % g.tile[1],
-                              DIM == 3 ? tz * g.tile[2] + q / (g.tile[0] * g.tile[1]) : 0};
+        const int o[3] = {tx * g.tile[0], ty * g.tile[1], DIM == 3 ? tz * g.tile[2] : 0};
+        // 1. bin ranges of the neighbour tiles (z, y, x order)
+        if (tid < NT3) {
+            const int ux = tx + tid % 3 - 1, uy = ty + (tid / 3) % 3 - 1,
+                      uz = tz + (DIM == 3 ? tid / 9 - 1 : 0);
+            int st = 0, cnt = 0;
+            if (ux >= 0 && uy >= 0 && uz >= 0 && ux < g.ntile[0] && uy < g.ntile[1] &&
+                uz < g.ntile[2]) {
+                const int u = ux + g.ntile[0] * (uy + g.ntile[1] * uz);
+                st = m.tile_off[u];
+                cnt = m.tile_off[u + 1] - st;
+            }
+            s_start[tid] = st;
+            s_cnt[tid + 1] = cnt;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            s_cnt[0] = 0;
+            for (int i = 1; i <= NT3; ++i) s_cnt[i] += s_cnt[i - 1];
+        }
+        __syncthreads();
+        const int total = s_cnt[NT3];
+        // 2. stage, in order, the markers whose owner cell lies in the tile
+        //    grown by one cell (their supports reach the tile)
+        int kept = 0;
+        for (int base = 0; base < total; base += SP_T) {
+            const int i = base + tid;
+            int keep = 0, p = 0, lc = 0;
+            if (i < total) {
+                int nt = 0;
+                while (s_cnt[nt + 1] <= i) ++nt;
+                p = s_start[nt] + (i - s_cnt[nt]);
+                const unsigned key = keys[p];
+                const int tu = (int)(key / (unsigned)cpt);
+                const int cin = (int)(key - (unsigned)tu * (unsigned)cpt);
+                const int cu[3] = {(tu % g.ntile[0]) * g.tile[0] + cin % g.tile[0],
+                                   ((tu / g.ntile[0]) % g.ntile[1]) * g.tile[1] +
+                                       (cin / g.tile[0]) % g.tile[1],
+                                   (tu / (g.ntile[0] * g.ntile[1])) * g.tile[2] +
+                                       cin / (g.tile[0] * g.tile[1])};
+                const int d0 = cu[0] - o[0] + 1, d1 = cu[1] - o[1] + 1,
+                          d2 = DIM == 3 ? cu[2] - o[2] + 1 : 0;
+                keep = d0 >= 0 && d0 < bx && d1 >= 0 && d1 < by && d2 >= 0 && d2 < bz;
+                lc = d0 + bx * (d1 + by * d2);
+            }
+            int tot;
+            const int pos = block_exclusive_scan(keep, s_warp, tot) + kept;
+            if (keep && pos < SP_MAXC) {
+                const int k = perm[p];
+                const double e = m.eps[k];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    s_xi[d * SP_MAXC + pos] =
+                        d < DIM ? (m.X[(long long)k * DIM + d] - g.lo[d]) * g.inv_h : 0.0;
+                    s_g[d * SP_MAXC + pos] = d < DIM ? (R)(m.G[(long long)k * DIM + d] * e) : R(0);
+                }
+                s_h[pos] = (R)(m.H[k] * e);
+                s_cell[pos] = lc;
+            }
+            kept += tot;
+        }
+        const bool overflow = kept > SP_MAXC;
+        // 3. runs of candidates per owner cell (contiguous in bin order)
+        if (!overflow) {
+            for (int q = tid; q < bn; q += SP_T) s_head[q] = -1;
+            __syncthreads();
+            for (int i = tid; i < kept; i += SP_T) {
+                const int c = s_cell[i];
+                if (i == 0 || s_cell[i - 1] != c) {
+                    int j = i + 1;
+                    while (j < kept && s_cell[j] == c) ++j;
+                    s_head[c] = i;
+                    s_len[c] = j - i;
+                }
+            }
+        }
+        __syncthreads();
+        // 4. gather per cell in the fixed order, then the forced update
+        for (int q = tid; q < cpt; q += SP_T) {
+            const int l[3] = {q % g.tile[0], (q / g.tile[0]) % g.tile[1],
+                              DIM == 3 ? q / (g.tile[0] * g.tile[1]) : 0};
+            const int c[3] = {o[0] + l[0], o[1] + l[1], o[2] + l[2]};
             if (c[0] >= g.n[0] || c[1] >= g.n[1] || (DIM == 3 && c[2] >= g.n[2])) continue;
-            double f[DIM], qh = 0.0;
+            R f[DIM], qh = R(0);
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) f[d] = 0.0;
-            const bool band = gather_markers<DIM>(g, m, keys, perm, c, [&](int k, double w) {
-                const double we = w * m.eps[k];
+            for (int d = 0; d < DIM; ++d) f[d] = R(0);
+            bool band = false;
+            if (!overflow) {
+                const int zr = DIM == 3 ? 1 : 0;
+                for (int oz = -zr; oz <= zr; ++oz)
+                    for (int oy = -1; oy <= 1; ++oy)
+                        for (int ox = -1; ox <= 1; ++ox) {
+                            const int lc = (l[0] + 1 + ox) +
+                                           bx * ((l[1] + 1 + oy) + by * (DIM == 3 ? l[2] + 1 + oz : 0));
+                            const int h0 = s_head[lc];
+                            if (h0 < 0) continue;
+                            const int h1 = h0 + s_len[lc];
+                            for (int i = h0; i < h1; ++i) {
+                                R w = R(1);
 #pragma unroll
-                for (int d = 0; d < DIM; ++d) f[d] += m.G[(long long)k * DIM + d] * we;
-                qh += m.H[k] * we;
-            });
+                                for (int d = 0; d < DIM; ++d)
+                                    w *= phi_r<R>((R)cell_offset(c[d], s_xi[d * SP_MAXC + i]));
+#pragma unroll
+                                for (int d = 0; d < DIM; ++d) f[d] += s_g[d * SP_MAXC + i] * w;
+                                qh += s_h[i] * w;
+                                band = true;
+                            }
+                        }
+            } else {
+                band = gather_markers<DIM, R>(g, m, keys, perm, c, [&](int k, R w) {
+                    const double e = m.eps[k];
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d) f[d] += (R)(m.G[(long long)k * DIM + d] * e) * w;
+                    qh += (R)(m.H[k] * e) * w;
+                });
+            }
             if (!band) continue;
             const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
-            const double rho = (double)U[j];
-            double ke0 = 0.0, ke1 = 0.0;
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                const double m0 = (double)U[(1 + d) * N + j];
-                const double m1 = m0 + f[d];
-                ke0 += m0 * m0;
-                ke1 += m1 * m1;
-                U[(1 + d) * N + j] = (T)m1;
-            }
-            const double E = (double)U[(DIM + 1) * N + j];
-            const double En = g.energy_reading == 1 ? E + qh
-                                                    : (E - 0.5 * ke0 / rho + qh) + 0.5 * ke1 / rho;
-            U[(DIM + 1) * N + j] = (T)En;
+            apply_forcing<DIM, T, R>(g, U, j, f, qh);
         }
+        __syncthreads();
     }
 }
 
@@ -419,22 +582,28 @@ spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m
 
 __global__ void __launch_bounds__(256)
 finish_kernel(int dim, int ns, const MarkerBuffers m, const double *__restrict__ dt) {
-    __shared__ double s[4][256];
+    __shared__ double s[4][8];
     double a[4] = {0, 0, 0, 0};
     for (int k = threadIdx.x; k < ns; k += 256) {
         const double e = m.eps[k];
         for (int d = 0; d < dim; ++d) a[d] += e * m.G[(long long)k * dim + d];
         a[3] += e * m.H[k];
     }
-    for (int i = 0; i < 4; ++i) s[i][threadIdx.x] = a[i];
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int i = 0; i < 4; ++i) s[i][threadIdx.x] += s[i][threadIdx.x + w];
-        __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
     }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int i = 0; i < 4; ++i) s[i][w] = a[i];
+    __syncthreads();
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 4; ++i) m.sums[i] = s[i][0];
+        for (int i = 0; i < 4; ++i) {
+            double t = 0.0;
+            for (int j = 0; j < 8; ++j) t += s[i][j];
+            m.sums[i] = t;
+        }
         m.sums[4] = *dt;
         *m.t += *dt;
         *m.steps += 1;
@@ -448,19 +617,21 @@ finish_kernel(int dim, int ns, const MarkerBuffers m, const double *__restrict__
 template <int DIM, typename T>
 __global__ void interpolate_op_kernel(const GridParams g, const T *__restrict__ field, int nc,
                                       const MarkerBuffers m, double *__restrict__ out) {
+    using R = T;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= m.ns) return;
-    double Xk[3] = {0, 0, 0};
+    double xi[3] = {0, 0, 0};
     int ck[3] = {0, 0, 0};
     for (int d = 0; d < DIM; ++d) {
-        Xk[d] = m.X[(long long)k * DIM + d];
-        ck[d] = owner_cell(Xk[d], g.lo[d], g.h);
+        const double X = m.X[(long long)k * DIM + d];
+        ck[d] = owner_cell(X, g.lo[d], g.h);
+        xi[d] = (X - g.lo[d]) * g.inv_h;
     }
     for (int c = 0; c < nc; ++c) out[(long long)k * nc + c] = 0.0;
     constexpr int NS = DIM == 3 ? 27 : 9;
     for (int l = 0; l < NS; ++l) {
         int cell[3];
-        const double w = lane_weight<DIM>(g, Xk, ck, l, cell);
+        const double w = (double)lane_weight<DIM, R>(xi, ck, l, cell);
         const long long j = cell[0] + (long long)g.n[0] * (cell[1] + (long long)g.n[1] * cell[2]);
         for (int c = 0; c < nc; ++c) out[(long long)k * nc + c] += w * (double)field[c * g.N + j];
     }
@@ -468,9 +639,10 @@ __global__ void interpolate_op_kernel(const GridParams g, const T *__restrict__ 
 
 template <int DIM, typename T>
 __global__ void __launch_bounds__(256)
-spread_op_kernel(const GridParams g, const double *__restrict__ R, int nc, const MarkerBuffers m,
+spread_op_kernel(const GridParams g, const double *__restrict__ R_, int nc, const MarkerBuffers m,
                  const unsigned *__restrict__ keys, const int *__restrict__ perm,
                  T *__restrict__ out) {
+    using R = T;
     const int n_band = m.counts[1];
     const int cpt = g.cells_per_tile;
     for (int it = blockIdx.x; it < n_band; it += gridDim.x) {
@@ -485,8 +657,8 @@ spread_op_kernel(const GridParams g, const double *__restrict__ R, int nc, const
             const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
             for (int cc = 0; cc < nc; ++cc) {
                 double acc = 0.0;
-                gather_markers<DIM>(g, m, keys, perm, c, [&](int k, double w) {
-                    acc += R[(long long)k * nc + cc] * (w * m.eps[k]);
+                gather_markers<DIM, R>(g, m, keys, perm, c, [&](int k, R w) {
+                    acc += R_[(long long)k * nc + cc] * ((double)w * m.eps[k]);
                 });
                 out[cc * g.N + j] = (T)acc;
             }
@@ -534,15 +706,16 @@ cudaError_t launch_bin(const GridParams &g, MarkerBuffers &m, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <typename T>
 static size_t interp_smem(const GridParams &g) {
     size_t bn = (size_t)(g.tile[0] + 2) * (g.tile[1] + 2) * (g.dim == 3 ? g.tile[2] + 2 : 1);
-    return bn * (g.dim + 2) * sizeof(double);
+    return bn * (g.dim + 2) * sizeof(T);
 }
 
 template <int DIM, typename T>
 static cudaError_t interp_force_t(const GridParams &g, const void *U, const MarkerBuffers &m,
                                   int grid_ctas, cudaStream_t s) {
-    const size_t smem = interp_smem(g);
+    const size_t smem = interp_smem<T>(g);
     static size_t configured = 0;
     if (smem > 48 * 1024 && configured < smem) {
         cudaError_t e = cudaFuncSetAttribute(interp_force_kernel<DIM, T>,
@@ -564,23 +737,30 @@ cudaError_t launch_interp_force(const GridParams &g, int fp_bytes, const void *U
                          : interp_force_t<2, double>(g, U, m, grid_ctas, s);
 }
 
+template <int DIM, typename T>
+static cudaError_t spread_apply_t(const GridParams &g, void *U, const MarkerBuffers &m,
+                                  int grid_ctas, cudaStream_t s) {
+    const size_t smem = spread_smem_bytes<T>(g);
+    static size_t configured = 0;
+    if (smem > 48 * 1024 && configured < smem) {
+        cudaError_t e = cudaFuncSetAttribute(spread_apply_kernel<DIM, T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    spread_apply_kernel<DIM, T><<<grid_ctas, SP_T, smem, s>>>(g, (T *)U, m, m.keys[m.sorted],
+                                                                m.perm[m.sorted]);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_spread_apply(const GridParams &g, int fp_bytes, void *U,
                                 const MarkerBuffers &m, int grid_ctas, cudaStream_t s) {
     if (m.ns <= 0) return cudaSuccess;
-    const unsigned *keys = m.keys[m.sorted];
-    const int *perm = m.perm[m.sorted];
-    if (g.dim == 3) {
-        if (fp_bytes == 4)
-            spread_apply_kernel<3, float><<<grid_ctas, 256, 0, s>>>(g, (float *)U, m, keys, perm);
-        else
-            spread_apply_kernel<3, double><<<grid_ctas, 256, 0, s>>>(g, (double *)U, m, keys, perm);
-    } else {
-        if (fp_bytes == 4)
-            spread_apply_kernel<2, float><<<grid_ctas, 256, 0, s>>>(g, (float *)U, m, keys, perm);
-        else
-            spread_apply_kernel<2, double><<<grid_ctas, 256, 0, s>>>(g, (double *)U, m, keys, perm);
-    }
-    return cudaGetLastError();
+    if (g.dim == 3)
+        return fp_bytes == 4 ? spread_apply_t<3, float>(g, U, m, grid_ctas, s)
+                             : spread_apply_t<3, double>(g, U, m, grid_ctas, s);
+    return fp_bytes == 4 ? spread_apply_t<2, float>(g, U, m, grid_ctas, s)
+                         : spread_apply_t<2, double>(g, U, m, grid_ctas, s);
 }
 
 cudaError_t launch_finish(const GridParams &g, const MarkerBuffers &m, const double *dt,

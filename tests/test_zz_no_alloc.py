@@ -63,7 +63,7 @@ def test_noalloc_rejects_oversized_grids():
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
     L = ibm.lib()
-    g = C.small_grid(3, (1024, 512, 72), h=0.1, fp_bytes=4)   # 73728 blocks of 8^3
+    g = C.small_grid(3, (8192, 4096, 32), h=0.1, fp_bytes=4)   # 131072 column blocks
     desc = ibm.make_desc(g)
     st = L.ibm_rhs_dt_noalloc(ctypes.byref(desc), ctypes.c_void_p(256), ctypes.c_void_p(256),
                               ctypes.c_void_p(256), None)
