@@ -19,6 +19,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 UNITS = ["flux.cu", "flux_zm.cu", "markers.cu", "quadrature.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
+# extra nvcc flags (e.g. -DIBM_ZM_MIN_BLOCKS=2) for build variants
+EXTRA = os.environ.get("IBM_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:
@@ -51,7 +53,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(unit):
         obj = os.path.join(objdir, unit.replace(".cu", ".o"))
-        cmd = [cc] + ARCH + FLAGS + ["-c", os.path.join(SRC, unit), "-o", obj]
+        cmd = [cc] + ARCH + FLAGS + EXTRA + ["-c", os.path.join(SRC, unit), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s" % (unit, r.stderr))

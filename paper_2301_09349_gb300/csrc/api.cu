@@ -175,6 +175,9 @@ void layout(ibm_grid *g, const ibm_grid_desc &d, int cap, char *base, size_t *to
     m.Ub = c.take<double>((size_t)cap * dim);
     m.Tw = c.take<double>(cap);
     m.eps = c.take<double>(cap);
+    m.cell = c.take<int>((size_t)cap * 3);
+    m.frac_d = c.take<double>((size_t)cap * 3);
+    m.frac_f = c.take<float>((size_t)cap * 3);
     m.rhoL = c.take<double>(cap);
     m.G = c.take<double>((size_t)cap * dim);
     m.H = c.take<double>(cap);

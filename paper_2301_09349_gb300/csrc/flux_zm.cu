@@ -60,29 +60,122 @@ __device__ __forceinline__ float vl(float a, float b) {
     return ab > 0.0f ? __fdividef(2.0f * ab, a + b) : 0.0f;
 }
 
-// Numerical flux through the face between ring cells a and b (normal axis
-// D).  am / bp are the next cells outward along the normal; t1* and t2* are
-// the neighbours of a and b along the two tangential axes E1 < E2.
-template <int D>
-__device__ __forceinline__ void face(const FC &c, const float *__restrict__ R, int am, int a, int b,
-                                     int bp, int t1ap, int t1am, int t1bp, int t1bm, int t2ap,
-                                     int t2am, int t2bp, int t2bm, float (&F)[NC]) {
-    constexpr int E1 = D == 0 ? 1 : 0;
-    constexpr int E2 = D == 2 ? 1 : 2;
-    float wl[NC], wr[NC];
+// ---- packed pairs: the x-face (.x) and the y-face (.y) of one thread ------
+// Both faces run the same arithmetic once their velocity components are
+// ordered (normal, tangential 1, tangential 2): the x-face takes (u, v, w),
+// the y-face (v, u, w).  Each pair operation is one packed FP32x2
+// instruction on sm_100-class GPUs.
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sp(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 rcp2(float2 a) {
+    return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y));
+}
+__device__ __forceinline__ float2 rsqrt2(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+__device__ __forceinline__ float2 abs2(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ float2 max2(float2 a, float2 b) {
+    return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y));
+}
+__device__ __forceinline__ float2 vl2(float2 a, float2 b) {
+    const float2 ab = a * b;
+    const float2 q = (ab + ab) * rcp2(a + b);
+    return make_float2(ab.x > 0.0f ? q.x : 0.0f, ab.y > 0.0f ? q.y : 0.0f);
+}
+
+// x-face between ring cells ax and ax+1 and y-face between ay and ay+PX of
+// the same plane; up / dn move to the planes above and below.  Outputs in
+// (rho, rho u, rho v, rho w, rho E) order.
+__device__ __forceinline__ void face_xy(const FC &c, const float *__restrict__ R, int ax, int ay,
+                                        int up, int dn, float (&Fx)[NC], float (&Fy)[NC]) {
+    // field of (rho, normal, tangential 1, tangential 2, p) for each face
+    constexpr int fx[NC] = {0, 1, 2, 3, 4};
+    constexpr int fy[NC] = {0, 2, 1, 3, 4};
+    float2 wl[NC], wr[NC];
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
-        const float *w = R + m * PP;
-        const float x0 = w[am], x1 = w[a], x2 = w[b], x3 = w[bp];
-        const float d0 = x1 - x0, d1 = x2 - x1, d2 = x3 - x2;
-        wl[m] = x1 + 0.5f * vl(d0, d1);
-        wr[m] = x2 - 0.5f * vl(d1, d2);
+        const float *X = R + fx[m] * PP;
+        const float *Y = R + fy[m] * PP;
+        const float2 x0 = make_float2(X[ax - 1], Y[ay - PX]);
+        const float2 x1 = make_float2(X[ax], Y[ay]);
+        const float2 x2 = make_float2(X[ax + 1], Y[ay + PX]);
+        const float2 x3 = make_float2(X[ax + 2], Y[ay + 2 * PX]);
+        const float2 d0 = x1 - x0, d1 = x2 - x1, d2 = x3 - x2;
+        wl[m] = fma2(sp(0.5f), vl2(d0, d1), x1);
+        wr[m] = fma2(sp(-0.5f), vl2(d1, d2), x2);
     }
+    const float2 keL = fma2(wl[1], wl[1], fma2(wl[2], wl[2], wl[3] * wl[3]));
+    const float2 keR = fma2(wr[1], wr[1], fma2(wr[2], wr[2], wr[3] * wr[3]));
+    const float2 EL = fma2(wl[4], sp(c.inv_gm1), sp(0.5f) * wl[0] * keL);
+    const float2 ER = fma2(wr[4], sp(c.inv_gm1), sp(0.5f) * wr[0] * keR);
+    const float2 unL = wl[1], unR = wr[1];
+    const float2 c2L = sp(c.gamma) * wl[4] * rcp2(wl[0]);
+    const float2 c2R = sp(c.gamma) * wr[4] * rcp2(wr[0]);
+    const float2 sL = fma2(c2L, rsqrt2(c2L), abs2(unL));
+    const float2 sR = fma2(c2R, rsqrt2(c2R), abs2(unR));
+    const float2 hs = sp(-0.5f) * max2(sL, sR);      // -smax/2
+    const float2 mL1 = wl[0] * unL, mR1 = wr[0] * unR;
+    const float2 mL2 = wl[0] * wl[2], mR2 = wr[0] * wr[2];
+    const float2 mL3 = wl[0] * wl[3], mR3 = wr[0] * wr[3];
+    float2 F0 = fma2(hs, wr[0] - wl[0], sp(0.5f) * (mL1 + mR1));
+    float2 Fn = fma2(hs, mR1 - mL1, sp(0.5f) * (fma2(mL1, unL, wl[4]) + fma2(mR1, unR, wr[4])));
+    float2 F1 = fma2(hs, mR2 - mL2, sp(0.5f) * fma2(mL2, unL, mR2 * unR));
+    float2 F2 = fma2(hs, mR3 - mL3, sp(0.5f) * fma2(mL3, unL, mR3 * unR));
+    float2 FE = fma2(hs, ER - EL, sp(0.5f) * fma2(EL + wl[4], unL, (ER + wr[4]) * unR));
+
+    if (c.viscous) {
+        const float *T = R + 5 * PP;
+        const float2 Ta = make_float2(T[ax], T[ay]), Tb = make_float2(T[ax + 1], T[ay + PX]);
+        const float2 Tf = sp(0.5f) * (Ta + Tb);
+        const float2 mu = sp(c.mu_inf * c.onepS) * Tf * (Tf * rsqrt2(Tf)) * rcp2(Tf + sp(c.S));
+        const float2 lam = mu * sp(c.lam_fac);
+        const float *Xn = R + PP, *Yn = R + 2 * PP;       // normal velocity: u / v
+        const float *X1 = R + 2 * PP, *Y1 = R + PP;       // tangential 1: v / u
+        const float *W3 = R + 3 * PP;                     // tangential 2: w
+        const int bx = ax + 1, by = ay + PX;
+        const float2 ih = sp(c.inv_h), qh = sp(c.qinv_h);
+        const float2 dn_n = (make_float2(Xn[bx], Yn[by]) - make_float2(Xn[ax], Yn[ay])) * ih;
+        const float2 dn_1 = (make_float2(X1[bx], Y1[by]) - make_float2(X1[ax], Y1[ay])) * ih;
+        const float2 dn_2 = (make_float2(W3[bx], W3[by]) - make_float2(W3[ax], W3[ay])) * ih;
+        const float2 dn_T = (Tb - Ta) * ih;
+        // along tangential 1 (y for the x-face, x for the y-face)
+        const float2 d1_n = ((make_float2(Xn[ax + PX], Yn[ay + 1]) - make_float2(Xn[ax - PX], Yn[ay - 1])) +
+                             (make_float2(Xn[bx + PX], Yn[by + 1]) - make_float2(Xn[bx - PX], Yn[by - 1]))) * qh;
+        const float2 d1_1 = ((make_float2(X1[ax + PX], Y1[ay + 1]) - make_float2(X1[ax - PX], Y1[ay - 1])) +
+                             (make_float2(X1[bx + PX], Y1[by + 1]) - make_float2(X1[bx - PX], Y1[by - 1]))) * qh;
+        // along z
+        const float2 d2_n = ((make_float2(Xn[ax + up], Yn[ay + up]) - make_float2(Xn[ax + dn], Yn[ay + dn])) +
+                             (make_float2(Xn[bx + up], Yn[by + up]) - make_float2(Xn[bx + dn], Yn[by + dn]))) * qh;
+        const float2 d2_2 = ((make_float2(W3[ax + up], W3[ay + up]) - make_float2(W3[ax + dn], W3[ay + dn])) +
+                             (make_float2(W3[bx + up], W3[by + up]) - make_float2(W3[bx + dn], W3[by + dn]))) * qh;
+        const float2 div = dn_n + d1_1 + d2_2;
+        const float2 tNN = mu * fma2(sp(2.0f), dn_n, sp(-2.0f / 3.0f) * div);
+        const float2 tN1 = mu * (d1_n + dn_1);
+        const float2 tN2 = mu * (d2_n + dn_2);
+        const float2 ufn = sp(0.5f) * (make_float2(Xn[ax], Yn[ay]) + make_float2(Xn[bx], Yn[by]));
+        const float2 uf1 = sp(0.5f) * (make_float2(X1[ax], Y1[ay]) + make_float2(X1[bx], Y1[by]));
+        const float2 uf2 = sp(0.5f) * (make_float2(W3[ax], W3[ay]) + make_float2(W3[bx], W3[by]));
+        Fn = Fn - tNN;
+        F1 = F1 - tN1;
+        F2 = F2 - tN2;
+        FE = FE - fma2(ufn, tNN, fma2(uf1, tN1, fma2(uf2, tN2, lam * dn_T)));
+    }
+    Fx[0] = F0.x; Fx[1] = Fn.x; Fx[2] = F1.x; Fx[3] = F2.x; Fx[4] = FE.x;
+    Fy[0] = F0.y; Fy[1] = F1.y; Fy[2] = Fn.y; Fy[3] = F2.y; Fy[4] = FE.y;
+}
+
+// z-face between ring cells a (plane z) and b (plane z+1) of one column from
+// given reconstructed states; tangential neighbours are a/b +-1 and +-PX.
+__device__ __forceinline__ void face_z(const FC &c, const float *__restrict__ R, int a, int b,
+                                       const float (&wl)[NC], const float (&wr)[NC], float (&F)[NC]) {
     const float keL = wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3];
     const float keR = wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
     const float EL = wl[4] * c.inv_gm1 + 0.5f * wl[0] * keL;
     const float ER = wr[4] * c.inv_gm1 + 0.5f * wr[0] * keR;
-    const float unL = wl[1 + D], unR = wr[1 + D];
+    const float unL = wl[3], unR = wr[3];
     const float cL2 = __fdividef(c.gamma * wl[4], wl[0]);
     const float cR2 = __fdividef(c.gamma * wr[4], wr[0]);
     const float sL = fabsf(unL) + cL2 * rsqrtf(cL2);
@@ -92,40 +185,48 @@ __device__ __forceinline__ void face(const FC &c, const float *__restrict__ R, i
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
         const float mL = wl[0] * wl[1 + m], mR = wr[0] * wr[1 + m];
-        const float fL = mL * unL + (m == D ? wl[4] : 0.0f);
-        const float fR = mR * unR + (m == D ? wr[4] : 0.0f);
+        const float fL = mL * unL + (m == 2 ? wl[4] : 0.0f);
+        const float fR = mR * unR + (m == 2 ? wr[4] : 0.0f);
         F[1 + m] = 0.5f * (fL + fR) - 0.5f * smax * (mR - mL);
     }
     F[4] = 0.5f * ((EL + wl[4]) * unL + (ER + wr[4]) * unR) - 0.5f * smax * (ER - EL);
-
     if (!c.viscous) return;
     const float *Tc = R + 5 * PP;
     const float Ta = Tc[a], Tb = Tc[b];
     const float Tf = 0.5f * (Ta + Tb);
     const float mu = __fdividef(c.mu_inf * Tf * (Tf * rsqrtf(Tf)) * c.onepS, Tf + c.S);
     const float lam = mu * c.lam_fac;
-    const float *uD = R + (1 + D) * PP;
-    const float *u1 = R + (1 + E1) * PP;
-    const float *u2 = R + (1 + E2) * PP;
-    const float dn_uD = (uD[b] - uD[a]) * c.inv_h;
-    const float dn_u1 = (u1[b] - u1[a]) * c.inv_h;
-    const float dn_u2 = (u2[b] - u2[a]) * c.inv_h;
+    const float *uz = R + 3 * PP, *ux = R + PP, *uy = R + 2 * PP;
+    const float dn_w = (uz[b] - uz[a]) * c.inv_h;
+    const float dn_u = (ux[b] - ux[a]) * c.inv_h;
+    const float dn_v = (uy[b] - uy[a]) * c.inv_h;
     const float dn_T = (Tb - Ta) * c.inv_h;
-    const float d1_uD = (uD[t1ap] - uD[t1am] + uD[t1bp] - uD[t1bm]) * c.qinv_h;
-    const float d2_uD = (uD[t2ap] - uD[t2am] + uD[t2bp] - uD[t2bm]) * c.qinv_h;
-    const float d1_u1 = (u1[t1ap] - u1[t1am] + u1[t1bp] - u1[t1bm]) * c.qinv_h;
-    const float d2_u2 = (u2[t2ap] - u2[t2am] + u2[t2bp] - u2[t2bm]) * c.qinv_h;
-    const float div = dn_uD + d1_u1 + d2_u2;
-    const float tDD = mu * (2.0f * dn_uD - (2.0f / 3.0f) * div);
-    const float tD1 = mu * (d1_uD + dn_u1);
-    const float tD2 = mu * (d2_uD + dn_u2);
-    const float ufD = 0.5f * (uD[a] + uD[b]);
-    const float uf1 = 0.5f * (u1[a] + u1[b]);
-    const float uf2 = 0.5f * (u2[a] + u2[b]);
-    F[1 + D] -= tDD;
-    F[1 + E1] -= tD1;
-    F[1 + E2] -= tD2;
-    F[4] -= ufD * tDD + uf1 * tD1 + uf2 * tD2 + lam * dn_T;
+    const float dx_w = (uz[a + 1] - uz[a - 1] + uz[b + 1] - uz[b - 1]) * c.qinv_h;
+    const float dy_w = (uz[a + PX] - uz[a - PX] + uz[b + PX] - uz[b - PX]) * c.qinv_h;
+    const float dx_u = (ux[a + 1] - ux[a - 1] + ux[b + 1] - ux[b - 1]) * c.qinv_h;
+    const float dy_v = (uy[a + PX] - uy[a - PX] + uy[b + PX] - uy[b - PX]) * c.qinv_h;
+    const float div = dn_w + dx_u + dy_v;
+    const float tzz = mu * (2.0f * dn_w - (2.0f / 3.0f) * div);
+    const float tzx = mu * (dx_w + dn_u);
+    const float tzy = mu * (dy_w + dn_v);
+    const float ufw = 0.5f * (uz[a] + uz[b]);
+    const float ufu = 0.5f * (ux[a] + ux[b]);
+    const float ufv = 0.5f * (uy[a] + uy[b]);
+    F[3] -= tzz;
+    F[1] -= tzx;
+    F[2] -= tzy;
+    F[4] -= ufw * tzz + ufu * tzx + ufv * tzy + lam * dn_T;
+}
+
+// limited slopes of the five primitives across three cells of a column
+__device__ __forceinline__ void column_slope(const float *__restrict__ R, int lo, int mid, int hi,
+                                             float (&sig)[NC]) {
+#pragma unroll
+    for (int m = 0; m < NC; ++m) {
+        const float *w = R + m * PP;
+        const float a = w[mid] - w[lo], b = w[hi] - w[mid];
+        sig[m] = vl(a, b);
+    }
 }
 
 // Load plane gz (ghosts through the boundary conditions), build U1 on the
@@ -193,8 +294,12 @@ __device__ __forceinline__ double warp_max_d(double v) {
 }
 
 // MODE 0: L only.  MODE 1: stage 1 (L and the step size).  MODE 2: stage 2.
+#ifndef IBM_ZM_MIN_BLOCKS
+#define IBM_ZM_MIN_BLOCKS 3
+#endif
+
 template <int MODE>
-__global__ void __launch_bounds__(NTH, 2)
+__global__ void __launch_bounds__(NTH, IBM_ZM_MIN_BLOCKS)
 zmarch_kernel(const GridParams g, const FC c, int zc, const float *__restrict__ U,
               const float *__restrict__ Lp, float *__restrict__ out,
               double *__restrict__ blockmax, unsigned *__restrict__ counter,
@@ -219,59 +324,67 @@ zmarch_kernel(const GridParams g, const FC c, int zc, const float *__restrict__ 
     __syncthreads();
 
     const int cxy = (lx + 2) + PX * (ly + 2);   // own column inside a plane
-    float Fz[NC];
+    // z-face below the first plane (z0 - 1/2) from the slopes of cells z0-1, z0
+    float Fz[NC], sig0[NC];
     {
-        const int sa = slot_of(z0 - 1), sb = slot_of(z0), sam = slot_of(z0 - 2), sbp = slot_of(z0 + 1);
-        face<2>(c, ring, sam + cxy, sa + cxy, sb + cxy, sbp + cxy, sa + cxy + 1, sa + cxy - 1,
-                sb + cxy + 1, sb + cxy - 1, sa + cxy + PX, sa + cxy - PX, sb + cxy + PX,
-                sb + cxy - PX, Fz);
+        const int sam = slot_of(z0 - 2), sa = slot_of(z0 - 1), sb = slot_of(z0), sbp = slot_of(z0 + 1);
+        float sgA[NC];
+        column_slope(ring, sam + cxy, sa + cxy, sb + cxy, sgA);
+        column_slope(ring, sa + cxy, sb + cxy, sbp + cxy, sig0);
+        float wl[NC], wr[NC];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            wl[m] = ring[sa + m * PP + cxy] + 0.5f * sgA[m];
+            wr[m] = ring[sb + m * PP + cxy] - 0.5f * sig0[m];
+        }
+        face_z(c, ring, sa + cxy, sb + cxy, wl, wr, Fz);
     }
     __syncthreads();
 
-    double smax = 0.0;
+    float smaxf = 0.0f;
     int bad = 0;
     for (int z = z0; z < z1; ++z) {
         load_plane<MODE>(g, c, U, Lp, dt, ring + slot_of(z + 2), ox, oy, z + 2, xyint);
         __syncthreads();
         const int sm1 = slot_of(z - 1), s0 = slot_of(z), s1 = slot_of(z + 1), s2 = slot_of(z + 2);
+        (void)sm1;
         const int up = s1 - s0, dn = sm1 - s0;
-        // x-faces of row ly: face lx lies between cells lx-1 and lx
+        // x-face lx of row ly (between cells lx-1 and lx) paired with y-face
+        // row ly (between cell rows ly-1 and ly) of column lx
         {
-            float F[NC];
-            const int a = s0 + (lx + 1) + PX * (ly + 2), b = a + 1;
-            face<0>(c, ring, a - 1, a, b, b + 1, a + PX, a - PX, b + PX, b - PX, a + up, a + dn,
-                    b + up, b + dn, F);
+            float Fx[NC], Fy[NC];
+            face_xy(c, ring, s0 + (lx + 1) + PX * (ly + 2), s0 + (lx + 2) + PX * (ly + 1), up, dn,
+                    Fx, Fy);
 #pragma unroll
-            for (int m = 0; m < NC; ++m) FXb[(m * TY + ly) * FXW + lx] = F[m];
-            if (ly == 0 && lx < TY) {   // the last face of each row
-                const int a2 = s0 + (TX + 1) + PX * (lx + 2), b2 = a2 + 1;
-                face<0>(c, ring, a2 - 1, a2, b2, b2 + 1, a2 + PX, a2 - PX, b2 + PX, b2 - PX,
-                        a2 + up, a2 + dn, b2 + up, b2 + dn, F);
+            for (int m = 0; m < NC; ++m) {
+                FXb[(m * TY + ly) * FXW + lx] = Fx[m];
+                FYb[(m * (TY + 1) + ly) * TX + lx] = Fy[m];
+            }
+            if (ly == 1) {   // the last x-face of each row and the last y-face row
+                const int r = lx < TY ? lx : 0;
+                face_xy(c, ring, s0 + (TX + 1) + PX * (r + 2), s0 + (lx + 2) + PX * (TY + 1), up, dn,
+                        Fx, Fy);
 #pragma unroll
-                for (int m = 0; m < NC; ++m) FXb[(m * TY + lx) * FXW + TX] = F[m];
+                for (int m = 0; m < NC; ++m) {
+                    if (lx < TY) FXb[(m * TY + lx) * FXW + TX] = Fx[m];
+                    FYb[(m * (TY + 1) + TY) * TX + lx] = Fy[m];
+                }
             }
         }
-        // y-faces: face row ly lies between cell rows ly-1 and ly
-        {
-            float F[NC];
-            const int a = s0 + (lx + 2) + PX * (ly + 1), b = a + PX;
-            face<1>(c, ring, a - PX, a, b, b + PX, a + 1, a - 1, b + 1, b - 1, a + up, a + dn,
-                    b + up, b + dn, F);
-#pragma unroll
-            for (int m = 0; m < NC; ++m) FYb[(m * (TY + 1) + ly) * TX + lx] = F[m];
-            if (ly == 1) {   // the last face row
-                const int a2 = s0 + (lx + 2) + PX * (TY + 1), b2 = a2 + PX;
-                face<1>(c, ring, a2 - PX, a2, b2, b2 + PX, a2 + 1, a2 - 1, b2 + 1, b2 - 1,
-                        a2 + up, a2 + dn, b2 + up, b2 + dn, F);
-#pragma unroll
-                for (int m = 0; m < NC; ++m) FYb[(m * (TY + 1) + TY) * TX + lx] = F[m];
-            }
-        }
-        // z-face above the column (between planes z and z+1)
+        // z-face above the column (between planes z and z+1); the slope of
+        // cell z is carried from the previous plane
         float Fh[NC];
-        face<2>(c, ring, sm1 + cxy, s0 + cxy, s1 + cxy, s2 + cxy, s0 + cxy + 1, s0 + cxy - 1,
-                s1 + cxy + 1, s1 + cxy - 1, s0 + cxy + PX, s0 + cxy - PX, s1 + cxy + PX,
-                s1 + cxy - PX, Fh);
+        {
+            float sig1[NC], wl[NC], wr[NC];
+            column_slope(ring, s0 + cxy, s1 + cxy, s2 + cxy, sig1);
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                wl[m] = ring[s0 + m * PP + cxy] + 0.5f * sig0[m];
+                wr[m] = ring[s1 + m * PP + cxy] - 0.5f * sig1[m];
+                sig0[m] = sig1[m];
+            }
+            face_z(c, ring, s0 + cxy, s1 + cxy, wl, wr, Fh);
+        }
         __syncthreads();
 
         float acc[NC];
@@ -307,13 +420,13 @@ zmarch_kernel(const GridParams g, const FC c, int zc, const float *__restrict__ 
                 const float s = (fabsf(P[PP + cxy]) + fabsf(P[2 * PP + cxy]) + fabsf(P[3 * PP + cxy]) +
                                  3.0f * snd) * c.inv_h + 6.0f * nu * c.inv_h * c.inv_h;
                 if (!(rho > 0.0f && p > 0.0f && s <= FLT_MAX)) bad = 1;
-                else smax = fmax(smax, (double)s);
+                else smaxf = fmaxf(smaxf, s);
             }
         }
     }
 
     if (MODE == 1) {
-        smax = warp_max_d(smax);
+        const double smax = warp_max_d((double)smaxf);
         bad = __syncthreads_or(bad);
         if ((tid & 31) == 0) s_red[tid >> 5] = smax;
         __syncthreads();
@@ -378,6 +491,9 @@ static cudaError_t zm_launch(const GridParams &g, const void *U, const void *Lp,
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(zmarch_kernel<MODE>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(zmarch_kernel<MODE>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         configured = true;
     }

@@ -40,6 +40,9 @@ struct MarkerBuffers {
     double *Ub0, *Ub;        // ns*dim body velocity (prescribed part, current)
     double *Tw;              // ns wall temperatures
     double *eps;             // ns quadrature weights eps~
+    int *cell;               // ns*3 owner cells floor((X - lo)/h) (bins kernel)
+    double *frac_d;          // ns*3 offsets (X - lo)/h - cell, in [0, 1)
+    float *frac_f;           // the same offsets in single precision
     double *rhoL, *G, *H;    // last forcing: rho_L, dt*F (ns*dim), dt*Q
     unsigned *keys[2];       // radix-sort ping-pong
     int *perm[2];

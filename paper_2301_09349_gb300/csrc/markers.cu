@@ -62,20 +62,32 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *s_warp, int &tot
 
 __global__ void __launch_bounds__(SORT_T)
 bin_sort_kernel(const GridParams g, int ns, const double *__restrict__ X, unsigned *keys0,
-                int *vals0, unsigned *keys1, int *vals1, int passes, int *err) {
+                int *vals0, unsigned *keys1, int *vals1, int passes, int *err,
+                int *__restrict__ cell_out, double *__restrict__ frac_d, float *__restrict__ frac_f) {
     __shared__ int hist[RADIX * HSTRIDE];
     __shared__ int s_warp[33];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     int bad = 0;
     for (int k = tid; k < ns; k += SORT_T) {
         int c[3] = {0, 0, 0};
-        for (int d = 0; d < g.dim; ++d) {
-            int cd = owner_cell(X[(long long)k * g.dim + d], g.lo[d], g.h);
-            if (!(cd >= 2 && cd <= g.n[d] - 3)) {
-                bad = 1;
-                cd = cd < 0 ? 0 : (cd >= g.n[d] ? g.n[d] - 1 : cd);
+        for (int d = 0; d < 3; ++d) {
+            double fr = 0.0;
+            if (d < g.dim) {
+                // xi = (X - lo)/h with IEEE subtraction and division; owner cell
+                // floor(xi) and the offset xi - cell feed every weight evaluation
+                const double xi = __ddiv_rn(__dsub_rn(X[(long long)k * g.dim + d], g.lo[d]), g.h);
+                int cd = (int)floor(xi);
+                fr = xi - (double)cd;
+                if (!(cd >= 2 && cd <= g.n[d] - 3)) {
+                    bad = 1;
+                    cd = cd < 0 ? 0 : (cd >= g.n[d] ? g.n[d] - 1 : cd);
+                    fr = 0.5;
+                }
+                c[d] = cd;
             }
-            c[d] = cd;
+            cell_out[(long long)k * 3 + d] = c[d];
+            frac_d[(long long)k * 3 + d] = fr;
+            frac_f[(long long)k * 3 + d] = (float)fr;
         }
         keys0[k] = cell_key(g, c[0], c[1], c[2]);
         vals0[k] = k;
@@ -241,10 +253,20 @@ template <> __device__ __forceinline__ float phi_r<float>(float r) {
 }
 template <> __device__ __forceinline__ double phi_r<double>(double r) { return phi_d(r); }
 
-// Offset in cells from a marker coordinate xi = (X - lo)/h to the centre of
-// cell c on one axis.  Every kernel evaluates the weights through this one
-// expression, so interpolation and spreading use identical weights.
-__device__ __forceinline__ double cell_offset(int c, double xi) { return ((double)c + 0.5) - xi; }
+// Offset in cells from marker k to the centre of the cell o cells away from
+// its owner cell on one axis: (o + 1/2) - frac, frac = (X - lo)/h - owner.
+// Every kernel evaluates the weights through this one expression (in the
+// field precision), so interpolation and spreading use identical weights.
+template <typename R> __device__ __forceinline__ R marker_frac(const MarkerBuffers &m, int k, int d);
+template <> __device__ __forceinline__ float marker_frac<float>(const MarkerBuffers &m, int k, int d) {
+    return m.frac_f[(long long)k * 3 + d];
+}
+template <> __device__ __forceinline__ double marker_frac<double>(const MarkerBuffers &m, int k, int d) {
+    return m.frac_d[(long long)k * 3 + d];
+}
+template <typename R> __device__ __forceinline__ R cell_offset(int o, R frac) {
+    return ((R)o + R(0.5)) - frac;
+}
 
 template <typename R>
 __device__ __forceinline__ R warp_sum_r(R v) {
@@ -259,13 +281,13 @@ template <> __device__ __forceinline__ double rdiv<double>(double a, double b) {
 
 // Phi_k(j) for the support cell `l` of 3^DIM (offsets in z, y, x order)
 template <int DIM, typename R>
-__device__ __forceinline__ R lane_weight(const double *xi, const int *ck, int l, int *cell) {
+__device__ __forceinline__ R lane_weight(const R *fr, const int *ck, int l, int *cell) {
     const int o[3] = {l % 3 - 1, (l / 3) % 3 - 1, DIM == 3 ? l / 9 - 1 : 0};
     R w = R(1);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         cell[d] = ck[d] + o[d];
-        w *= phi_r<R>((R)cell_offset(cell[d], xi[d]));
+        w *= phi_r<R>(cell_offset<R>(o[d], fr[d]));
     }
     if (DIM == 2) cell[2] = 0;
     return w;
@@ -321,20 +343,19 @@ interp_force_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuf
         const int p0 = m.tile_off[t], p1 = m.tile_off[t + 1];
         for (int p = p0 + warp; p < p1; p += nwarps) {
             const int k = perm[p];
-            double xi[3] = {0, 0, 0};
+            R fr[3] = {R(0), R(0), R(0)};
             int ck[3] = {0, 0, 0};
 #pragma unroll
             for (int d = 0; d < DIM; ++d) {
-                const double X = m.X[(long long)k * DIM + d];
-                ck[d] = owner_cell(X, g.lo[d], g.h);
-                xi[d] = (X - g.lo[d]) * g.inv_h;
+                ck[d] = m.cell[(long long)k * 3 + d];
+                fr[d] = marker_frac<R>(m, k, d);
             }
             R acc[NF];
 #pragma unroll
             for (int f = 0; f < NF; ++f) acc[f] = R(0);
             if (lane < NS) {
                 int cell[3];
-                const R w = lane_weight<DIM, R>(xi, ck, lane, cell);
+                const R w = lane_weight<DIM, R>(fr, ck, lane, cell);
                 const int li = (cell[0] - ox) + bx * ((cell[1] - oy) + by * (cell[2] - oz));
 #pragma unroll
                 for (int f = 0; f < NF; ++f) acc[f] = w * sS[f * bn + li];
@@ -383,14 +404,12 @@ __device__ __forceinline__ bool gather_markers(const GridParams &g, const Marker
                     else hi = mid;
                 }
                 const int end = m.tile_off[tc + 1];
+                const int oo[3] = {-ox, -oy, -oz};   // cell c seen from owner cell (x, y, z)
                 for (int p = lo; p < end && keys[p] == key; ++p) {
                     const int k = perm[p];
                     R w = R(1);
 #pragma unroll
-                    for (int d = 0; d < DIM; ++d) {
-                        const double xi = (m.X[(long long)k * DIM + d] - g.lo[d]) * g.inv_h;
-                        w *= phi_r<R>((R)cell_offset(c[d], xi));
-                    }
+                    for (int d = 0; d < DIM; ++d) w *= phi_r<R>(cell_offset<R>(oo[d], marker_frac<R>(m, k, d)));
                     visit(k, w);
                     any = true;
                 }
@@ -404,7 +423,7 @@ constexpr int SP_MAXC = 1024;   // staged candidates per band tile
 template <typename R>
 size_t spread_smem_bytes(const GridParams &g) {
     const size_t bn = (size_t)(g.tile[0] + 2) * (g.tile[1] + 2) * (g.dim == 3 ? g.tile[2] + 2 : 1);
-    return SP_MAXC * (3 * sizeof(double) + 4 * sizeof(R) + sizeof(int)) + 2 * bn * sizeof(int);
+    return SP_MAXC * (7 * sizeof(R) + sizeof(int)) + 2 * bn * sizeof(int);
 }
 
 // Forced update of one band cell (App. B, Eqs. u_centralF2 and e_centralF2;
@@ -438,8 +457,8 @@ spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m
     extern __shared__ __align__(16) unsigned char smem_sp[];
     const int bx = g.tile[0] + 2, by = g.tile[1] + 2, bz = DIM == 3 ? g.tile[2] + 2 : 1;
     const int bn = bx * by * bz;
-    double *s_xi = reinterpret_cast<double *>(smem_sp);   // [3][SP_MAXC]
-    R *s_g = reinterpret_cast<R *>(s_xi + 3 * SP_MAXC);    // [3][SP_MAXC]  eps~ G
+    R *s_fr = reinterpret_cast<R *>(smem_sp);              // [3][SP_MAXC]  marker offsets
+    R *s_g = s_fr + 3 * SP_MAXC;                           // [3][SP_MAXC]  eps~ G
     R *s_h = s_g + 3 * SP_MAXC;                            // [SP_MAXC]     eps~ H
     int *s_cell = reinterpret_cast<int *>(s_h + SP_MAXC);  // [SP_MAXC]     owner cell in box
     int *s_head = s_cell + SP_MAXC;                        // [bn]
@@ -504,8 +523,7 @@ spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m
                 const double e = m.eps[k];
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    s_xi[d * SP_MAXC + pos] =
-                        d < DIM ? (m.X[(long long)k * DIM + d] - g.lo[d]) * g.inv_h : 0.0;
+                    s_fr[d * SP_MAXC + pos] = marker_frac<R>(m, k, d);
                     s_g[d * SP_MAXC + pos] = d < DIM ? (R)(m.G[(long long)k * DIM + d] * e) : R(0);
                 }
                 s_h[pos] = (R)(m.H[k] * e);
@@ -549,11 +567,12 @@ spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m
                             const int h0 = s_head[lc];
                             if (h0 < 0) continue;
                             const int h1 = h0 + s_len[lc];
+                            const int oo[3] = {-ox, -oy, -oz};   // this cell seen from the owner cell
                             for (int i = h0; i < h1; ++i) {
                                 R w = R(1);
 #pragma unroll
                                 for (int d = 0; d < DIM; ++d)
-                                    w *= phi_r<R>((R)cell_offset(c[d], s_xi[d * SP_MAXC + i]));
+                                    w *= phi_r<R>(cell_offset<R>(oo[d], s_fr[d * SP_MAXC + i]));
 #pragma unroll
                                 for (int d = 0; d < DIM; ++d) f[d] += s_g[d * SP_MAXC + i] * w;
                                 qh += s_h[i] * w;
@@ -620,18 +639,17 @@ __global__ void interpolate_op_kernel(const GridParams g, const T *__restrict__ 
     using R = T;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= m.ns) return;
-    double xi[3] = {0, 0, 0};
+    R fr[3] = {R(0), R(0), R(0)};
     int ck[3] = {0, 0, 0};
     for (int d = 0; d < DIM; ++d) {
-        const double X = m.X[(long long)k * DIM + d];
-        ck[d] = owner_cell(X, g.lo[d], g.h);
-        xi[d] = (X - g.lo[d]) * g.inv_h;
+        ck[d] = m.cell[(long long)k * 3 + d];
+        fr[d] = marker_frac<R>(m, k, d);
     }
     for (int c = 0; c < nc; ++c) out[(long long)k * nc + c] = 0.0;
     constexpr int NS = DIM == 3 ? 27 : 9;
     for (int l = 0; l < NS; ++l) {
         int cell[3];
-        const double w = (double)lane_weight<DIM, R>(xi, ck, l, cell);
+        const double w = (double)lane_weight<DIM, R>(fr, ck, l, cell);
         const long long j = cell[0] + (long long)g.n[0] * (cell[1] + (long long)g.n[1] * cell[2]);
         for (int c = 0; c < nc; ++c) out[(long long)k * nc + c] += w * (double)field[c * g.N + j];
     }
@@ -693,7 +711,7 @@ cudaError_t launch_bin(const GridParams &g, MarkerBuffers &m, cudaStream_t s) {
     m.sorted = passes & 1;
     if (m.ns > 0) {
         bin_sort_kernel<<<1, SORT_T, 0, s>>>(g, m.ns, m.X, m.keys[0], m.perm[0], m.keys[1],
-                                             m.perm[1], passes, m.err);
+                                             m.perm[1], passes, m.err, m.cell, m.frac_d, m.frac_f);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

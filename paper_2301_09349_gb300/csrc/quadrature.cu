@@ -20,13 +20,12 @@ __global__ void assemble_kernel(const GridParams g, const MarkerBuffers m, const
                                 const unsigned *__restrict__ keys, const int *__restrict__ perm) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= m.ns) return;
-    double Xk[3] = {0, 0, 0};
     int ck[3] = {0, 0, 0};
     double wk[3][3];
     for (int d = 0; d < DIM; ++d) {
-        Xk[d] = m.X[(long long)k * DIM + d];
-        ck[d] = owner_cell(Xk[d], g.lo[d], g.h);
-        for (int i = 0; i < 3; ++i) wk[d][i] = phi_d((cell_center(g, d, ck[d] - 1 + i) - Xk[d]) * g.inv_h);
+        ck[d] = m.cell[(long long)k * 3 + d];
+        const double fk = m.frac_d[(long long)k * 3 + d];
+        for (int i = 0; i < 3; ++i) wk[d][i] = phi_d(((double)(i - 1) + 0.5) - fk);
     }
     int cnt = 0;
     bool overflow = false;
@@ -50,10 +49,11 @@ __global__ void assemble_kernel(const GridParams g, const MarkerBuffers m, const
                     const int l = perm[p];
                     double a = 1.0;
                     for (int d = 0; d < DIM; ++d) {
-                        const double Xl = m.X[(long long)l * DIM + d];
+                        const int cl = m.cell[(long long)l * 3 + d];
+                        const double fl = m.frac_d[(long long)l * 3 + d];
                         double s = 0.0;
                         for (int i = 0; i < 3; ++i)
-                            s += wk[d][i] * phi_d((cell_center(g, d, ck[d] - 1 + i) - Xl) * g.inv_h);
+                            s += wk[d][i] * phi_d(((double)(ck[d] - 1 + i - cl) + 0.5) - fl);
                         a *= s;
                     }
                     if (l == k) q.diag[k] = a;
