@@ -58,8 +58,8 @@ def dist_env():
 
 
 def case_for(rank: int, world: int, n: int) -> C.Case:
-    variants = C.sphere_variants(n)
-    return variants[0] if world == 1 else variants[rank % len(variants)]
+    from paper_2301_09349_gb300 import replicas
+    return replicas.case_for_rank(rank, world, n)
 
 
 def workload_name(c: C.Case, n_kept: int) -> str:
@@ -281,15 +281,9 @@ def run_ours(args, rank, world, local):
     e2e_s = time.perf_counter() - t0
     barrier()
 
-    times = torch.tensor([ms, e2e_s * 1e3, float(N), float(n_kept)], dtype=torch.float64,
-                         device="cuda")
-    if dist is not None:
-        mx = times.clone()
-        dist.all_reduce(mx[:2], op=dist.ReduceOp.MAX)
-        sm = times.clone()
-        dist.all_reduce(sm[2:], op=dist.ReduceOp.SUM)
-        times = torch.cat([mx[:2], sm[2:]])
-    ms_max, e2e_ms_max, cells_all, markers_all = [float(x) for x in times.cpu()]
+    from paper_2301_09349_gb300 import replicas
+    ms_max, e2e_ms_max, cells_all, markers_all = replicas.reduce_timings(
+        dist, torch.device("cuda", local), ms, e2e_s * 1e3, float(N), float(n_kept))
 
     if rank == 0:
         steps = args.steps

@@ -30,7 +30,8 @@ constexpr int NC = 5;
 constexpr int RING = 4;
 constexpr int SLOT = NW * PP;
 constexpr int FXW = TX + 1;                              // x-faces per row
-constexpr size_t SMEM = sizeof(float) * (size_t)(RING * SLOT + NC * TY * FXW + NC * (TY + 1) * TX);
+constexpr size_t SMEM =
+    sizeof(float) * (size_t)(RING * SLOT + NC * TY * FXW + NC * (TY + 1) * TX + 2 * NC * TY * TX);
 
 struct FC {
     float gamma, inv_gm1, gm1, invR, mu_inf, S, onepS, lam_fac, inv_h, qinv_h, kvisc, E_inf;
@@ -53,11 +54,6 @@ FC make_fc(const GridParams &g) {
     c.E_inf = (float)(g.p_inf / (g.gamma - 1.0) + 0.5);
     c.viscous = g.mu_inf > 0.0;
     return c;
-}
-
-__device__ __forceinline__ float vl(float a, float b) {
-    const float ab = a * b;
-    return ab > 0.0f ? __fdividef(2.0f * ab, a + b) : 0.0f;
 }
 
 // ---- packed pairs: the x-face (.x) and the y-face (.y) of one thread ------
@@ -167,65 +163,73 @@ __device__ __forceinline__ void face_xy(const FC &c, const float *__restrict__ R
     Fy[0] = F0.y; Fy[1] = F1.y; Fy[2] = Fn.y; Fy[3] = F2.y; Fy[4] = FE.y;
 }
 
-// z-face between ring cells a (plane z) and b (plane z+1) of one column from
-// given reconstructed states; tangential neighbours are a/b +-1 and +-PX.
-__device__ __forceinline__ void face_z(const FC &c, const float *__restrict__ R, int a, int b,
-                                       const float (&wl)[NC], const float (&wr)[NC], float (&F)[NC]) {
-    const float keL = wl[1] * wl[1] + wl[2] * wl[2] + wl[3] * wl[3];
-    const float keR = wr[1] * wr[1] + wr[2] * wr[2] + wr[3] * wr[3];
-    const float EL = wl[4] * c.inv_gm1 + 0.5f * wl[0] * keL;
-    const float ER = wr[4] * c.inv_gm1 + 0.5f * wr[0] * keR;
-    const float unL = wl[3], unR = wr[3];
-    const float cL2 = __fdividef(c.gamma * wl[4], wl[0]);
-    const float cR2 = __fdividef(c.gamma * wr[4], wr[0]);
-    const float sL = fabsf(unL) + cL2 * rsqrtf(cL2);
-    const float sR = fabsf(unR) + cR2 * rsqrtf(cR2);
-    const float smax = fmaxf(sL, sR);
-    F[0] = 0.5f * (wl[0] * unL + wr[0] * unR) - 0.5f * smax * (wr[0] - wl[0]);
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        const float mL = wl[0] * wl[1 + m], mR = wr[0] * wr[1 + m];
-        const float fL = mL * unL + (m == 2 ? wl[4] : 0.0f);
-        const float fR = mR * unR + (m == 2 ? wr[4] : 0.0f);
-        F[1 + m] = 0.5f * (fL + fR) - 0.5f * smax * (mR - mL);
-    }
-    F[4] = 0.5f * ((EL + wl[4]) * unL + (ER + wr[4]) * unR) - 0.5f * smax * (ER - EL);
+// Two z-faces (columns A -> .x, B -> .y) between planes z (cells aA, aB) and
+// z+1 (bA, bB) from given reconstructed states; tangential neighbours are
+// +-1 (x) and +-PX (y) within each plane.
+__device__ __forceinline__ void face_zz(const FC &c, const float *__restrict__ R, int aA, int bA,
+                                        int aB, int bB, const float2 (&wl)[NC],
+                                        const float2 (&wr)[NC], float2 (&F)[NC]) {
+    const float2 keL = fma2(wl[1], wl[1], fma2(wl[2], wl[2], wl[3] * wl[3]));
+    const float2 keR = fma2(wr[1], wr[1], fma2(wr[2], wr[2], wr[3] * wr[3]));
+    const float2 EL = fma2(wl[4], sp(c.inv_gm1), sp(0.5f) * wl[0] * keL);
+    const float2 ER = fma2(wr[4], sp(c.inv_gm1), sp(0.5f) * wr[0] * keR);
+    const float2 unL = wl[3], unR = wr[3];
+    const float2 c2L = sp(c.gamma) * wl[4] * rcp2(wl[0]);
+    const float2 c2R = sp(c.gamma) * wr[4] * rcp2(wr[0]);
+    const float2 sL = fma2(c2L, rsqrt2(c2L), abs2(unL));
+    const float2 sR = fma2(c2R, rsqrt2(c2R), abs2(unR));
+    const float2 hs = sp(-0.5f) * max2(sL, sR);
+    const float2 mLn = wl[0] * unL, mRn = wr[0] * unR;
+    const float2 mLu = wl[0] * wl[1], mRu = wr[0] * wr[1];
+    const float2 mLv = wl[0] * wl[2], mRv = wr[0] * wr[2];
+    F[0] = fma2(hs, wr[0] - wl[0], sp(0.5f) * (mLn + mRn));
+    F[1] = fma2(hs, mRu - mLu, sp(0.5f) * fma2(mLu, unL, mRu * unR));
+    F[2] = fma2(hs, mRv - mLv, sp(0.5f) * fma2(mLv, unL, mRv * unR));
+    F[3] = fma2(hs, mRn - mLn, sp(0.5f) * (fma2(mLn, unL, wl[4]) + fma2(mRn, unR, wr[4])));
+    F[4] = fma2(hs, ER - EL, sp(0.5f) * fma2(EL + wl[4], unL, (ER + wr[4]) * unR));
     if (!c.viscous) return;
-    const float *Tc = R + 5 * PP;
-    const float Ta = Tc[a], Tb = Tc[b];
-    const float Tf = 0.5f * (Ta + Tb);
-    const float mu = __fdividef(c.mu_inf * Tf * (Tf * rsqrtf(Tf)) * c.onepS, Tf + c.S);
-    const float lam = mu * c.lam_fac;
-    const float *uz = R + 3 * PP, *ux = R + PP, *uy = R + 2 * PP;
-    const float dn_w = (uz[b] - uz[a]) * c.inv_h;
-    const float dn_u = (ux[b] - ux[a]) * c.inv_h;
-    const float dn_v = (uy[b] - uy[a]) * c.inv_h;
-    const float dn_T = (Tb - Ta) * c.inv_h;
-    const float dx_w = (uz[a + 1] - uz[a - 1] + uz[b + 1] - uz[b - 1]) * c.qinv_h;
-    const float dy_w = (uz[a + PX] - uz[a - PX] + uz[b + PX] - uz[b - PX]) * c.qinv_h;
-    const float dx_u = (ux[a + 1] - ux[a - 1] + ux[b + 1] - ux[b - 1]) * c.qinv_h;
-    const float dy_v = (uy[a + PX] - uy[a - PX] + uy[b + PX] - uy[b - PX]) * c.qinv_h;
-    const float div = dn_w + dx_u + dy_v;
-    const float tzz = mu * (2.0f * dn_w - (2.0f / 3.0f) * div);
-    const float tzx = mu * (dx_w + dn_u);
-    const float tzy = mu * (dy_w + dn_v);
-    const float ufw = 0.5f * (uz[a] + uz[b]);
-    const float ufu = 0.5f * (ux[a] + ux[b]);
-    const float ufv = 0.5f * (uy[a] + uy[b]);
-    F[3] -= tzz;
-    F[1] -= tzx;
-    F[2] -= tzy;
-    F[4] -= ufw * tzz + ufu * tzx + ufv * tzy + lam * dn_T;
+    const float *T = R + 5 * PP, *U = R + PP, *V = R + 2 * PP, *Wz = R + 3 * PP;
+    const float2 Ta = make_float2(T[aA], T[aB]), Tb = make_float2(T[bA], T[bB]);
+    const float2 Tf = sp(0.5f) * (Ta + Tb);
+    const float2 mu = sp(c.mu_inf * c.onepS) * Tf * (Tf * rsqrt2(Tf)) * rcp2(Tf + sp(c.S));
+    const float2 lam = mu * sp(c.lam_fac);
+    const float2 ih = sp(c.inv_h), qh = sp(c.qinv_h);
+    auto P2 = [&](const float *f, int oA, int oB) { return make_float2(f[oA], f[oB]); };
+    const float2 dn_w = (P2(Wz, bA, bB) - P2(Wz, aA, aB)) * ih;
+    const float2 dn_u = (P2(U, bA, bB) - P2(U, aA, aB)) * ih;
+    const float2 dn_v = (P2(V, bA, bB) - P2(V, aA, aB)) * ih;
+    const float2 dn_T = (Tb - Ta) * ih;
+    const float2 dx_w = ((P2(Wz, aA + 1, aB + 1) - P2(Wz, aA - 1, aB - 1)) +
+                         (P2(Wz, bA + 1, bB + 1) - P2(Wz, bA - 1, bB - 1))) * qh;
+    const float2 dy_w = ((P2(Wz, aA + PX, aB + PX) - P2(Wz, aA - PX, aB - PX)) +
+                         (P2(Wz, bA + PX, bB + PX) - P2(Wz, bA - PX, bB - PX))) * qh;
+    const float2 dx_u = ((P2(U, aA + 1, aB + 1) - P2(U, aA - 1, aB - 1)) +
+                         (P2(U, bA + 1, bB + 1) - P2(U, bA - 1, bB - 1))) * qh;
+    const float2 dy_v = ((P2(V, aA + PX, aB + PX) - P2(V, aA - PX, aB - PX)) +
+                         (P2(V, bA + PX, bB + PX) - P2(V, bA - PX, bB - PX))) * qh;
+    const float2 div = dn_w + dx_u + dy_v;
+    const float2 tzz = mu * fma2(sp(2.0f), dn_w, sp(-2.0f / 3.0f) * div);
+    const float2 tzx = mu * (dx_w + dn_u);
+    const float2 tzy = mu * (dy_w + dn_v);
+    const float2 ufw = sp(0.5f) * (P2(Wz, aA, aB) + P2(Wz, bA, bB));
+    const float2 ufu = sp(0.5f) * (P2(U, aA, aB) + P2(U, bA, bB));
+    const float2 ufv = sp(0.5f) * (P2(V, aA, aB) + P2(V, bA, bB));
+    F[3] = F[3] - tzz;
+    F[1] = F[1] - tzx;
+    F[2] = F[2] - tzy;
+    F[4] = F[4] - fma2(ufw, tzz, fma2(ufu, tzx, fma2(ufv, tzy, lam * dn_T)));
 }
 
-// limited slopes of the five primitives across three cells of a column
-__device__ __forceinline__ void column_slope(const float *__restrict__ R, int lo, int mid, int hi,
-                                             float (&sig)[NC]) {
+// limited z-slopes of two columns (A -> .x, B -> .y) at the middle plane
+__device__ __forceinline__ void column_slope2(const float *__restrict__ R, int loA, int midA,
+                                              int hiA, int loB, int midB, int hiB,
+                                              float2 (&sig)[NC]) {
 #pragma unroll
     for (int m = 0; m < NC; ++m) {
         const float *w = R + m * PP;
-        const float a = w[mid] - w[lo], b = w[hi] - w[mid];
-        sig[m] = vl(a, b);
+        const float2 lo = make_float2(w[loA], w[loB]), mid = make_float2(w[midA], w[midB]),
+                     hi = make_float2(w[hiA], w[hiB]);
+        sig[m] = vl2(mid - lo, hi - mid);
     }
 }
 
@@ -308,6 +312,7 @@ zmarch_kernel(const GridParams g, const FC c, int zc, const float *__restrict__ 
     float *ring = smem_zm;
     float *FXb = ring + RING * SLOT;          // [NC][TY][FXW]
     float *FYb = FXb + NC * TY * FXW;         // [NC][TY+1][TX]
+    float *FZb = FYb + NC * (TY + 1) * TX;    // [2][NC][TY][TX] upper z-faces by plane parity
     __shared__ double s_red[NTH / 32];
     __shared__ int s_flag;
 
@@ -324,20 +329,27 @@ zmarch_kernel(const GridParams g, const FC c, int zc, const float *__restrict__ 
     __syncthreads();
 
     const int cxy = (lx + 2) + PX * (ly + 2);   // own column inside a plane
-    // z-face below the first plane (z0 - 1/2) from the slopes of cells z0-1, z0
-    float Fz[NC], sig0[NC];
-    {
+    // warps 0-3 own the z-faces of two cell rows each (2w -> .x, 2w+1 -> .y)
+    const bool zwarp = ly < TY / 2;
+    const int cA = (lx + 2) + PX * (2 * ly + 2), cB = cA + PX;
+    float2 sig0[NC];   // limited z-slopes of the current plane's cells, carried up
+    if (zwarp) {       // z-face below the first plane (z0 - 1/2)
         const int sam = slot_of(z0 - 2), sa = slot_of(z0 - 1), sb = slot_of(z0), sbp = slot_of(z0 + 1);
-        float sgA[NC];
-        column_slope(ring, sam + cxy, sa + cxy, sb + cxy, sgA);
-        column_slope(ring, sa + cxy, sb + cxy, sbp + cxy, sig0);
-        float wl[NC], wr[NC];
+        float2 sgA[NC], wl[NC], wr[NC], F[NC];
+        column_slope2(ring, sam + cA, sa + cA, sb + cA, sam + cB, sa + cB, sb + cB, sgA);
+        column_slope2(ring, sa + cA, sb + cA, sbp + cA, sa + cB, sb + cB, sbp + cB, sig0);
 #pragma unroll
         for (int m = 0; m < NC; ++m) {
-            wl[m] = ring[sa + m * PP + cxy] + 0.5f * sgA[m];
-            wr[m] = ring[sb + m * PP + cxy] - 0.5f * sig0[m];
+            wl[m] = fma2(sp(0.5f), sgA[m], make_float2(ring[sa + m * PP + cA], ring[sa + m * PP + cB]));
+            wr[m] = fma2(sp(-0.5f), sig0[m], make_float2(ring[sb + m * PP + cA], ring[sb + m * PP + cB]));
         }
-        face_z(c, ring, sa + cxy, sb + cxy, wl, wr, Fz);
+        face_zz(c, ring, sa + cA, sb + cA, sa + cB, sb + cB, wl, wr, F);
+        float *Fz = FZb + ((z0 - 1) & 1) * NC * TY * TX;
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            Fz[(m * TY + 2 * ly) * TX + lx] = F[m].x;
+            Fz[(m * TY + 2 * ly + 1) * TX + lx] = F[m].y;
+        }
     }
     __syncthreads();
 
@@ -360,40 +372,48 @@ zmarch_kernel(const GridParams g, const FC c, int zc, const float *__restrict__ 
                 FXb[(m * TY + ly) * FXW + lx] = Fx[m];
                 FYb[(m * (TY + 1) + ly) * TX + lx] = Fy[m];
             }
-            if (ly == 1) {   // the last x-face of each row and the last y-face row
-                const int r = lx < TY ? lx : 0;
-                face_xy(c, ring, s0 + (TX + 1) + PX * (r + 2), s0 + (lx + 2) + PX * (TY + 1), up, dn,
-                        Fx, Fy);
-#pragma unroll
-                for (int m = 0; m < NC; ++m) {
-                    if (lx < TY) FXb[(m * TY + lx) * FXW + TX] = Fx[m];
-                    FYb[(m * (TY + 1) + TY) * TX + lx] = Fy[m];
-                }
-            }
         }
-        // z-face above the column (between planes z and z+1); the slope of
-        // cell z is carried from the previous plane
-        float Fh[NC];
-        {
-            float sig1[NC], wl[NC], wr[NC];
-            column_slope(ring, s0 + cxy, s1 + cxy, s2 + cxy, sig1);
+        if (zwarp) {
+            // z-faces above two columns (between planes z and z+1); the slopes
+            // of the plane-z cells come from the previous plane
+            float2 sig1[NC], wl[NC], wr[NC], F[NC];
+            column_slope2(ring, s0 + cA, s1 + cA, s2 + cA, s0 + cB, s1 + cB, s2 + cB, sig1);
 #pragma unroll
             for (int m = 0; m < NC; ++m) {
-                wl[m] = ring[s0 + m * PP + cxy] + 0.5f * sig0[m];
-                wr[m] = ring[s1 + m * PP + cxy] - 0.5f * sig1[m];
+                wl[m] = fma2(sp(0.5f), sig0[m], make_float2(ring[s0 + m * PP + cA], ring[s0 + m * PP + cB]));
+                wr[m] = fma2(sp(-0.5f), sig1[m], make_float2(ring[s1 + m * PP + cA], ring[s1 + m * PP + cB]));
                 sig0[m] = sig1[m];
             }
-            face_z(c, ring, s0 + cxy, s1 + cxy, wl, wr, Fh);
+            face_zz(c, ring, s0 + cA, s1 + cA, s0 + cB, s1 + cB, wl, wr, F);
+            float *Fz = FZb + (z & 1) * NC * TY * TX;
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                Fz[(m * TY + 2 * ly) * TX + lx] = F[m].x;
+                Fz[(m * TY + 2 * ly + 1) * TX + lx] = F[m].y;
+            }
+        } else if (ly == TY / 2) {
+            // the last x-face of each row paired with the last y-face row
+            float Fx[NC], Fy[NC];
+            const int r = lx < TY ? lx : 0;
+            face_xy(c, ring, s0 + (TX + 1) + PX * (r + 2), s0 + (lx + 2) + PX * (TY + 1), up, dn,
+                    Fx, Fy);
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                if (lx < TY) FXb[(m * TY + lx) * FXW + TX] = Fx[m];
+                FYb[(m * (TY + 1) + TY) * TX + lx] = Fy[m];
+            }
         }
         __syncthreads();
 
         float acc[NC];
+        {
+            const float *Fzl = FZb + ((z - 1) & 1) * NC * TY * TX;
+            const float *Fzh = FZb + (z & 1) * NC * TY * TX;
 #pragma unroll
-        for (int m = 0; m < NC; ++m) {
-            acc[m] = (FXb[(m * TY + ly) * FXW + lx] - FXb[(m * TY + ly) * FXW + lx + 1]) +
-                     (FYb[(m * (TY + 1) + ly) * TX + lx] - FYb[(m * (TY + 1) + ly + 1) * TX + lx]) +
-                     (Fz[m] - Fh[m]);
-            Fz[m] = Fh[m];
+            for (int m = 0; m < NC; ++m)
+                acc[m] = (FXb[(m * TY + ly) * FXW + lx] - FXb[(m * TY + ly) * FXW + lx + 1]) +
+                         (FYb[(m * (TY + 1) + ly) * TX + lx] - FYb[(m * (TY + 1) + ly + 1) * TX + lx]) +
+                         (Fzl[(m * TY + ly) * TX + lx] - Fzh[(m * TY + ly) * TX + lx]);
         }
         const int gx = ox + lx, gy = oy + ly;
         if (gx < g.n[0] && gy < g.n[1]) {
