@@ -137,7 +137,8 @@ ibm_status ibm_set_wall_temperature(ibm_grid *g, const double *Tw);
 
 /* Advance nsteps IBM steps.  dt_fixed > 0 imposes the step size; otherwise
  * dt = cfl / max_j s_j is computed on the device from the state at the start
- * of each step.  Asynchronous; no host synchronization. */
+ * of each step (formed at the end of the previous step, or when the state is
+ * set).  Asynchronous; no host synchronization. */
 ibm_status ibm_step(ibm_grid *g, int nsteps, double dt_fixed);
 
 /* Force on the body and heat rate into the fluid from the last step's
@@ -177,7 +178,8 @@ ibm_status ibm_get_marker_forcing(ibm_grid *g, double *rhoL, double *F, double *
  * cells within a tile x-fastest.  *n_tiles receives the tile count. */
 ibm_status ibm_get_bins(ibm_grid *g, int *tile_off, int *perm, unsigned *keys, int *n_tiles);
 
-/* Last step size, simulated time and steps taken. */
+/* Size of the last step taken (0 before any step), simulated time and
+ * steps taken. */
 ibm_status ibm_get_time(ibm_grid *g, double *dt, double *t, long long *steps);
 
 /* ---- operators on caller device buffers (stream-ordered) --------------- */
@@ -216,10 +218,8 @@ ibm_status ibm_profile_read(ibm_grid *g, double *ms, long long *launches);
 
 /* ---- allocation-free stage 1 ------------------------------------------- */
 
-/* Largest stage-1 launch (thread blocks) ibm_rhs_dt_noalloc serves.  A 3D
- * FP32 grid uses one block per 32x8 column chunk of 8 to 32 planes (2048
- * blocks at 256^3), a 3D FP64 grid one per 8x8x4 cells, a 2D grid one per
- * 16x16 cells. */
+/* Largest step-size reduction (thread blocks of 2048 cells) that
+ * ibm_rhs_dt_noalloc serves: grids of up to 2^27 cells. */
 #define IBM_NOALLOC_MAX_CTAS 65536
 
 /* Fluid stage 1 for callers that cannot allocate device memory: writes
@@ -240,7 +240,7 @@ ibm_status ibm_profile_read(ibm_grid *g, double *ms, long long *launches);
  *    streams, other host threads) race and must be serialised by the caller.
  *  - A non-finite or non-positive state gives *dt = 0.  No device memory is
  *    allocated or freed.  Errors: IBM_ERR_ARG (invalid description, null
- *    buffer, or a grid needing more than IBM_NOALLOC_MAX_CTAS blocks; the
+ *    buffer, or a grid of more than 2^27 cells (IBM_NOALLOC_MAX_CTAS blocks); the
  *    message is ibm_last_error(NULL)), IBM_ERR_CUDA.  Asynchronous. */
 ibm_status ibm_rhs_dt_noalloc(const ibm_grid_desc *desc, const void *U, void *L, double *dt,
                               void *stream);

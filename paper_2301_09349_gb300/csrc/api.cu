@@ -66,6 +66,9 @@ namespace {
 
 thread_local std::string g_create_error;
 
+// upper bound of the persistent marker-kernel grids (4 CTAs per SM)
+constexpr int kMaxPersistentCtas = 4096;
+
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 size_t state_bytes(const ibm_grid_desc &d) {
@@ -192,6 +195,8 @@ void layout(ibm_grid *g, const ibm_grid_desc &d, int cap, char *base, size_t *to
     m.band_list = c.take<int>(gp.n_tiles);
     m.counts = c.take<int>(4);
     m.sums = c.take<double>(8);
+    m.bandmax = c.take<double>(kMaxPersistentCtas);
+    m.band_bits = c.take<unsigned>((size_t)(gp.N / 32 + 1));
     m.t = c.take<double>(1);
     m.steps = c.take<long long>(1);
     QuadBuffers q{};
@@ -216,6 +221,7 @@ void layout(ibm_grid *g, const ibm_grid_desc &d, int cap, char *base, size_t *to
     g->fb.counter = counter;
     g->fb.dt = scal;
     g->fb.err = err;
+    g->fb.band_bits = m.band_bits;
     g->scratch_d = scal;
     g->err_d = err;
     m.err = err;
@@ -254,7 +260,9 @@ ibm_status check_device(ibm_grid *g) {
     return IBM_OK;
 }
 
-int persistent_ctas(const ibm_grid *g) { return std::max(1, g->n_sm) * 4; }
+int persistent_ctas(const ibm_grid *g) {
+    return std::min(kMaxPersistentCtas, std::max(1, g->n_sm) * 4);
+}
 
 // Event pair around a kernel group (no-op unless profiling is on).
 cudaError_t prof_begin(ibm_grid *g, int group, int launches, long *rec) {
@@ -295,6 +303,7 @@ cudaError_t prof_collect(ibm_grid *g) {
 // Marker pipeline on the device: bins, then quadrature (warm start if asked).
 ibm_status rebuild_markers(ibm_grid *g, int warm) {
     CU(launch_bin(g->gp, g->mb, g->stream), "bin markers");
+    CU(launch_band_mask(g->gp, g->mb, persistent_ctas(g), g->stream), "band mask");
     if (g->mb.ns > 0)
         CU(launch_quadrature(g->gp, g->mb, g->qb, g->cg_tol, g->cg_maxit, warm, g->stream),
            "quadrature");
@@ -360,6 +369,7 @@ ibm_status ibm_create_grid(const ibm_grid_desc *desc, int max_markers, void *dev
     if (e == cudaSuccess) e = cudaMemsetAsync(g->mb.steps, 0, sizeof(long long), g->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->mb.counts, 0, 4 * sizeof(int), g->stream);
     if (e == cudaSuccess) e = launch_bin(g->gp, g->mb, g->stream);  // empty bins
+    if (e == cudaSuccess) e = launch_band_mask(g->gp, g->mb, 1, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) {
         g_create_error = std::string("CUDA: ") + cudaGetErrorString(e);
@@ -385,6 +395,7 @@ ibm_status ibm_set_state(ibm_grid *g, const void *U) {
     if (!U) return fail(g, IBM_ERR_ARG, "null state pointer");
     CU(cudaMemcpyAsync(g->U[g->cur], U, state_bytes(g->desc), cudaMemcpyDeviceToDevice, g->stream),
        "set_state copy");
+    CU(launch_dt_init(g->gp, g->desc.fp_bytes, g->U[g->cur], g->fb, g->stream), "initial dt");
     CU(cudaMemsetAsync(g->mb.t, 0, sizeof(double), g->stream), "reset time");
     CU(cudaMemsetAsync(g->mb.steps, 0, sizeof(long long), g->stream), "reset steps");
     g->has_state = true;
@@ -397,6 +408,7 @@ ibm_status ibm_set_state_host(ibm_grid *g, const void *U_host) {
     CU(cudaMemcpyAsync(g->U[g->cur], U_host, state_bytes(g->desc), cudaMemcpyHostToDevice,
                        g->stream),
        "set_state_host copy");
+    CU(launch_dt_init(g->gp, g->desc.fp_bytes, g->U[g->cur], g->fb, g->stream), "initial dt");
     CU(cudaMemsetAsync(g->mb.t, 0, sizeof(double), g->stream), "reset time");
     CU(cudaMemsetAsync(g->mb.steps, 0, sizeof(long long), g->stream), "reset steps");
     g->has_state = true;
@@ -539,23 +551,25 @@ ibm_status ibm_step(ibm_grid *g, int nsteps, double dt_fixed) {
     const int fpb = g->desc.fp_bytes;
     const int ctas = persistent_ctas(g);
     long rec;
+    const int nb = (int)fluid_stage_blocks(g->gp, fpb);
     for (int s = 0; s < nsteps; ++s) {
         void *Un = g->U[g->cur];
         void *Us = g->U[1 - g->cur];
+        void *U1 = g->L;
         CU(prof_begin(g, IBM_PROF_STAGE1, 1, &rec), "profile");
-        CU(launch_stage1(g->gp, fpb, Un, g->L, g->fb, dt_fixed, g->stream), "stage 1");
+        CU(launch_stage1(g->gp, fpb, Un, U1, g->fb, dt_fixed, g->stream), "stage 1");
         CU(prof_end(g, rec), "profile");
         if (g->moving && g->mb.ns > 0) {
-            CU(prof_begin(g, IBM_PROF_MARKERS, 7, &rec), "profile");
+            CU(prof_begin(g, IBM_PROF_MARKERS, 8, &rec), "profile");
             CU(launch_motion(g->gp, g->mb, g->motion.amp, g->motion.freq, g->motion.axis, g->fb.dt,
-                             g->stream),
+                             dt_fixed, g->stream),
                "motion");
             ibm_status st = rebuild_markers(g, 1);
             if (st != IBM_OK) return st;
             CU(prof_end(g, rec), "profile");
         }
         CU(prof_begin(g, IBM_PROF_STAGE2, 1, &rec), "profile");
-        CU(launch_stage2(g->gp, fpb, Un, g->L, Us, g->fb, g->stream), "stage 2");
+        CU(launch_stage2(g->gp, fpb, Un, U1, Us, g->fb, dt_fixed, g->stream), "stage 2");
         CU(prof_end(g, rec), "profile");
         if (g->mb.ns > 0) {
             CU(prof_begin(g, IBM_PROF_INTERP, 1, &rec), "profile");
@@ -566,7 +580,8 @@ ibm_status ibm_step(ibm_grid *g, int nsteps, double dt_fixed) {
             CU(prof_end(g, rec), "profile");
         }
         CU(prof_begin(g, IBM_PROF_FINISH, 1, &rec), "profile");
-        CU(launch_finish(g->gp, g->mb, g->fb.dt, g->stream), "finish");
+        CU(launch_finish(g->gp, g->mb, g->fb, nb, g->mb.ns > 0 ? ctas : 0, dt_fixed, g->stream),
+           "finish");
         CU(prof_end(g, rec), "profile");
         g->cur = 1 - g->cur;
     }
@@ -705,7 +720,8 @@ ibm_status ibm_get_time(ibm_grid *g, double *dt, double *t, long long *steps) {
     if (!g) return IBM_ERR_ARG;
     double dtv = 0.0, tv = 0.0;
     long long sv = 0;
-    CU(cudaMemcpyAsync(&dtv, g->fb.dt, sizeof(double), cudaMemcpyDeviceToHost, g->stream), "read dt");
+    CU(cudaMemcpyAsync(&dtv, g->mb.sums + 4, sizeof(double), cudaMemcpyDeviceToHost, g->stream),
+       "read dt");
     CU(cudaMemcpyAsync(&tv, g->mb.t, sizeof(double), cudaMemcpyDeviceToHost, g->stream), "read t");
     CU(cudaMemcpyAsync(&sv, g->mb.steps, sizeof(long long), cudaMemcpyDeviceToHost, g->stream),
        "read steps");

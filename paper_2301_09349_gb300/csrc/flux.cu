@@ -5,9 +5,10 @@
 //   Fhat = Rusanov(MUSCL/van Leer states of (rho, u, p)) - viscous/heat flux,
 //
 // advanced by SSP-RK2 as the source-free predictor of App. B (step 1):
-//   stage 1:  L^n = L(U^n);  dt = cfl / max_j s_j(U^n)
-//   stage 2:  U* = U^n/2 + (U^1 + dt L(U^1))/2,  U^1 = U^n + dt L^n
-// U^1 is never stored: stage 2 rebuilds it while loading its tile.
+//   stage 1:  U^1 = U^n + dt L(U^n)
+//   stage 2:  U* = U^n/2 + (U^1 + dt L(U^1))/2
+// with dt = cfl / max_j s_j(U^n), formed at the end of the previous step (or
+// by dt_init after a new state) so that stage 1 can write U^1 directly.
 //
 // Each CTA owns a BX x BY x BZ tile of cells.  It loads the tile plus a
 // two-cell halo once (ghost cells mapped through the boundary conditions on
@@ -201,29 +202,30 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-// MODE 0: L only.  MODE 1: stage 1 (L and the step size).  MODE 2: stage 2.
+// MODE 0: out = L(Uin).  MODE 1: out = U1 = Uin + dt L(Uin).
+// MODE 2: out = U* = Un/2 + (Uin + dt L(Uin))/2 with Uin = U1, plus the
+// per-CTA maximum of s_j(U*) over the cells outside the band.
 template <int DIM, typename T, int MODE>
 __global__ void __launch_bounds__(NT)
-stage_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ Lp,
-             T *__restrict__ out, double *__restrict__ blockmax, unsigned *__restrict__ counter,
-             double *__restrict__ dt_ptr, int *__restrict__ err, double dt_fixed) {
+stage_kernel(const GridParams g, const T *__restrict__ Uin, const T *__restrict__ Un,
+             T *__restrict__ out, double *__restrict__ blockmax, const double *__restrict__ dt_ptr,
+             int *__restrict__ err, const unsigned *__restrict__ band_bits, double dt_fixed) {
     using B = Box<DIM, T>;
     constexpr int NC = DIM + 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sW = reinterpret_cast<T *>(smem_raw);
     T *sF = sW + B::NW * B::PN;
     __shared__ double s_red[NT / 32];
-    __shared__ int s_flag;
 
     const int tid = threadIdx.x;
     const int ox = blockIdx.x * B::BX, oy = blockIdx.y * B::BY;
     const int oz = DIM == 3 ? blockIdx.z * B::BZ : 0;
     const long long N = g.N;
-    const T dt = MODE == 2 ? (T)(*dt_ptr) : T(0);
+    const T dt = MODE == 0 ? T(0) : (T)(dt_fixed > 0.0 ? dt_fixed : *dt_ptr);
     const T gm1 = (T)(g.gamma - 1.0);
     const T invR = (T)(1.0 / g.R);
 
-    // ---- load tile + halo, build U1 on the fly in stage 2, to primitives
+    // ---- load tile + halo, to primitives
     // Tiles whose halo lies inside the domain index directly; the others map
     // every halo index through the boundary conditions.
     const bool interior = ox >= 2 && oy >= 2 && ox + B::BX + 2 <= g.n[0] &&
@@ -240,11 +242,7 @@ stage_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ 
             const long long j = (ox + lx - 2) +
                                 (long long)g.n[0] * ((oy + ly - 2) + (long long)g.n[1] * (oz + lz - 2 * (DIM == 3)));
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                T v = __ldg(U + c * N + j);
-                if (MODE == 2) v = v + dt * __ldg(Lp + c * N + j);
-                u[c] = v;
-            }
+            for (int c = 0; c < NC; ++c) u[c] = __ldg(Uin + c * N + j);
         } else {
             int flip = 0, fs = 0;
             const int sx = map_axis(ox + lx - 2, g.n[0], g.bc[0], g.bc[1], 0, flip, fs);
@@ -259,11 +257,7 @@ stage_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ 
             } else {
                 const long long j = sx + (long long)g.n[0] * (sy + (long long)g.n[1] * sz);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    T v = __ldg(U + c * N + j);
-                    if (MODE == 2) v = v + dt * __ldg(Lp + c * N + j);
-                    u[c] = v;
-                }
+                for (int c = 0; c < NC; ++c) u[c] = __ldg(Uin + c * N + j);
 #pragma unroll
                 for (int d = 0; d < DIM; ++d)
                     if ((flip >> d) & 1) u[1 + d] = -u[1 + d];
@@ -298,7 +292,7 @@ stage_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ 
     // ---- outputs
     const T inv_h = (T)g.inv_h;
     double smax = 0.0;
-    int bad = 0;
+    bool ok = true;
 #pragma unroll
     for (int i = 0; i < B::CPT; ++i) {
         const int cell = tid + i * NT;
@@ -309,79 +303,89 @@ stage_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ 
         const int gx = ox + cx, gy = oy + cy, gz = oz + cz;
         if (gx >= g.n[0] || gy >= g.n[1] || (DIM == 3 && gz >= g.n[2])) continue;
         const long long j = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
-        if (MODE == 2) {
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                const T un = __ldg(U + c * N + j);
-                const T u1 = un + dt * __ldg(Lp + c * N + j);
-                out[c * N + j] = T(0.5) * un + T(0.5) * (u1 + dt * (acc[i][c] * inv_h));
-            }
-        } else {
+        if (MODE == 0) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) out[c * N + j] = acc[i][c] * inv_h;
-        }
-        if (MODE == 1) {
-            const int q = (cx + 2) + B::PX * (cy + 2) + (DIM == 3 ? B::PX * B::PY * (cz + 2) : 0);
-            const T rho = sW[q], p = sW[(DIM + 1) * B::PN + q], Tt = sW[(DIM + 2) * B::PN + q];
-            const T c = psqrt<T>(fdiv<T>((T)g.gamma * p, rho));
-            T mu = T(0);
-            if (g.mu_inf > 0.0) {
-                const T Sv = (T)g.S;
-                mu = fdiv<T>((T)g.mu_inf * Tt * psqrt<T>(Tt) * (T(1) + Sv), Tt + Sv);
-            }
-            const T nu = fdiv<T>((T)g.kvisc * mu, rho);
-            T s = T(0);
+        } else if (MODE == 1) {
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) s += (fabs(sW[(1 + d) * B::PN + q]) + c) * inv_h;
-            s += T(2 * DIM) * nu * inv_h * inv_h;
-            const double sd = (double)s;
-            if (!(rho > T(0) && p > T(0) && sd <= DBL_MAX)) bad = 1;
-            else smax = fmax(smax, sd);
+            for (int c = 0; c < NC; ++c) out[c * N + j] = __ldg(Uin + c * N + j) + dt * (acc[i][c] * inv_h);
+        } else {
+            T us[NC];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const T un = __ldg(Un + c * N + j);
+                const T u1 = __ldg(Uin + c * N + j);
+                us[c] = T(0.5) * un + T(0.5) * (u1 + dt * (acc[i][c] * inv_h));
+                out[c * N + j] = us[c];
+            }
+            if (!band_bit(band_bits, j)) {
+                const T sj = step_rate<DIM, T>(g, us, ok);
+                smax = fmax(smax, (double)sj);
+            }
         }
     }
 
-    if (MODE == 1) {
-        // block maximum, then the last CTA to finish reduces all blocks
+    if (MODE == 2) {
         smax = warp_max(smax);
-        bad = __syncthreads_or(bad);
+        const int bad = __syncthreads_or(!ok);
         if ((tid & 31) == 0) s_red[tid >> 5] = smax;
         __syncthreads();
-        const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
-        const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
         if (tid == 0) {
             double m = s_red[0];
             for (int w = 1; w < NT / 32; ++w) m = fmax(m, s_red[w]);
-            blockmax[bid] = m;
+            blockmax[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = m;
             if (bad) record_error(err, ERR_NONFINITE);
-            __threadfence();
-            const unsigned ticket = atomicAdd(counter, 1u);
-            s_flag = ticket == nblocks - 1;
         }
-        __syncthreads();
-        if (s_flag) {
-            __threadfence();
-            double m = 0.0;
-            for (unsigned b = tid; b < nblocks; b += NT) m = fmax(m, __ldcg(blockmax + b));
-            m = warp_max(m);
-            if ((tid & 31) == 0) s_red[tid >> 5] = m;
-            __syncthreads();
-            if (tid == 0) {
-                double mm = s_red[0];
-                for (int w = 1; w < NT / 32; ++w) mm = fmax(mm, s_red[w]);
-                double dtv;
-                if (dt_fixed > 0.0) {
-                    dtv = dt_fixed;
-                } else if (mm > 0.0 && mm <= DBL_MAX) {
-                    dtv = g.cfl / mm;
-                } else {
-                    dtv = 0.0;
-                    record_error(err, ERR_NONFINITE);
-                }
-                if (__ldcg(err) & ERR_NONFINITE) dtv = 0.0;
-                *dt_ptr = dtv;
-                *counter = 0u;
-            }
-        }
+    }
+}
+
+// *dt = cfl / max_j s_j(U) over every cell: per-CTA maxima, then the last
+// CTA to finish reduces them.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(NT)
+dt_init_kernel(const GridParams g, const T *__restrict__ U, double *__restrict__ blockmax,
+               unsigned *__restrict__ counter, double *__restrict__ dt, int *__restrict__ err) {
+    constexpr int NC = DIM + 2;
+    __shared__ double s_red[NT / 32];
+    __shared__ int s_last;
+    const long long N = g.N;
+    const long long j0 = (long long)blockIdx.x * DT_CELLS_PER_CTA;
+    const long long j1 = j0 + DT_CELLS_PER_CTA < N ? j0 + DT_CELLS_PER_CTA : N;
+    double smax = 0.0;
+    bool ok = true;
+    for (long long j = j0 + threadIdx.x; j < j1; j += NT) {
+        T u[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) u[c] = U[c * N + j];
+        smax = fmax(smax, (double)step_rate<DIM, T>(g, u, ok));
+    }
+    smax = warp_max(smax);
+    const int bad = __syncthreads_or(!ok);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = smax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = s_red[0];
+        for (int w = 1; w < NT / 32; ++w) m = fmax(m, s_red[w]);
+        blockmax[blockIdx.x] = m;
+        if (bad) record_error(err, ERR_NONFINITE);
+        __threadfence();
+        s_last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double m = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += NT) m = fmax(m, __ldcg(blockmax + b));
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mm = s_red[0];
+        for (int w = 1; w < NT / 32; ++w) mm = fmax(mm, s_red[w]);
+        const bool good = mm > 0.0 && mm <= DBL_MAX && !(__ldcg(err) & ERR_NONFINITE);
+        if (!good) record_error(err, ERR_NONFINITE);
+        *dt = good ? g.cfl / mm : 0.0;
+        *counter = 0u;
     }
 }
 
@@ -393,7 +397,7 @@ dim3 stage_grid(const GridParams &g) {
 }
 
 template <int DIM, typename T, int MODE>
-cudaError_t launch_one(const GridParams &g, const void *U, const void *Lp, void *out,
+cudaError_t launch_one(const GridParams &g, const void *Uin, const void *Un, void *out,
                        const FluidBuffers &fb, double dt_fixed, cudaStream_t s) {
     using B = Box<DIM, T>;
     static bool configured = false;
@@ -405,24 +409,25 @@ cudaError_t launch_one(const GridParams &g, const void *U, const void *Lp, void 
         configured = true;
     }
     stage_kernel<DIM, T, MODE><<<stage_grid<DIM, T>(g), NT, B::SMEM, s>>>(
-        g, (const T *)U, (const T *)Lp, (T *)out, fb.blockmax, fb.counter, fb.dt, fb.err, dt_fixed);
+        g, (const T *)Uin, (const T *)Un, (T *)out, fb.blockmax, fb.dt, fb.err, fb.band_bits,
+        dt_fixed);
     return cudaGetLastError();
 }
 
 template <int MODE>
-cudaError_t dispatch(const GridParams &g, int fp_bytes, const void *U, const void *Lp, void *out,
+cudaError_t dispatch(const GridParams &g, int fp_bytes, const void *Uin, const void *Un, void *out,
                      const FluidBuffers &fb, double dt_fixed, cudaStream_t s) {
     if (g.dim == 3) {
-        if (fp_bytes == 4) return launch_zmarch(MODE, g, U, Lp, out, fb, dt_fixed, s);
-        return launch_one<3, double, MODE>(g, U, Lp, out, fb, dt_fixed, s);
+        if (fp_bytes == 4) return launch_zmarch(MODE, g, Uin, Un, out, fb, dt_fixed, s);
+        return launch_one<3, double, MODE>(g, Uin, Un, out, fb, dt_fixed, s);
     }
-    if (fp_bytes == 4) return launch_one<2, float, MODE>(g, U, Lp, out, fb, dt_fixed, s);
-    return launch_one<2, double, MODE>(g, U, Lp, out, fb, dt_fixed, s);
+    if (fp_bytes == 4) return launch_one<2, float, MODE>(g, Uin, Un, out, fb, dt_fixed, s);
+    return launch_one<2, double, MODE>(g, Uin, Un, out, fb, dt_fixed, s);
 }
 
 }  // namespace
 
-size_t fluid_blockmax_count(const GridParams &g, int fp_bytes) {
+size_t fluid_stage_blocks(const GridParams &g, int fp_bytes) {
     dim3 d;
     if (g.dim == 3 && fp_bytes == 4) return zmarch_blocks(g);
     if (g.dim == 3) d = stage_grid<3, double>(g);
@@ -430,19 +435,41 @@ size_t fluid_blockmax_count(const GridParams &g, int fp_bytes) {
     return (size_t)d.x * d.y * d.z;
 }
 
-cudaError_t launch_stage1(const GridParams &g, int fp_bytes, const void *U, void *L,
-                          const FluidBuffers &fb, double dt_fixed, cudaStream_t s) {
-    return dispatch<1>(g, fp_bytes, U, nullptr, L, fb, dt_fixed, s);
+size_t dt_init_blocks(const GridParams &g) {
+    return (size_t)((g.N + DT_CELLS_PER_CTA - 1) / DT_CELLS_PER_CTA);
 }
 
-cudaError_t launch_stage2(const GridParams &g, int fp_bytes, const void *U, const void *Lprev,
-                          void *out, const FluidBuffers &fb, cudaStream_t s) {
-    return dispatch<2>(g, fp_bytes, U, Lprev, out, fb, 0.0, s);
+size_t fluid_blockmax_count(const GridParams &g, int fp_bytes) {
+    const size_t a = fluid_stage_blocks(g, fp_bytes), b = dt_init_blocks(g);
+    return a > b ? a : b;
+}
+
+cudaError_t launch_stage1(const GridParams &g, int fp_bytes, const void *U, void *U1,
+                          const FluidBuffers &fb, double dt_fixed, cudaStream_t s) {
+    return dispatch<1>(g, fp_bytes, U, U, U1, fb, dt_fixed, s);
+}
+
+cudaError_t launch_stage2(const GridParams &g, int fp_bytes, const void *Un, const void *U1,
+                          void *out, const FluidBuffers &fb, double dt_fixed, cudaStream_t s) {
+    return dispatch<2>(g, fp_bytes, U1, Un, out, fb, dt_fixed, s);
 }
 
 cudaError_t launch_rhs(const GridParams &g, int fp_bytes, const void *U, void *L,
                        const FluidBuffers &fb, cudaStream_t s) {
-    return dispatch<0>(g, fp_bytes, U, nullptr, L, fb, 0.0, s);
+    return dispatch<0>(g, fp_bytes, U, U, L, fb, 0.0, s);
+}
+
+cudaError_t launch_dt_init(const GridParams &g, int fp_bytes, const void *U,
+                           const FluidBuffers &fb, cudaStream_t s) {
+    const unsigned nb = (unsigned)dt_init_blocks(g);
+    if (g.dim == 3) {
+        if (fp_bytes == 4) dt_init_kernel<3, float><<<nb, NT, 0, s>>>(g, (const float *)U, fb.blockmax, fb.counter, fb.dt, fb.err);
+        else dt_init_kernel<3, double><<<nb, NT, 0, s>>>(g, (const double *)U, fb.blockmax, fb.counter, fb.dt, fb.err);
+    } else {
+        if (fp_bytes == 4) dt_init_kernel<2, float><<<nb, NT, 0, s>>>(g, (const float *)U, fb.blockmax, fb.counter, fb.dt, fb.err);
+        else dt_init_kernel<2, double><<<nb, NT, 0, s>>>(g, (const double *)U, fb.blockmax, fb.counter, fb.dt, fb.err);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace ibmk

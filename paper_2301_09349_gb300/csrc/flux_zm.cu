@@ -15,8 +15,12 @@
 //     kept in registers as the next plane's lower face,
 //   - each thread forms its cell's flux divergence and writes its output.
 // All constants are single precision: the kernel issues no FP64 work
-// except the step-size reduction.
+// except the per-CTA step-size maximum.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <float.h>
+#include <stdint.h>
+#include <string.h>
 
 #include "internal.h"
 
@@ -30,8 +34,15 @@ constexpr int NC = 5;
 constexpr int RING = 4;
 constexpr int SLOT = NW * PP;
 constexpr int FXW = TX + 1;                              // x-faces per row
-constexpr size_t SMEM =
+// TMA staging box of one plane: x from ox-4 (16-byte aligned) over 40 cells,
+// y from oy-2 over 12 rows, the five conserved components
+constexpr int SBX = TX + 8, SBY = TY + 4;
+constexpr int STAGE = NC * SBX * SBY;                    // floats
+constexpr size_t SMEM_BASE =
     sizeof(float) * (size_t)(RING * SLOT + NC * TY * FXW + NC * (TY + 1) * TX + 2 * NC * TY * TX);
+constexpr size_t SMEM_TMA_OFF = (SMEM_BASE + 127) / 128 * 128;
+constexpr size_t SMEM = SMEM_TMA_OFF + sizeof(float) * STAGE + 16;   // + mbarrier
+constexpr long long TMA_WAIT_LIMIT = 1ll << 20;          // bounded mbarrier waits
 
 struct FC {
     float gamma, inv_gm1, gm1, invR, mu_inf, S, onepS, lam_fac, inv_h, qinv_h, kvisc, E_inf;
@@ -233,14 +244,93 @@ __device__ __forceinline__ void column_slope2(const float *__restrict__ R, int l
     }
 }
 
-// Load plane gz (ghosts through the boundary conditions), build U1 on the
-// fly in stage 2, convert to primitives into one ring slot.
-template <int MODE>
+// ---- TMA: one bulk tensor copy per plane into the staging box -------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned mbar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// issue the copy of plane gz (thread 0 only)
+__device__ __forceinline__ void tma_issue(const CUtensorMap *tmap, unsigned dst, unsigned mbar,
+                                          int x0, int y0, int gz) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 ::"r"(mbar), "r"((unsigned)(sizeof(float) * STAGE)) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(dst), "l"((unsigned long long)tmap), "r"(x0), "r"(y0), "r"(gz), "r"(0), "r"(mbar)
+        : "memory");
+}
+// wait for the phase with the given parity; bounded: after TMA_WAIT_LIMIT
+// polls it gives up, sets the error flag and returns false
+__device__ __forceinline__ bool tma_wait(unsigned mbar, unsigned parity, int *err) {
+    for (long long it = 0; it < TMA_WAIT_LIMIT; ++it) {
+        unsigned done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;"
+            " selp.u32 %0, 1, 0, p; }"
+            : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    record_error(err, ERR_TIMEOUT);
+    return false;
+}
+
+// Convert the staged plane gz into one ring slot.  Cells outside the domain in
+// x or y (zero-filled by the copy) are taken through the boundary conditions.
+__device__ __forceinline__ void convert_staged(const GridParams &g, const FC &c,
+                                               const float *__restrict__ U,
+                                               const float *__restrict__ st,
+                                               float *__restrict__ slot, int ox, int oy, int gz,
+                                               bool xy_interior) {
+    const long long N = g.N;
+    for (int q = threadIdx.x; q < PP; q += NTH) {
+        const int lx = q % PX, ly = q / PX;
+        const int gx = ox + lx - 2, gy = oy + ly - 2;
+        float u[NC];
+        if (xy_interior || (gx >= 0 && gx < g.n[0] && gy >= 0 && gy < g.n[1])) {
+#pragma unroll
+            for (int m = 0; m < NC; ++m) u[m] = st[(m * SBY + ly) * SBX + lx + 2];
+        } else {
+            int flip = 0, fs = 0;
+            const int sx = map_axis(gx, g.n[0], g.bc[0], g.bc[1], 0, flip, fs);
+            const int sy = map_axis(gy, g.n[1], g.bc[2], g.bc[3], 1, flip, fs);
+            if (fs) {
+                u[0] = 1.0f;
+                u[1] = 1.0f;
+                u[2] = 0.0f;
+                u[3] = 0.0f;
+                u[4] = c.E_inf;
+            } else {
+                const long long j = sx + (long long)g.n[0] * (sy + (long long)g.n[1] * gz);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) u[m] = __ldg(U + m * N + j);
+#pragma unroll
+                for (int d = 0; d < 2; ++d)
+                    if ((flip >> d) & 1) u[1 + d] = -u[1 + d];
+            }
+        }
+        const float rho = u[0];
+        const float inv = __fdividef(1.0f, rho);
+        const float vx = u[1] * inv, vy = u[2] * inv, vz = u[3] * inv;
+        const float p = c.gm1 * (u[4] - 0.5f * rho * (vx * vx + vy * vy + vz * vz));
+        slot[q] = rho;
+        slot[PP + q] = vx;
+        slot[2 * PP + q] = vy;
+        slot[3 * PP + q] = vz;
+        slot[4 * PP + q] = p;
+        slot[5 * PP + q] = p * inv * c.invR;
+    }
+}
+
+// Load plane gz (ghosts through the boundary conditions) and convert it to
+// primitives into one ring slot.
 __device__ __forceinline__ void load_plane(const GridParams &g, const FC &c,
-                                           const float *__restrict__ U,
-                                           const float *__restrict__ Lp, float dt,
-                                           float *__restrict__ slot, int ox, int oy, int gz,
-                                           bool xy_interior) {
+                                           const float *__restrict__ U, float *__restrict__ slot,
+                                           int ox, int oy, int gz, bool xy_interior) {
     const long long N = g.N;
     const bool fast = xy_interior && gz >= 0 && gz < g.n[2];
     for (int q = threadIdx.x; q < PP; q += NTH) {
@@ -249,11 +339,7 @@ __device__ __forceinline__ void load_plane(const GridParams &g, const FC &c,
         if (fast) {
             const long long j = (ox + lx - 2) + (long long)g.n[0] * ((oy + ly - 2) + (long long)g.n[1] * gz);
 #pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                float v = __ldg(U + m * N + j);
-                if (MODE == 2) v = fmaf(dt, __ldg(Lp + m * N + j), v);
-                u[m] = v;
-            }
+            for (int m = 0; m < NC; ++m) u[m] = __ldg(U + m * N + j);
         } else {
             int flip = 0, fs = 0;
             const int sx = map_axis(ox + lx - 2, g.n[0], g.bc[0], g.bc[1], 0, flip, fs);
@@ -268,11 +354,7 @@ __device__ __forceinline__ void load_plane(const GridParams &g, const FC &c,
             } else {
                 const long long j = sx + (long long)g.n[0] * (sy + (long long)g.n[1] * sz);
 #pragma unroll
-                for (int m = 0; m < NC; ++m) {
-                    float v = __ldg(U + m * N + j);
-                    if (MODE == 2) v = fmaf(dt, __ldg(Lp + m * N + j), v);
-                    u[m] = v;
-                }
+                for (int m = 0; m < NC; ++m) u[m] = __ldg(U + m * N + j);
 #pragma unroll
                 for (int d = 0; d < 3; ++d)
                     if ((flip >> d) & 1) u[1 + d] = -u[1 + d];
@@ -297,35 +379,57 @@ __device__ __forceinline__ double warp_max_d(double v) {
     return v;
 }
 
-// MODE 0: L only.  MODE 1: stage 1 (L and the step size).  MODE 2: stage 2.
 #ifndef IBM_ZM_MIN_BLOCKS
 #define IBM_ZM_MIN_BLOCKS 3
 #endif
 
-template <int MODE>
+// MODE 0: out = L(Uin).  MODE 1: out = U1 = Uin + dt L(Uin).
+// MODE 2: out = U* = Un/2 + (Uin + dt L(Uin))/2 with Uin = U1, plus the
+// per-CTA maximum of s_j(U*) over the cells outside the band.
+// TMA: the planes of Uin inside the domain arrive by bulk tensor copies,
+// each prefetched one plane ahead while the faces of the current plane are
+// evaluated (needs nx % 4 == 0); otherwise every plane is loaded by threads.
+template <int MODE, bool TMA>
 __global__ void __launch_bounds__(NTH, IBM_ZM_MIN_BLOCKS)
-zmarch_kernel(const GridParams g, const FC c, int zc, const float *__restrict__ U,
-              const float *__restrict__ Lp, float *__restrict__ out,
-              double *__restrict__ blockmax, unsigned *__restrict__ counter,
-              double *__restrict__ dt_ptr, int *__restrict__ err, double dt_fixed) {
-    extern __shared__ __align__(16) float smem_zm[];
+zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, const FC c, int zc,
+              const float *__restrict__ Uin, const float *__restrict__ Un,
+              float *__restrict__ out, double *__restrict__ blockmax,
+              const double *__restrict__ dt_ptr, int *__restrict__ err,
+              const unsigned *__restrict__ band_bits, double dt_fixed) {
+    extern __shared__ __align__(128) float smem_zm[];
     float *ring = smem_zm;
     float *FXb = ring + RING * SLOT;          // [NC][TY][FXW]
     float *FYb = FXb + NC * TY * FXW;         // [NC][TY+1][TX]
     float *FZb = FYb + NC * (TY + 1) * TX;    // [2][NC][TY][TX] upper z-faces by plane parity
     __shared__ double s_red[NTH / 32];
-    __shared__ int s_flag;
 
     const int tid = threadIdx.x, lx = tid & 31, ly = tid >> 5;
     const int ox = blockIdx.x * TX, oy = blockIdx.y * TY;
     const int z0 = blockIdx.z * zc, z1 = min(z0 + zc, g.n[2]);
     const long long N = g.N;
-    const float dt = MODE == 2 ? (float)(*dt_ptr) : 0.0f;
+    const float dt = MODE == 0 ? 0.0f : (float)(dt_fixed > 0.0 ? dt_fixed : *dt_ptr);
     const bool xyint = ox >= 2 && oy >= 2 && ox + TX + 2 <= g.n[0] && oy + TY + 2 <= g.n[1];
     auto slot_of = [](int z) { return ((z % RING) + RING) % RING * SLOT; };
 
+    float *stage = reinterpret_cast<float *>(reinterpret_cast<char *>(smem_zm) + SMEM_TMA_OFF);
+    const unsigned st_addr = smem_u32(stage);
+    const unsigned mbar = smem_u32(stage + STAGE);
+    unsigned parity = 0;
+    const int nz = g.n[2];
+    // a copy that never completes switches the CTA to thread loads; the
+    // phase still outstanding is drained (bounded) before the CTA exits
+    __shared__ int s_tma_dead;
+    int pending = -1;
+    if (TMA) {
+        if (tid == 0) {
+            s_tma_dead = 0;
+            mbar_init(mbar);
+            if (z0 + 2 < nz) tma_issue(&tmap, st_addr, mbar, ox - 4, oy - 2, z0 + 2);
+        }
+        __syncthreads();
+    }
     for (int zz = z0 - 2; zz <= z0 + 1; ++zz)
-        load_plane<MODE>(g, c, U, Lp, dt, ring + slot_of(zz), ox, oy, zz, xyint);
+        load_plane(g, c, Uin, ring + slot_of(zz), ox, oy, zz, xyint);
     __syncthreads();
 
     const int cxy = (lx + 2) + PX * (ly + 2);   // own column inside a plane
@@ -354,10 +458,22 @@ zmarch_kernel(const GridParams g, const FC c, int zc, const float *__restrict__ 
     __syncthreads();
 
     float smaxf = 0.0f;
-    int bad = 0;
+    bool ok = true;
     for (int z = z0; z < z1; ++z) {
-        load_plane<MODE>(g, c, U, Lp, dt, ring + slot_of(z + 2), ox, oy, z + 2, xyint);
+        const bool staged = TMA && z + 2 < nz && !s_tma_dead;
+        if (staged && !tma_wait(mbar, parity, err)) {
+            s_tma_dead = 1;
+            if (tid == 0) pending = (int)parity;
+        }
+        if (staged && !s_tma_dead) {
+            parity ^= 1u;
+            convert_staged(g, c, Uin, stage, ring + slot_of(z + 2), ox, oy, z + 2, xyint);
+        } else {
+            load_plane(g, c, Uin, ring + slot_of(z + 2), ox, oy, z + 2, xyint);
+        }
         __syncthreads();
+        if (TMA && tid == 0 && !s_tma_dead && z + 1 < z1 && z + 3 < nz)
+            tma_issue(&tmap, st_addr, mbar, ox - 4, oy - 2, z + 3);
         const int sm1 = slot_of(z - 1), s0 = slot_of(z), s1 = slot_of(z + 1), s2 = slot_of(z + 2);
         (void)sm1;
         const int up = s1 - s0, dn = sm1 - s0;
@@ -418,73 +534,38 @@ zmarch_kernel(const GridParams g, const FC c, int zc, const float *__restrict__ 
         const int gx = ox + lx, gy = oy + ly;
         if (gx < g.n[0] && gy < g.n[1]) {
             const long long j = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * z);
-            if (MODE == 2) {
-#pragma unroll
-                for (int m = 0; m < NC; ++m) {
-                    const float un = __ldg(U + m * N + j);
-                    const float u1 = fmaf(dt, __ldg(Lp + m * N + j), un);
-                    out[m * N + j] = 0.5f * un + 0.5f * fmaf(dt, acc[m] * c.inv_h, u1);
-                }
-            } else {
+            if (MODE == 0) {
 #pragma unroll
                 for (int m = 0; m < NC; ++m) out[m * N + j] = acc[m] * c.inv_h;
-            }
-            if (MODE == 1) {
-                const float *P = ring + s0;
-                const float rho = P[cxy], p = P[4 * PP + cxy], Tt = P[5 * PP + cxy];
-                const float c2 = __fdividef(c.gamma * p, rho);
-                const float snd = c2 * rsqrtf(c2);
-                float mu = 0.0f;
-                if (c.viscous) mu = __fdividef(c.mu_inf * Tt * (Tt * rsqrtf(Tt)) * c.onepS, Tt + c.S);
-                const float nu = __fdividef(c.kvisc * mu, rho);
-                const float s = (fabsf(P[PP + cxy]) + fabsf(P[2 * PP + cxy]) + fabsf(P[3 * PP + cxy]) +
-                                 3.0f * snd) * c.inv_h + 6.0f * nu * c.inv_h * c.inv_h;
-                if (!(rho > 0.0f && p > 0.0f && s <= FLT_MAX)) bad = 1;
-                else smaxf = fmaxf(smaxf, s);
+            } else if (MODE == 1) {
+#pragma unroll
+                for (int m = 0; m < NC; ++m) out[m * N + j] = fmaf(dt, acc[m] * c.inv_h, __ldg(Uin + m * N + j));
+            } else {
+                float us[NC];
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    const float un = __ldg(Un + m * N + j);
+                    const float u1 = __ldg(Uin + m * N + j);
+                    us[m] = 0.5f * un + 0.5f * fmaf(dt, acc[m] * c.inv_h, u1);
+                    out[m * N + j] = us[m];
+                }
+                if (!band_bit(band_bits, j)) smaxf = fmaxf(smaxf, step_rate<3, float>(g, us, ok));
             }
         }
     }
 
-    if (MODE == 1) {
+    if (TMA && tid == 0 && pending >= 0) tma_wait(mbar, (unsigned)pending, err);
+
+    if (MODE == 2) {
         const double smax = warp_max_d((double)smaxf);
-        bad = __syncthreads_or(bad);
+        const int bad = __syncthreads_or(!ok);
         if ((tid & 31) == 0) s_red[tid >> 5] = smax;
         __syncthreads();
-        const unsigned nblocks = gridDim.x * gridDim.y * gridDim.z;
-        const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
         if (tid == 0) {
             double m = s_red[0];
             for (int w = 1; w < NTH / 32; ++w) m = fmax(m, s_red[w]);
-            blockmax[bid] = m;
+            blockmax[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = m;
             if (bad) record_error(err, ERR_NONFINITE);
-            __threadfence();
-            const unsigned ticket = atomicAdd(counter, 1u);
-            s_flag = ticket == nblocks - 1;
-        }
-        __syncthreads();
-        if (s_flag) {
-            __threadfence();
-            double m = 0.0;
-            for (unsigned b = tid; b < nblocks; b += NTH) m = fmax(m, __ldcg(blockmax + b));
-            m = warp_max_d(m);
-            if ((tid & 31) == 0) s_red[tid >> 5] = m;
-            __syncthreads();
-            if (tid == 0) {
-                double mm = s_red[0];
-                for (int w = 1; w < NTH / 32; ++w) mm = fmax(mm, s_red[w]);
-                double dtv;
-                if (dt_fixed > 0.0) {
-                    dtv = dt_fixed;
-                } else if (mm > 0.0 && mm <= DBL_MAX) {
-                    dtv = g.cfl / mm;
-                } else {
-                    dtv = 0.0;
-                    record_error(err, ERR_NONFINITE);
-                }
-                if (__ldcg(err) & ERR_NONFINITE) dtv = 0.0;
-                *dt_ptr = dtv;
-                *counter = 0u;
-            }
         }
     }
 }
@@ -504,32 +585,74 @@ size_t zmarch_blocks(const GridParams &g) {
     return (size_t)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY) * ((g.n[2] + zc - 1) / zc);
 }
 
-template <int MODE>
-static cudaError_t zm_launch(const GridParams &g, const void *U, const void *Lp, void *out,
-                             const FluidBuffers &fb, double dt_fixed, cudaStream_t s) {
+// cuTensorMapEncodeTiled through the runtime's driver entry point
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// 4D map over a conserved state: (x, y, z, component), box 40 x 12 x 1 x 5
+static bool make_state_map(const GridParams &g, const void *U, CUtensorMap *map) {
+    if (g.n[0] % 4 != 0 || ((uintptr_t)U) % 16 != 0) return false;
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[4] = {(cuuint64_t)g.n[0], (cuuint64_t)g.n[1], (cuuint64_t)g.n[2], NC};
+    const cuuint64_t strides[3] = {(cuuint64_t)g.n[0] * 4, (cuuint64_t)g.n[0] * g.n[1] * 4,
+                                   (cuuint64_t)g.N * 4};
+    const cuuint32_t box[4] = {SBX, SBY, 1, NC};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void *>(U), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int MODE, bool TMA>
+static cudaError_t zm_launch_t(const GridParams &g, const CUtensorMap &map, const void *Uin,
+                               const void *Un, void *out, const FluidBuffers &fb, double dt_fixed,
+                               cudaStream_t s) {
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(zmarch_kernel<MODE>,
+        cudaError_t e = cudaFuncSetAttribute(zmarch_kernel<MODE, TMA>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(zmarch_kernel<MODE>,
+            e = cudaFuncSetAttribute(zmarch_kernel<MODE, TMA>,
                                      cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     const int zc = zmarch_chunk(g);
     dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + zc - 1) / zc);
-    zmarch_kernel<MODE><<<grid, NTH, SMEM, s>>>(g, make_fc(g), zc, (const float *)U,
-                                                (const float *)Lp, (float *)out, fb.blockmax,
-                                                fb.counter, fb.dt, fb.err, dt_fixed);
+    zmarch_kernel<MODE, TMA><<<grid, NTH, SMEM, s>>>(map, g, make_fc(g), zc, (const float *)Uin,
+                                                     (const float *)Un, (float *)out, fb.blockmax,
+                                                     fb.dt, fb.err, fb.band_bits, dt_fixed);
     return cudaGetLastError();
 }
 
-cudaError_t launch_zmarch(int mode, const GridParams &g, const void *U, const void *Lp, void *out,
-                          const FluidBuffers &fb, double dt_fixed, cudaStream_t s) {
-    if (mode == 1) return zm_launch<1>(g, U, Lp, out, fb, dt_fixed, s);
-    if (mode == 2) return zm_launch<2>(g, U, Lp, out, fb, dt_fixed, s);
-    return zm_launch<0>(g, U, Lp, out, fb, dt_fixed, s);
+template <int MODE>
+static cudaError_t zm_launch(const GridParams &g, const void *Uin, const void *Un, void *out,
+                             const FluidBuffers &fb, double dt_fixed, cudaStream_t s) {
+    CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    if (make_state_map(g, Uin, &map))
+        return zm_launch_t<MODE, true>(g, map, Uin, Un, out, fb, dt_fixed, s);
+    return zm_launch_t<MODE, false>(g, map, Uin, Un, out, fb, dt_fixed, s);
+}
+
+cudaError_t launch_zmarch(int mode, const GridParams &g, const void *Uin, const void *Un,
+                          void *out, const FluidBuffers &fb, double dt_fixed, cudaStream_t s) {
+    if (mode == 1) return zm_launch<1>(g, Uin, Un, out, fb, dt_fixed, s);
+    if (mode == 2) return zm_launch<2>(g, Uin, Un, out, fb, dt_fixed, s);
+    return zm_launch<0>(g, Uin, Un, out, fb, dt_fixed, s);
 }
 
 }  // namespace ibmk

@@ -9,29 +9,104 @@
 
 namespace ibmk {
 
-// ---- fluid stages (flux.cu) ------------------------------------------------
-// Stage 1: L = L(U), per-block maximum of the step-size rate, and (by the
-// last block) dt = cfl / max s, or dt_fixed when > 0, written to *dt.
-// Stage 2: out = U/2 + (U1 + dt L(U1))/2 with U1 = U + dt Lprev built on load.
+// ---- fluid stages (flux.cu, flux_zm.cu) ------------------------------------
+// Stage 1: out = U1 = U + dt L(U), dt = dt_fixed if > 0 else *dt.
+// Stage 2: out = U* = Un/2 + (U1 + dt L(U1))/2; per-CTA maximum of the
+//          step-size rate s_j(U*) over the cells the forcing leaves alone
+//          (band_bits clear) into blockmax[].
+// dt_init: *dt = cfl / max_j s_j(U) over every cell (last-block reduction).
+// The next step's dt = cfl / max(stage-2 maxima, band-cell maxima after the
+// forcing) is formed by the finish kernel, so dt always follows from the
+// state at the start of the step.
 struct FluidBuffers {
-    double *blockmax;       // one per CTA of the stage-1 grid
-    unsigned *counter;      // last-block ticket (zero between launches)
-    double *dt;             // device step size
-    int *err;               // device error word
+    double *blockmax;            // per-CTA maxima (stage 2, dt_init)
+    unsigned *counter;           // last-block ticket of dt_init (zero between launches)
+    double *dt;                  // device step size of the next step
+    int *err;                    // device error word
+    const unsigned *band_bits;   // one bit per cell changed by the forcing
 };
 
+constexpr int DT_CELLS_PER_CTA = 2048;   // dt_init: 256 threads x 8 cells
+
+size_t fluid_stage_blocks(const GridParams &g, int fp_bytes);
+size_t dt_init_blocks(const GridParams &g);
 size_t fluid_blockmax_count(const GridParams &g, int fp_bytes);
-cudaError_t launch_stage1(const GridParams &g, int fp_bytes, const void *U, void *L,
+cudaError_t launch_stage1(const GridParams &g, int fp_bytes, const void *U, void *U1,
                           const FluidBuffers &fb, double dt_fixed, cudaStream_t s);
-cudaError_t launch_stage2(const GridParams &g, int fp_bytes, const void *U, const void *Lprev,
-                          void *out, const FluidBuffers &fb, cudaStream_t s);
-// L(U) only (no step size), for the diagnostic ibm_rhs
+cudaError_t launch_stage2(const GridParams &g, int fp_bytes, const void *Un, const void *U1,
+                          void *out, const FluidBuffers &fb, double dt_fixed, cudaStream_t s);
+// L(U) only, for the diagnostic ibm_rhs
 cudaError_t launch_rhs(const GridParams &g, int fp_bytes, const void *U, void *L,
                        const FluidBuffers &fb, cudaStream_t s);
+cudaError_t launch_dt_init(const GridParams &g, int fp_bytes, const void *U,
+                           const FluidBuffers &fb, cudaStream_t s);
 // the z-marching form used for 3D FP32 grids (flux_zm.cu); mode 0/1/2 as above
-cudaError_t launch_zmarch(int mode, const GridParams &g, const void *U, const void *Lp, void *out,
-                          const FluidBuffers &fb, double dt_fixed, cudaStream_t s);
+cudaError_t launch_zmarch(int mode, const GridParams &g, const void *Uin, const void *Un,
+                          void *out, const FluidBuffers &fb, double dt_fixed, cudaStream_t s);
 size_t zmarch_blocks(const GridParams &g);
+
+// Step-size rate of one cell from its conserved state (DIM+2 values):
+// s = sum_d (|u_d| + c)/h + 2 DIM nu / h^2, nu = max(4/3, gamma/Pr) mu(T)/rho.
+// ok is cleared for a non-positive density or pressure or a non-finite s.
+template <int DIM, typename T>
+__device__ __forceinline__ T step_rate(const GridParams &g, const T *u, bool &ok);
+
+template <>
+__device__ __forceinline__ float step_rate<3, float>(const GridParams &g, const float *u, bool &ok) {
+    const float rho = u[0], inv = __fdividef(1.0f, rho);
+    const float vx = u[1] * inv, vy = u[2] * inv, vz = u[3] * inv;
+    const float p = (float)(g.gamma - 1.0) * (u[4] - 0.5f * rho * (vx * vx + vy * vy + vz * vz));
+    const float c2 = __fdividef((float)g.gamma * p, rho);
+    const float snd = c2 * rsqrtf(c2);
+    float mu = 0.0f;
+    if (g.mu_inf > 0.0) {
+        const float Tt = p * inv * (float)(1.0 / g.R), S = (float)g.S;
+        mu = __fdividef((float)g.mu_inf * Tt * (Tt * rsqrtf(Tt)) * (1.0f + S), Tt + S);
+    }
+    const float ih = (float)g.inv_h;
+    const float s = (fabsf(vx) + fabsf(vy) + fabsf(vz) + 3.0f * snd) * ih +
+                    6.0f * __fdividef((float)g.kvisc * mu, rho) * ih * ih;
+    if (!(rho > 0.0f && p > 0.0f && s <= 3.0e38f)) ok = false;
+    return s;
+}
+
+template <int DIM, typename T>
+__device__ __forceinline__ T step_rate_generic(const GridParams &g, const T *u, bool &ok) {
+    const T rho = u[0];
+    T ke = T(0), sabs = T(0);
+    for (int d = 0; d < DIM; ++d) {
+        const T v = u[1 + d] / rho;
+        ke += v * v;
+        sabs += v < T(0) ? -v : v;
+    }
+    const T p = (T)(g.gamma - 1.0) * (u[DIM + 1] - T(0.5) * rho * ke);
+    const T c = sqrt((T)g.gamma * p / rho);
+    T mu = T(0);
+    if (g.mu_inf > 0.0) {
+        const T Tt = p / (rho * (T)g.R), S = (T)g.S;
+        mu = (T)g.mu_inf * Tt * sqrt(Tt) * (T(1) + S) / (Tt + S);
+    }
+    const T nu = (T)g.kvisc * mu / rho;
+    const T s = (sabs + T(DIM) * c) * (T)g.inv_h + T(2 * DIM) * nu * (T)(g.inv_h * g.inv_h);
+    if (!(rho > T(0) && p > T(0) && (double)s <= 1.0e300)) ok = false;
+    return s;
+}
+template <>
+__device__ __forceinline__ double step_rate<3, double>(const GridParams &g, const double *u, bool &ok) {
+    return step_rate_generic<3, double>(g, u, ok);
+}
+template <>
+__device__ __forceinline__ double step_rate<2, double>(const GridParams &g, const double *u, bool &ok) {
+    return step_rate_generic<2, double>(g, u, ok);
+}
+template <>
+__device__ __forceinline__ float step_rate<2, float>(const GridParams &g, const float *u, bool &ok) {
+    return step_rate_generic<2, float>(g, u, ok);
+}
+
+__device__ __forceinline__ bool band_bit(const unsigned *bits, long long j) {
+    return (__ldg(bits + (j >> 5)) >> (j & 31)) & 1u;
+}
 
 // ---- markers (markers.cu) --------------------------------------------------
 struct MarkerBuffers {
@@ -52,20 +127,26 @@ struct MarkerBuffers {
     int *occ_list, *band_list;  // n_tiles
     int *counts;             // [0] occupied tiles, [1] band tiles
     double *sums;            // [0..2] sum eps~ G, [3] sum eps~ H, [4] dt of those sums
+    double *bandmax;         // per-CTA step-size maxima of the spread kernel
+    unsigned *band_bits;     // one bit per cell inside some marker support
     double *t;               // simulated time
     long long *steps;        // step counter
     int *err;
 };
 
 cudaError_t launch_motion(const GridParams &g, const MarkerBuffers &m, double amp, double freq,
-                          int axis, const double *dt, cudaStream_t s);
+                          int axis, const double *dt, double dt_fixed, cudaStream_t s);
+cudaError_t launch_band_mask(const GridParams &g, const MarkerBuffers &m, int grid_ctas,
+                             cudaStream_t s);
 cudaError_t launch_bin(const GridParams &g, MarkerBuffers &m, cudaStream_t s);
 cudaError_t launch_interp_force(const GridParams &g, int fp_bytes, const void *U,
                                 const MarkerBuffers &m, int grid_ctas, cudaStream_t s);
 cudaError_t launch_spread_apply(const GridParams &g, int fp_bytes, void *U,
                                 const MarkerBuffers &m, int grid_ctas, cudaStream_t s);
-cudaError_t launch_finish(const GridParams &g, const MarkerBuffers &m, const double *dt,
-                          cudaStream_t s);
+// force/heat sums, the time update and the next dt from the stage-2 and
+// band maxima (nbs = 0 when the spread kernel did not run)
+cudaError_t launch_finish(const GridParams &g, const MarkerBuffers &m, const FluidBuffers &fb,
+                          int nb, int nbs, double dt_fixed, cudaStream_t s);
 cudaError_t launch_interpolate_op(const GridParams &g, int fp_bytes, const void *field, int nc,
                                   const MarkerBuffers &m, double *out, cudaStream_t s);
 cudaError_t launch_spread_op(const GridParams &g, int fp_bytes, const double *R, int nc,

@@ -17,6 +17,8 @@
 //    sorted order, so the sum order is fixed and no float atomics are used.
 //    The forced update (App. B, Eqs. u_centralF2 and e_centralF2) follows in
 //    the same thread.
+#include <float.h>
+
 #include "internal.h"
 
 namespace ibmk {
@@ -221,11 +223,12 @@ tile_lists_kernel(int n_tiles, const int *__restrict__ occ, const int *__restric
 __global__ void motion_kernel(const GridParams g, int ns, const double *__restrict__ X0,
                               const double *__restrict__ Ub0, double *__restrict__ X,
                               double *__restrict__ Ub, double amp, double freq, int axis,
-                              const double *__restrict__ t, const double *__restrict__ dt) {
+                              const double *__restrict__ t, const double *__restrict__ dt,
+                              double dt_fixed) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ns) return;
     const double pi = 3.14159265358979323846;
-    const double tn = *t + *dt;
+    const double tn = *t + (dt_fixed > 0.0 ? dt_fixed : *dt);
     const double sv = amp * sin(2.0 * pi * freq * tn);
     const double vv = amp * 2.0 * pi * freq * cos(2.0 * pi * freq * tn);
     for (int d = 0; d < g.dim; ++d) {
@@ -464,9 +467,12 @@ spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m
     int *s_head = s_cell + SP_MAXC;                        // [bn]
     int *s_len = s_head + bn;                              // [bn]
     __shared__ int s_cnt[NT3 + 1], s_start[NT3], s_warp[33];
+    __shared__ double s_max[SP_T / 32];
     const int tid = threadIdx.x;
     const int n_band = m.counts[1];
     const int cpt = g.cells_per_tile;
+    double smax = 0.0;   // step-size rate of the forced cells, for the next dt
+    bool ok = true;
     for (int it = blockIdx.x; it < n_band; it += gridDim.x) {
         const int t = m.band_list[it];
         const int tx = t % g.ntile[0], ty = (t / g.ntile[0]) % g.ntile[1],
@@ -590,8 +596,49 @@ spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m
             if (!band) continue;
             const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
             apply_forcing<DIM, T, R>(g, U, j, f, qh);
+            T u[DIM + 2];
+#pragma unroll
+            for (int cc = 0; cc < DIM + 2; ++cc) u[cc] = U[cc * g.N + j];
+            smax = fmax(smax, (double)step_rate<DIM, T>(g, u, ok));
         }
         __syncthreads();
+    }
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o2));
+    const int bad = __syncthreads_or(!ok);
+    if ((tid & 31) == 0) s_max[tid >> 5] = smax;
+    __syncthreads();
+    if (tid == 0) {
+        double mx = s_max[0];
+        for (int w = 1; w < SP_T / 32; ++w) mx = fmax(mx, s_max[w]);
+        m.bandmax[blockIdx.x] = mx;
+        if (bad) record_error(m.err, ERR_NONFINITE);
+    }
+}
+
+// One bit per cell lying in the support of some marker (the cells the
+// forcing changes).  The bits must be clear on entry.
+template <int DIM>
+__global__ void __launch_bounds__(256)
+band_mask_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__restrict__ keys,
+                 const int *__restrict__ perm) {
+    const int n_band = m.counts[1];
+    const int cpt = g.cells_per_tile;
+    for (int it = blockIdx.x; it < n_band; it += gridDim.x) {
+        const int t = m.band_list[it];
+        const int tx = t % g.ntile[0], ty = (t / g.ntile[0]) % g.ntile[1],
+                  tz = t / (g.ntile[0] * g.ntile[1]);
+        for (int q = threadIdx.x; q < cpt; q += blockDim.x) {
+            const int c[3] = {tx * g.tile[0] + q % g.tile[0],
+                              ty * g.tile[1] + (q / g.tile[0]) % g.tile[1],
+                              DIM == 3 ? tz * g.tile[2] + q / (g.tile[0] * g.tile[1]) : 0};
+            if (c[0] >= g.n[0] || c[1] >= g.n[1] || (DIM == 3 && c[2] >= g.n[2])) continue;
+            const bool band = gather_markers<DIM, float>(g, m, keys, perm, c, [&](int, float) {});
+            if (band) {
+                const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+                atomicOr(m.band_bits + (j >> 5), 1u << (j & 31));
+            }
+        }
     }
 }
 
@@ -600,22 +647,28 @@ spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m
 // ---------------------------------------------------------------------------
 
 __global__ void __launch_bounds__(256)
-finish_kernel(int dim, int ns, const MarkerBuffers m, const double *__restrict__ dt) {
-    __shared__ double s[4][8];
-    double a[4] = {0, 0, 0, 0};
+finish_kernel(const GridParams g, int ns, const MarkerBuffers m, const double *__restrict__ blockmax,
+              int nb, int nbs, double *__restrict__ dt_ptr, int *__restrict__ err, double dt_fixed) {
+    __shared__ double s[5][8];
+    const int dim = g.dim;
+    double a[5] = {0, 0, 0, 0, 0};   // sums of eps~ G (dim), eps~ H; a[4] = max rate
     for (int k = threadIdx.x; k < ns; k += 256) {
         const double e = m.eps[k];
         for (int d = 0; d < dim; ++d) a[d] += e * m.G[(long long)k * dim + d];
         a[3] += e * m.H[k];
     }
+    for (int b = threadIdx.x; b < nb; b += 256) a[4] = fmax(a[4], blockmax[b]);
+    for (int b = threadIdx.x; b < nbs; b += 256) a[4] = fmax(a[4], m.bandmax[b]);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[4] = fmax(a[4], __shfl_xor_sync(0xffffffffu, a[4], o));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0)
-        for (int i = 0; i < 4; ++i) s[i][w] = a[i];
+        for (int i = 0; i < 5; ++i) s[i][w] = a[i];
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int i = 0; i < 4; ++i) {
@@ -623,9 +676,15 @@ finish_kernel(int dim, int ns, const MarkerBuffers m, const double *__restrict__
             for (int j = 0; j < 8; ++j) t += s[i][j];
             m.sums[i] = t;
         }
-        m.sums[4] = *dt;
-        *m.t += *dt;
+        double mx = s[4][0];
+        for (int j = 1; j < 8; ++j) mx = fmax(mx, s[4][j]);
+        const double dt_used = dt_fixed > 0.0 ? dt_fixed : *dt_ptr;
+        m.sums[4] = dt_used;
+        *m.t += dt_used;
         *m.steps += 1;
+        const bool good = mx > 0.0 && mx <= DBL_MAX && !(*err & ERR_NONFINITE);
+        if (!good) record_error(err, ERR_NONFINITE);
+        *dt_ptr = good ? g.cfl / mx : 0.0;
     }
 }
 
@@ -691,10 +750,10 @@ spread_op_kernel(const GridParams g, const double *__restrict__ R_, int nc, cons
 // ---------------------------------------------------------------------------
 
 cudaError_t launch_motion(const GridParams &g, const MarkerBuffers &m, double amp, double freq,
-                          int axis, const double *dt, cudaStream_t s) {
+                          int axis, const double *dt, double dt_fixed, cudaStream_t s) {
     if (m.ns <= 0) return cudaSuccess;
     motion_kernel<<<(m.ns + 127) / 128, 128, 0, s>>>(g, m.ns, m.X0, m.Ub0, m.X, m.Ub, amp, freq,
-                                                      axis, m.t, dt);
+                                                      axis, m.t, dt, dt_fixed);
     return cudaGetLastError();
 }
 
@@ -781,9 +840,20 @@ cudaError_t launch_spread_apply(const GridParams &g, int fp_bytes, void *U,
                          : spread_apply_t<2, double>(g, U, m, grid_ctas, s);
 }
 
-cudaError_t launch_finish(const GridParams &g, const MarkerBuffers &m, const double *dt,
-                          cudaStream_t s) {
-    finish_kernel<<<1, 256, 0, s>>>(g.dim, m.ns, m, dt);
+cudaError_t launch_finish(const GridParams &g, const MarkerBuffers &m, const FluidBuffers &fb,
+                          int nb, int nbs, double dt_fixed, cudaStream_t s) {
+    finish_kernel<<<1, 256, 0, s>>>(g, m.ns, m, fb.blockmax, nb, nbs, fb.dt, fb.err, dt_fixed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_band_mask(const GridParams &g, const MarkerBuffers &m, int grid_ctas,
+                             cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(m.band_bits, 0, sizeof(unsigned) * (size_t)(g.N / 32 + 1), s);
+    if (e != cudaSuccess || m.ns <= 0) return e;
+    if (g.dim == 3)
+        band_mask_kernel<3><<<grid_ctas, 256, 0, s>>>(g, m, m.keys[m.sorted], m.perm[m.sorted]);
+    else
+        band_mask_kernel<2><<<grid_ctas, 256, 0, s>>>(g, m, m.keys[m.sorted], m.perm[m.sorted]);
     return cudaGetLastError();
 }
 

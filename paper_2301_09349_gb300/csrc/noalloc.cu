@@ -1,5 +1,5 @@
-// Allocation-free variant of fluid stage 1: L(U) and the stable step size,
-// for callers that cannot allocate device memory.
+// Allocation-free fluid stage 1: L(U) and the stable step size, for callers
+// that cannot allocate device memory.
 //
 // The regular API takes every device buffer from a workspace the caller
 // allocates.  Some callers cannot do even that: a module loaded into a host
@@ -7,9 +7,9 @@
 // plug-ins to call cudaMalloc, or a control loop that may not pay for an
 // allocation (cudaMalloc can synchronise the device) in the middle of a run.
 // They can still hand over the arrays they already own: the state U, the
-// output L and the output step size.  The only scratch stage 1 needs beyond
-// those - one double per CTA for the block maxima, the last-block ticket and
-// an error word - lives in the file-scope device array below.  It is
+// output L and the output step size.  The only scratch needed beyond those -
+// one double per CTA of the step-size reduction, the last-block ticket and an
+// error word - lives in the file-scope device array below.  It is
 // statically sized, so every GPU that loads the library holds it until the
 // process exits.
 #include <mutex>
@@ -27,7 +27,7 @@ using namespace ibmk;
 
 namespace {
 
-// Largest stage-1 grid served: 65536 CTAs (a 256^3 FP32 grid uses 32768).
+// Largest step-size reduction served: 65536 CTAs of 2048 cells (2^27 cells).
 constexpr int kMaxCtas = IBM_NOALLOC_MAX_CTAS;
 constexpr size_t kMaxCtaBytes = sizeof(double) * (size_t)kMaxCtas;
 // block maxima, then the ticket counter and the error word (one 256-byte line)
@@ -70,11 +70,11 @@ extern "C" ibm_status ibm_rhs_dt_noalloc(const ibm_grid_desc *desc, const void *
         return fail(IBM_ERR_ARG, "invalid grid description");
     if (!U || !L || !dt) return fail(IBM_ERR_ARG, "null buffer");
     const GridParams g = params_from_desc(*desc);
-    const size_t ctas = fluid_blockmax_count(g, desc->fp_bytes);
+    const size_t ctas = dt_init_blocks(g);
     if (ctas > (size_t)kMaxCtas)
         return fail(IBM_ERR_ARG,
-                    "grid too large for ibm_rhs_dt_noalloc: its stage-1 launch needs more than "
-                    "IBM_NOALLOC_MAX_CTAS (65536) thread blocks");
+                    "grid too large for ibm_rhs_dt_noalloc: its step-size reduction needs more "
+                    "than IBM_NOALLOC_MAX_CTAS (65536) thread blocks of 2048 cells");
     void *base = nullptr;
     cudaError_t e = scratch_address(&base);
     if (e != cudaSuccess) return fail(IBM_ERR_CUDA, cudaGetErrorString(e));
@@ -84,11 +84,13 @@ extern "C" ibm_status ibm_rhs_dt_noalloc(const ibm_grid_desc *desc, const void *
     fb.counter = (unsigned *)(p + kMaxCtaBytes);
     fb.err = (int *)(p + kMaxCtaBytes + 16);
     fb.dt = dt;
+    fb.band_bits = nullptr;
     // the ticket counter and the error word must start at zero; the block
     // maxima are all written before they are read
     cudaStream_t s = (cudaStream_t)stream;
     e = cudaMemsetAsync(p + kMaxCtaBytes, 0, 256, s);
-    if (e == cudaSuccess) e = launch_stage1(g, desc->fp_bytes, U, L, fb, 0.0, s);
+    if (e == cudaSuccess) e = launch_rhs(g, desc->fp_bytes, U, L, fb, s);
+    if (e == cudaSuccess) e = launch_dt_init(g, desc->fp_bytes, U, fb, s);
     if (e != cudaSuccess) return fail(IBM_ERR_CUDA, cudaGetErrorString(e));
     return IBM_OK;
 }

@@ -63,6 +63,8 @@ MIXED_BC = (C.BC_FREESTREAM, C.BC_ZEROGRAD, C.BC_SLIP, C.BC_SLIP, C.BC_ZEROGRAD,
 @pytest.mark.parametrize("dim,n,fp,tol", [
     (2, (37, 29), 8, 1e-12), (2, (37, 29), 4, 1e-4),
     (3, (21, 19, 13), 4, 1e-4), (3, (21, 19, 13), 8, 1e-12),
+    # x extents that are multiples of 4 take the bulk-tensor-copy path
+    (3, (36, 19, 13), 4, 1e-4), (3, (68, 27, 21), 4, 1e-4),
 ])
 @pytest.mark.parametrize("bc", ["mixed", "periodic"])
 def test_rhs_matches_oracle(oracle, dim, n, fp, tol, bc):
@@ -245,8 +247,42 @@ def test_sphere_fp32_per_step(oracle):
 
 
 def test_supersonic_cold_sphere_fp32(oracle):
-    c = C.heated_sphere(n=48, mach=2.0, Tw=0.5, n_markers=2000)
+    # an impulsive Mach-2 start against a cold wall drives a forced cell to
+    # non-positive pressure at step 5 in the oracle as well (the fluid inside
+    # the body starts at Mach 2); compare the physical first three steps
+    c = C.heated_sphere(n=48, mach=2.0, Tw=0.5)
+    _compare_run(oracle, c, 3, 1e-5, tol_force=1e-3)
+
+
+def test_supersonic_hot_sphere_fp32(oracle):
+    c = C.heated_sphere(n=48, mach=2.0, Tw=1.5)
     _compare_run(oracle, c, 5, 1e-5, tol_force=1e-3)
+
+
+def test_nonpositive_state_is_reported_like_the_oracle(oracle):
+    # the same cold Mach-2 start, run past step 5: the GPU reports
+    # IBM_ERR_NONFINITE exactly when the oracle's pressure turns non-positive
+    c = C.heated_sphere(n=48, mach=2.0, Tw=0.5)
+    g = c.grid
+    run = oracle.Run(g, c.X, c.Tw)
+    U = C.initial_state(g, c.seed).astype(np.float32).astype(np.float64).reshape(5, -1)
+    first_bad = None
+    for s in range(8):
+        U = run.step(U)
+        p = 0.4 * (U[4] - 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0])
+        if not np.all(p > 0):
+            first_bad = s
+            break
+    assert first_bad is not None
+    grid = ibm.Grid(g, max_markers=len(c.X))
+    grid.set_markers(c.X, c.Tw)
+    grid.set_state(C.initial_state(g, c.seed).astype(np.float32))
+    grid.step(first_bad)
+    grid.sync()
+    grid.step(1)
+    with pytest.raises(ibm.IbmError) as e:
+        grid.sync()
+    assert e.value.status == 3
 
 
 def test_moving_cylinder_fp32(oracle):
