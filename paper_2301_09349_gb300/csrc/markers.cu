@@ -646,19 +646,21 @@ band_mask_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__re
 // forces/heat sums (fixed-order reduction) and the time update
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256)
+constexpr int FIN_T = 1024;
+
+__global__ void __launch_bounds__(FIN_T)
 finish_kernel(const GridParams g, int ns, const MarkerBuffers m, const double *__restrict__ blockmax,
               int nb, int nbs, double *__restrict__ dt_ptr, int *__restrict__ err, double dt_fixed) {
-    __shared__ double s[5][8];
+    __shared__ double s[5][FIN_T / 32];
     const int dim = g.dim;
     double a[5] = {0, 0, 0, 0, 0};   // sums of eps~ G (dim), eps~ H; a[4] = max rate
-    for (int k = threadIdx.x; k < ns; k += 256) {
-        const double e = m.eps[k];
-        for (int d = 0; d < dim; ++d) a[d] += e * m.G[(long long)k * dim + d];
-        a[3] += e * m.H[k];
+    for (int k = threadIdx.x; k < ns; k += FIN_T) {
+        const double e = __ldg(m.eps + k);
+        for (int d = 0; d < dim; ++d) a[d] += e * __ldg(m.G + (long long)k * dim + d);
+        a[3] += e * __ldg(m.H + k);
     }
-    for (int b = threadIdx.x; b < nb; b += 256) a[4] = fmax(a[4], blockmax[b]);
-    for (int b = threadIdx.x; b < nbs; b += 256) a[4] = fmax(a[4], m.bandmax[b]);
+    for (int b = threadIdx.x; b < nb; b += FIN_T) a[4] = fmax(a[4], __ldg(blockmax + b));
+    for (int b = threadIdx.x; b < nbs; b += FIN_T) a[4] = fmax(a[4], __ldg(m.bandmax + b));
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
 #pragma unroll
@@ -673,11 +675,11 @@ finish_kernel(const GridParams g, int ns, const MarkerBuffers m, const double *_
     if (threadIdx.x == 0) {
         for (int i = 0; i < 4; ++i) {
             double t = 0.0;
-            for (int j = 0; j < 8; ++j) t += s[i][j];
+            for (int j = 0; j < FIN_T / 32; ++j) t += s[i][j];
             m.sums[i] = t;
         }
         double mx = s[4][0];
-        for (int j = 1; j < 8; ++j) mx = fmax(mx, s[4][j]);
+        for (int j = 1; j < FIN_T / 32; ++j) mx = fmax(mx, s[4][j]);
         const double dt_used = dt_fixed > 0.0 ? dt_fixed : *dt_ptr;
         m.sums[4] = dt_used;
         *m.t += dt_used;
@@ -842,7 +844,7 @@ cudaError_t launch_spread_apply(const GridParams &g, int fp_bytes, void *U,
 
 cudaError_t launch_finish(const GridParams &g, const MarkerBuffers &m, const FluidBuffers &fb,
                           int nb, int nbs, double dt_fixed, cudaStream_t s) {
-    finish_kernel<<<1, 256, 0, s>>>(g, m.ns, m, fb.blockmax, nb, nbs, fb.dt, fb.err, dt_fixed);
+    finish_kernel<<<1, FIN_T, 0, s>>>(g, m.ns, m, fb.blockmax, nb, nbs, fb.dt, fb.err, dt_fixed);
     return cudaGetLastError();
 }
 
