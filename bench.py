@@ -2,6 +2,7 @@
 """Benchmark of the IBM step (3D heated sphere, 256^3 FP32).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload sphere|batched]
 
 One step = the whole hot path: fluid stage 1 (L(U^n), dt), fluid stage 2
 (SSP-RK2 predictor), interpolation + direct forcing at the markers,
@@ -14,6 +15,13 @@ no collective on the data path.  Rank 0 prints one JSON line.
 
 --impl reference times the FP64 CPU oracle on this host's cores on a slab
 sample of the same workload (rank 0 only).
+
+--workload batched times 64 independent 2D heated-cylinder cases of uneven
+size (128^2 to 512^2, 1 to 8 cylinders each) advanced as one batch: one
+persistent launch per stage over (case, tile) work items, the step replayed
+from a CUDA graph, tile shape and markers per block autotuned; the plain
+per-case loop of single-grid steps is timed beside it on the same cases.
+With N > 1 the cases are dealt out to the ranks (weak scaling).
 """
 from __future__ import annotations
 
@@ -47,6 +55,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target seconds of oracle work for the cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="sphere", choices=["sphere", "batched"])
     return p.parse_args()
 
 
@@ -347,9 +356,239 @@ def run_ours(args, rank, world, local):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# batched 2D cylinders
+# ---------------------------------------------------------------------------
+
+BATCH_METRIC = ("cell-updates/s of a batch of 64 uneven 2D heated-cylinder cases at 1 GB300 "
+                "(one launch per stage over all cases); speed-up over the per-case loop")
+
+
+def batch_cases(rank: int, world: int):
+    """the 64-case batch, cases dealt round-robin to the ranks"""
+    cs = C.batched_cylinders()
+    return [c for i, c in enumerate(cs) if i % world == rank]
+
+
+def batch_workload_name(cs) -> str:
+    sizes = sorted({c.grid.n[0] for c in cs})
+    return ("batch of %d 2D heated-cylinder cases FP32, n^2 cells with n in %s over "
+            "[-4,12]x[-8,8], 1-8 cylinders (D = 1) per case, %d markers, T_w~U[0.5,2], "
+            "Ma~U[0.1,0.5], Re~U[40,200]"
+            % (len(cs), sizes, sum(len(c.X) for c in cs)))
+
+
+def oracle_batch_rate(cs, target_s: float, threads: int):
+    """The oracle over the cases of the batch, one step each (set-up untimed),
+    until about target_s seconds of stepping have been spent."""
+    from oracle import oracle as O
+    O.build()
+    O.set_threads(threads)
+    cells, el, used = 0, 0.0, 0
+    for c in cs:
+        run = O.Run(c.grid, c.X, c.Tw)
+        U = C.initial_state(c.grid, c.seed).astype(np.float32).astype(np.float64)
+        t = time.perf_counter()
+        run.step(U)
+        el += time.perf_counter() - t
+        cells += c.grid.ncells
+        used += 1
+        if el >= target_s:
+            break
+    sample = "one step of each of the first %d of the %d cases (%d cells)" % (used, len(cs), cells)
+    return cells / el, {"seconds": el, "sample": sample, "ms_per_step": 1e3 * el}
+
+
+def run_reference_batched(args, rank, world):
+    if rank != 0:
+        return 0
+    cs = batch_cases(0, 1)
+    threads = os.cpu_count() or 1
+    target = max(30.0, min(150.0, 1.0 * (args.steps + args.warmup)))
+    rate, det = oracle_batch_rate(cs, target, threads)
+    line = {
+        "impl": "reference", "metric": BATCH_METRIC, "value": rate, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": det["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": batch_workload_name(cs) + "; " + det["sample"]},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": det["sample"]},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_batched(args, rank, world, local):
+    import torch
+    from paper_2301_09349_gb300 import build, ibm
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    cs = batch_cases(rank, world)
+    stream = torch.cuda.Stream()
+    b = ibm.Batch([c.grid for c in cs], [len(c.X) for c in cs], stream=stream)
+    kept = []
+    for cg, c in zip(b.cases, cs):
+        kept.append(cg.set_markers(c.X, c.Tw))
+        cg.set_state(C.initial_state(c.grid, c.seed).astype(np.float32))
+    N = float(sum(c.grid.ncells for c in cs))
+    tune_ms = b.autotune(reps=10)
+    tuning = b.tuning()
+
+    def timed(fn, steps):
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return e0.elapsed_time(e1)
+
+    b.step(args.warmup)
+    b.sync()
+    uuid = str(torch.cuda.get_device_properties(local).uuid)
+    gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    clocks = ClockSampler(gpu_id)
+    time.sleep(0.3)
+    ms = timed(b.step, args.steps)
+    clk = clocks.stop()
+    b.sync()
+
+    # the same steps launched kernel by kernel with event pairs: the split
+    ibm.ibm_batch_profile(b.h, True)
+    b.step(args.steps)
+    prof = ibm.ibm_batch_profile_read(b.h)
+    ibm.ibm_batch_profile(b.h, False)
+    b.sync()
+
+    # the plain per-case loop: one single-grid step per case per step
+    loop = []
+    for c in cs:
+        gr = ibm.Grid(c.grid, max_markers=len(c.X), stream=stream)
+        gr.set_markers(c.X, c.Tw)
+        gr.set_state(C.initial_state(c.grid, c.seed).astype(np.float32))
+        loop.append(gr)
+
+    def loop_steps(k):
+        for _ in range(k):
+            for gr in loop:
+                gr.step(1)
+
+    loop_steps(args.warmup)
+    ms_loop = timed(loop_steps, args.steps)
+    for gr in loop:
+        gr.sync()
+    for gr in loop:
+        gr.close()
+
+    # end to end through the C ABI with host buffers: per step the wall
+    # temperatures of every case go up from page-locked memory, the batch
+    # steps, and the forces of all cases come back in one read
+    Tw_pin = []
+    for cg, c in zip(b.cases, cs):
+        _, _, idx = cg.markers()
+        t = torch.empty(len(idx), dtype=torch.float64, pin_memory=True).numpy()
+        t[:] = c.Tw[idx]
+        Tw_pin.append(t)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for cg, t in zip(b.cases, Tw_pin):
+            ibm.ibm_set_wall_temperature(cg.h, t)
+        ibm.ibm_batch_step(b.h, 1)
+        res = ibm.ibm_batch_forces(b.h, len(cs))
+    e2e_s = time.perf_counter() - t0
+    barrier()
+
+    from paper_2301_09349_gb300 import replicas
+    ms_max, e2e_ms_max, cells_all, markers_all = replicas.reduce_timings(
+        dist, torch.device("cuda", local), ms, e2e_s * 1e3, N, float(sum(kept)))
+    loop_max, _, _, _ = replicas.reduce_timings(
+        dist, torch.device("cuda", local), ms_loop, 0.0, N, 0.0)
+
+    if rank == 0:
+        steps = args.steps
+        value = cells_all * steps / (ms_max * 1e-3)
+        nc, bpe = 4, 4
+        alg = {"stage1": 2 * nc * bpe * N, "stage2": 3 * nc * bpe * N}
+        peak, peak_kind = measured_peaks()
+        kernels = {}
+        total_ms = sum(v[0] for v in prof.values())
+        for name, (kms, nl) in prof.items():
+            if nl == 0:
+                continue
+            ent = {"launches": nl, "ms_per_launch": kms / nl, "share": kms / total_ms}
+            if name in alg:
+                ent["GB_per_s"] = alg[name] / (kms / nl * 1e-3) / 1e9
+            kernels[name] = ent
+        dom = max(("stage1", "stage2"), key=lambda k: prof[k][0])
+        dms = prof[dom][0] / prof[dom][1]
+        achieved = alg[dom] / (dms * 1e-3) / 1e9
+        line = {
+            "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": ms_max / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded free stream + 1e-3 density noise; circle markers)",
+            "config": {"workload": batch_workload_name(cs), "cases": len(cs),
+                       "cells": int(N), "markers_kept": int(sum(kept)),
+                       "tuning": tuning,
+                       "l2": "inputs larger than L2 (state %.0f MB + stage-1 buffer %.0f MB "
+                             "> 129 MB)" % (nc * bpe * N / 1e6, nc * bpe * N / 1e6)},
+            "per_case_loop": {"ms_per_step": loop_max / steps,
+                              "value": cells_all * steps / (loop_max * 1e-3),
+                              "launches_per_step": 5 * len(cs),
+                              "speedup_of_batch": loop_max / ms_max},
+            "autotune_ms": {"stage_ms_per_shape": list(map(float, tune_ms["stage_ms"])),
+                            "interp_ms_per_warps": list(map(float, tune_ms["interp_ms"]))},
+            "roofline": {"bound": "hbm", "kernel": "batch_" + dom, "achieved": achieved,
+                         "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None,
+                         "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
+                                        if peak_kind == "measured" else "fallback 6.8 TB/s",
+                         "algorithmic_bytes_per_launch": alg[dom]},
+            "kernels": kernels,
+            "gpu_launches": 5 * steps * world,
+            "e2e": {"value": cells_all * steps / (e2e_ms_max * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * int(sum(kept)),
+                    "d2h_bytes_per_step": 48 * len(cs),
+                    "path": "ibm_set_wall_temperature per case (pinned host) + ibm_batch_step + "
+                            "ibm_batch_forces per step"},
+            "clocks": clk,
+            "result": {"Cd_case0": float(res[0, 3]), "Nu_case0": float(res[0, 5])},
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            threads = os.cpu_count() or 1
+            rate, det = oracle_batch_rate(cs, args.cpu_seconds, threads)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads,
+                                    "kind": "oracle", "sample": det["sample"]}
+        print(json.dumps(line), flush=True)
+    b.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload == "batched":
+        if args.impl == "reference":
+            return run_reference_batched(args, rank, world)
+        return run_batched(args, rank, world, local)
     if args.impl == "reference":
         return run_reference(args, rank, world)
     return run_ours(args, rank, world, local)

@@ -245,6 +245,80 @@ ibm_status ibm_profile_read(ibm_grid *g, double *ms, long long *launches);
 ibm_status ibm_rhs_dt_noalloc(const ibm_grid_desc *desc, const void *U, void *L, double *dt,
                               void *stream);
 
+/* ---- batches of independent 2D grids ----------------------------------- */
+
+/* A batch advances many independent 2D cases (their own grid size, flow
+ * parameters, markers and step size) together: each stage of the step is one
+ * persistent kernel launch over a list of (case, tile) work items, so small
+ * grids do not each pay a launch and leave most of the GPU idle.  The method
+ * per case is exactly that of ibm_step (Sec. 2.1-2.2, App. B); a batch step
+ * gives bitwise the same states, step sizes and force sums as calling
+ * ibm_step on every case, for every tuning.  Static markers only.
+ *
+ * Each case is an ordinary ibm_grid owned by the batch (ibm_batch_case):
+ * set its state and markers, read its state, forces and time with the usual
+ * calls.  ibm_step on one case alone is allowed (the batch notices and
+ * rebuilds its tables); ibm_destroy on it is refused. */
+typedef struct ibm_batch ibm_batch;
+
+typedef struct {
+    int tile_shape;        /* fluid-stage tile: 0 = 16x16, 1 = 32x8, 2 = 64x4, 3 = 8x32 cells */
+    int markers_per_block; /* interpolation: warps (one marker each) per CTA, 1..16 */
+    int use_graph;         /* != 0: replay each step from a captured CUDA graph */
+} ibm_batch_tuning;
+
+/* Bytes of device workspace for ncases grids (descs[ncases], host) with the
+ * given marker capacities (max_markers[ncases], host; NULL = 0 each).  All
+ * cases must be 2D with the same fp_bytes.  0 if any argument is invalid. */
+size_t ibm_batch_workspace_bytes(int ncases, const ibm_grid_desc *descs, const int *max_markers);
+
+/* Create the batch and its ncases grids in one 256-byte aligned device
+ * workspace of at least ibm_batch_workspace_bytes bytes (caller-owned).
+ * All device work is ordered on `stream`.  Default tuning: shape 0, 4 warps,
+ * graphs on.  Errors: IBM_ERR_ARG, IBM_ERR_UNSUPPORTED (a 3D case or mixed
+ * fp_bytes), IBM_ERR_WORKSPACE, IBM_ERR_CUDA (message: ibm_batch_last_error(NULL)). */
+ibm_status ibm_create_batch(int ncases, const ibm_grid_desc *descs, const int *max_markers,
+                            void *dev_workspace, size_t bytes, void *stream, ibm_batch **out);
+ibm_status ibm_batch_destroy(ibm_batch *b);
+
+/* The grid of case c (owned by the batch; NULL if out of range). */
+ibm_grid *ibm_batch_case(ibm_batch *b, int c);
+
+/* nsteps steps of every case (dt_fixed as in ibm_step).  Every case needs a
+ * state; a case with moving markers gives IBM_ERR_UNSUPPORTED.  The first
+ * step after a marker change reads the cases' tile counts (synchronizes);
+ * otherwise asynchronous, five kernel launches (or one graph) per step. */
+ibm_status ibm_batch_step(ibm_batch *b, int nsteps, double dt_fixed);
+
+/* Synchronize and check every case's error word; on error *bad_case (may be
+ * NULL) is the first failing case and the status is that case's. */
+ibm_status ibm_batch_sync(ibm_batch *b, int *bad_case);
+
+/* Forces of all cases from one gathered device read: out[c*8 + i] for
+ * i = 0..7 holds Fx, Fy, Q, Cd, Cl, Nu, dt, t of case c (as
+ * ibm_forces_and_nusselt and ibm_get_time).  Synchronizes. */
+ibm_status ibm_batch_forces(ibm_batch *b, double *out);
+
+ibm_status ibm_batch_get_tuning(const ibm_batch *b, ibm_batch_tuning *t);
+ibm_status ibm_batch_set_tuning(ibm_batch *b, const ibm_batch_tuning *t);
+
+/* Time every tile shape (stage 1 + stage 2, reps passes each) and every
+ * markers-per-block choice (1, 2, 4, 8, 16 warps; reps interpolation passes)
+ * on the current states, keep the fastest of each, and return the measured
+ * milliseconds per pass in stage_ms[4] and interp_ms[5] (either may be NULL).
+ * The states, step sizes and last marker forcing are left unchanged; the
+ * tuning only changes speed, never results.  Synchronizes. */
+ibm_status ibm_batch_autotune(ibm_batch *b, int reps, double *stage_ms, double *interp_ms);
+
+/* Kernel timing of batch steps, as ibm_profile / ibm_profile_read (groups
+ * IBM_PROF_STAGE1, _STAGE2, _INTERP, _SPREAD, _FINISH; each counts one
+ * launch per step).  While it is enabled, steps are launched directly
+ * rather than replayed from graphs. */
+ibm_status ibm_batch_profile(ibm_batch *b, int enable);
+ibm_status ibm_batch_profile_read(ibm_batch *b, double *ms, long long *launches);
+
+const char *ibm_batch_last_error(const ibm_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,8 @@ SRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libibm_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-UNITS = ["flux.cu", "flux_zm.cu", "markers.cu", "quadrature.cu", "api.cu", "noalloc.cu"]
+UNITS = ["flux.cu", "flux_zm.cu", "markers.cu", "quadrature.cu", "api.cu", "noalloc.cu",
+         "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
 # extra nvcc flags (e.g. -DIBM_ZM_MIN_BLOCKS=2) for build variants

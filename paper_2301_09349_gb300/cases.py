@@ -232,6 +232,43 @@ def sphere_variants(n: int = 256) -> list:
     return out
 
 
+def batched_cylinders(ncases: int = 64, sizes: Sequence[int] = (128, 256, 384, 512),
+                      seed: int = 4, fp_bytes: int = 4) -> list:
+    """A batch of independent 2D heated-cylinder cases of uneven size (a
+    design-space sweep): case i draws, from PCG64(1000 * seed + i), a grid of
+    n^2 cells with n from `sizes` over [-4,12]x[-8,8] (h = 16/n), 1 to 8
+    cylinders of diameter 1 with centres uniform in [-2,6]x[-6,6] and every
+    two centres at least 1.5 + 4h apart (a gap of at least half a diameter
+    plus four cells), ceil(pi/h) markers per cylinder, T_w ~ U[0.5, 2],
+    Ma ~ U[0.1, 0.5], Re ~ U[40, 200].  The initial state's noise seed is the
+    case seed."""
+    out = []
+    for i in range(ncases):
+        cs = 1000 * seed + i
+        rng = np.random.Generator(np.random.PCG64(cs))
+        n = int(sizes[int(rng.integers(len(sizes)))])
+        h = 16.0 / n
+        ncyl = int(rng.integers(1, 9))
+        gap = 1.5 + 4.0 * h
+        centres = []
+        for _ in range(10000):
+            if len(centres) == ncyl:
+                break
+            c = (float(rng.uniform(-2.0, 6.0)), float(rng.uniform(-6.0, 6.0)))
+            if all(math.hypot(c[0] - q[0], c[1] - q[1]) >= gap for q in centres):
+                centres.append(c)
+        Tw = float(rng.uniform(0.5, 2.0))
+        mach = float(rng.uniform(0.1, 0.5))
+        Re = float(rng.uniform(40.0, 200.0))
+        g = GridDesc(dim=2, n=(n, n, 1), lo=(-4.0, -8.0, 0.0), h=h, fp_bytes=fp_bytes, Re=Re,
+                     Mach=mach, bc=_bc_for(2, mach), tile=(16, 16, 1))
+        nm = int(math.ceil(math.pi / h))
+        X = np.concatenate([circle_markers(nm, 0.5, c) for c in centres], axis=0)
+        out.append(Case(f"batch{seed}_case{i}_{n}^2_{len(centres)}cyl", g, X, np.full(len(X), Tw),
+                        None, None, 1000, cs))
+    return out
+
+
 def small_grid(dim: int, n: Sequence[int], h: float = 0.125, lo=None, fp_bytes: int = 8,
                bc=None, Re: float = 100.0, Mach: float = 0.3, tile=None) -> GridDesc:
     """A small grid for operator tests."""

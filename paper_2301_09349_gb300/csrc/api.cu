@@ -12,55 +12,10 @@
 #include <vector>
 
 #include "../../include/ibm.h"
+#include "handle.h"
 #include "internal.h"
 
 using namespace ibmk;
-
-struct ibm_grid {
-    ibm_grid_desc desc;
-    GridParams gp;
-    cudaStream_t stream = nullptr;
-    int device = 0;
-    int n_sm = 0;
-    int max_markers = 0;
-    char *ws = nullptr;
-    size_t ws_bytes = 0;
-
-    void *U[2] = {nullptr, nullptr};
-    int cur = 0;
-    void *L = nullptr;
-    FluidBuffers fb{};
-    MarkerBuffers mb{};
-    QuadBuffers qb{};
-    int *err_d = nullptr;
-    double *scratch_d = nullptr;   // small device scalars: dt, t
-
-    bool has_state = false;
-    bool moving = false;
-    ibm_motion motion{};
-    std::vector<int> kept;
-    std::vector<double> Tw_h;
-    int cg_maxit = 4000;
-    double cg_tol = 1e-12;
-    std::string err;
-
-    // kernel timing: event pairs recorded around kernel groups
-    struct ProfRec {
-        int group;
-        int launches;
-        size_t ev;   // index of the start event; the stop event follows
-    };
-    bool prof = false;
-    std::vector<cudaEvent_t> ev_pool;
-    size_t ev_used = 0;
-    std::vector<ProfRec> recs;
-    double prof_ms[IBM_PROF_GROUPS] = {0};
-    long long prof_n[IBM_PROF_GROUPS] = {0};
-
-    ~ibm_grid() {
-        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
-    }
-};
 
 namespace {
 
@@ -142,6 +97,7 @@ GridParams make_params(const ibm_grid_desc &d) {
     g.n_tiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
     g.cells_per_tile = g.tile[0] * g.tile[1] * g.tile[2];
     g.energy_reading = d.energy_reading;
+    g.f = float_consts(g);
     return g;
 }
 
@@ -315,6 +271,34 @@ ibm_status rebuild_markers(ibm_grid *g, int warm) {
 namespace ibmk {
 GridParams params_from_desc(const ibm_grid_desc &d) { return make_params(d); }
 void set_handle_free_error(const char *msg) { g_create_error = msg; }
+
+// Eq. Bulk: F_body = -h^d sum_k eps~_k F_k, Q_body = h^d sum_k eps~_k Q_k with
+// F = G/dt, Q = H/dt; coefficients and Nu as documented in include/ibm.h.
+void forces_from_sums(const ibm_grid *g, const double *sums, double force[3], double *heat_rate,
+                      double *Cd, double *Cl, double *Nu) {
+    const int dim = g->desc.dim;
+    const double hd = pow(g->desc.h, dim);
+    const double dt = sums[4];
+    double f[3] = {0, 0, 0}, q = 0.0;
+    if (dt > 0.0) {
+        for (int d = 0; d < dim; ++d) f[d] = -hd * sums[d] / dt;
+        q = hd * sums[3] / dt;
+    }
+    const double pi = 3.14159265358979323846;
+    const double Dr = g->desc.D;
+    const double lref = dim == 2 ? Dr : pi * Dr * Dr / 4.0;
+    const double As = dim == 2 ? pi * Dr : pi * Dr * Dr;
+    const double lam_inf = g->desc.Re > 0.0 ? g->gp.mu_inf * g->gp.cp / g->desc.Pr : 0.0;
+    double tw = 0.0;
+    for (double v : g->Tw_h) tw += v;
+    const double dT = (g->Tw_h.empty() ? 0.0 : tw / g->Tw_h.size()) - 1.0;
+    if (force)
+        for (int d = 0; d < 3; ++d) force[d] = f[d];
+    if (heat_rate) *heat_rate = q;
+    if (Cd) *Cd = 2.0 * f[0] / lref;
+    if (Cl) *Cl = 2.0 * f[1] / lref;
+    if (Nu) *Nu = (lam_inf > 0.0 && dT != 0.0) ? q * Dr / (lam_inf * As * dT) : NAN;
+}
 }  // namespace ibmk
 
 extern "C" {
@@ -382,6 +366,7 @@ ibm_status ibm_create_grid(const ibm_grid_desc *desc, int max_markers, void *dev
 
 ibm_status ibm_destroy(ibm_grid *g) {
     if (!g) return IBM_ERR_ARG;
+    if (g->in_batch) return fail(g, IBM_ERR_ARG, "this grid belongs to a batch: destroy the batch");
     delete g;
     return IBM_OK;
 }
@@ -519,6 +504,7 @@ ibm_status ibm_set_markers(ibm_grid *g, int n, const double *X0, const double *U
     g->mb.ns = ns;
     g->kept = keep;
     g->Tw_h = Twh;
+    ++g->marker_gen;
     g->moving = motion != nullptr;
     if (motion) g->motion = *motion;
     ibm_status st = rebuild_markers(g, 0);
@@ -627,28 +613,7 @@ ibm_status ibm_forces_and_nusselt(ibm_grid *g, double force[3], double *heat_rat
        "read force sums");
     ibm_status st = check_device(g);
     if (st != IBM_OK) return st;
-    const int dim = g->desc.dim;
-    const double hd = pow(g->desc.h, dim);
-    const double dt = sums[4];
-    double f[3] = {0, 0, 0}, q = 0.0;
-    if (dt > 0.0) {
-        for (int d = 0; d < dim; ++d) f[d] = -hd * sums[d] / dt;
-        q = hd * sums[3] / dt;
-    }
-    const double pi = 3.14159265358979323846;
-    const double Dr = g->desc.D;
-    const double lref = dim == 2 ? Dr : pi * Dr * Dr / 4.0;
-    const double As = dim == 2 ? pi * Dr : pi * Dr * Dr;
-    const double lam_inf = g->desc.Re > 0.0 ? g->gp.mu_inf * g->gp.cp / g->desc.Pr : 0.0;
-    double tw = 0.0;
-    for (double v : g->Tw_h) tw += v;
-    const double dT = (g->Tw_h.empty() ? 0.0 : tw / g->Tw_h.size()) - 1.0;
-    if (force)
-        for (int d = 0; d < 3; ++d) force[d] = f[d];
-    if (heat_rate) *heat_rate = q;
-    if (Cd) *Cd = 2.0 * f[0] / lref;
-    if (Cl) *Cl = 2.0 * f[1] / lref;
-    if (Nu) *Nu = (lam_inf > 0.0 && dT != 0.0) ? q * Dr / (lam_inf * As * dT) : NAN;
+    forces_from_sums(g, sums, force, heat_rate, Cd, Cl, Nu);
     return IBM_OK;
 }
 

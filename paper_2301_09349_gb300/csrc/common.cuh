@@ -21,6 +21,15 @@ enum : int {
 
 enum : int { BC_FREESTREAM = 0, BC_ZEROGRAD = 1, BC_SLIP = 2, BC_PERIODIC = 3 };
 
+// Single-precision copies of the gas and grid constants, each rounded once
+// from its double value on the host, for kernels that compute in FP32
+// (double arithmetic runs at a small fraction of the FP32 rate on this GPU,
+// so no FP32 kernel converts or divides doubles per cell or per face).
+struct FloatConsts {
+    float gamma, inv_gm1, gm1, invR, mu_inf, S, onepS, lam_fac, inv_h, qinv_h, kvisc, E_inf;
+    int viscous;
+};
+
 struct GridParams {
     int dim;
     int n[3];
@@ -38,7 +47,26 @@ struct GridParams {
     int n_tiles;
     int cells_per_tile;
     int energy_reading;
+    FloatConsts f;        // FP32 copies of the constants above
 };
+
+inline FloatConsts float_consts(const GridParams &g) {
+    FloatConsts c;
+    c.gamma = (float)g.gamma;
+    c.inv_gm1 = (float)(1.0 / (g.gamma - 1.0));
+    c.gm1 = (float)(g.gamma - 1.0);
+    c.invR = (float)(1.0 / g.R);
+    c.mu_inf = (float)g.mu_inf;
+    c.S = (float)g.S;
+    c.onepS = (float)(1.0 + g.S);
+    c.lam_fac = (float)(g.cp / g.Pr);
+    c.inv_h = (float)g.inv_h;
+    c.qinv_h = (float)(0.25 * g.inv_h);
+    c.kvisc = (float)g.kvisc;
+    c.E_inf = (float)(g.p_inf / (g.gamma - 1.0) + 0.5);
+    c.viscous = g.mu_inf > 0.0;
+    return c;
+}
 
 // The 1D regularised 3-point delta of Sec. 2.2 (Pinelli et al.); r in cells.
 __device__ __forceinline__ double phi_d(double r) {

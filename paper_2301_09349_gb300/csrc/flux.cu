@@ -24,18 +24,13 @@ namespace {
 
 constexpr int NT = 256;
 
-template <int DIM, typename T> struct TileShape;
-template <> struct TileShape<3, float> { static constexpr int BX = 8, BY = 8, BZ = 8; };
-template <> struct TileShape<3, double> { static constexpr int BX = 8, BY = 8, BZ = 4; };
-template <> struct TileShape<2, float> { static constexpr int BX = 16, BY = 16, BZ = 1; };
-template <> struct TileShape<2, double> { static constexpr int BX = 16, BY = 16, BZ = 1; };
-
 constexpr int cmax(int a, int b) { return a > b ? a : b; }
 
-template <int DIM, typename T>
-struct Box {
-    static constexpr int BX = TileShape<DIM, T>::BX, BY = TileShape<DIM, T>::BY,
-                         BZ = TileShape<DIM, T>::BZ;
+// A BX x BY x BZ tile of cells with its two-cell halo, 256 threads.
+template <int DIM_, typename T, int BX_, int BY_, int BZ_>
+struct BoxT {
+    static constexpr int DIM = DIM_;
+    static constexpr int BX = BX_, BY = BY_, BZ = DIM_ == 3 ? BZ_ : 1;
     static constexpr int PX = BX + 4, PY = BY + 4, PZ = DIM == 3 ? BZ + 4 : 1;
     static constexpr int PN = PX * PY * PZ;          // cells in tile + halo
     static constexpr int NC = DIM + 2;               // conserved components
@@ -49,6 +44,23 @@ struct Box {
     static constexpr int NFMAX = cmax(NF0, cmax(NF1, NF2));
     static constexpr size_t SMEM = sizeof(T) * (size_t)(NW * PN + NC * NFMAX);
 };
+
+// Tile of the single-grid kernels.
+template <int DIM, typename T> struct DefaultBox;
+template <> struct DefaultBox<3, float> { using type = BoxT<3, float, 8, 8, 8>; };
+template <> struct DefaultBox<3, double> { using type = BoxT<3, double, 8, 8, 4>; };
+template <> struct DefaultBox<2, float> { using type = BoxT<2, float, 16, 16, 1>; };
+template <> struct DefaultBox<2, double> { using type = BoxT<2, double, 16, 16, 1>; };
+template <int DIM, typename T> using Box = typename DefaultBox<DIM, T>::type;
+
+// 2D tile shapes of the batched kernel (all 256 cells): the autotuner's
+// choices.  Every face is evaluated by the same arithmetic whatever the
+// tile, so the shape changes the speed, never the result.
+template <typename T, int S> struct Shape2;
+template <typename T> struct Shape2<T, 0> { using type = BoxT<2, T, 16, 16, 1>; };
+template <typename T> struct Shape2<T, 1> { using type = BoxT<2, T, 32, 8, 1>; };
+template <typename T> struct Shape2<T, 2> { using type = BoxT<2, T, 64, 4, 1>; };
+template <typename T> struct Shape2<T, 3> { using type = BoxT<2, T, 8, 32, 1>; };
 
 // Arithmetic helpers.  FP32 uses the hardware approximations (MUFU
 // reciprocal / reciprocal square root, ~2 ulp), which are far inside the
@@ -68,16 +80,37 @@ __device__ __forceinline__ T van_leer(T a, T b) {
     return ab > T(0) ? fdiv<T>(T(2) * ab, a + b) : T(0);
 }
 
+// The constants of the face flux in the compute type: FP32 kernels read the
+// host-rounded copies, FP64 kernels the doubles (same values either way as
+// converting in the kernel).
+template <typename T> struct FluxK;
+template <> struct FluxK<float> {
+    float gam, inv_gm1, inv_h, S, mu_inf, lam_fac, gm1, invR, E_inf;
+    bool viscous;
+    __device__ __forceinline__ explicit FluxK(const GridParams &g)
+        : gam(g.f.gamma), inv_gm1(g.f.inv_gm1), inv_h(g.f.inv_h), S(g.f.S), mu_inf(g.f.mu_inf),
+          lam_fac(g.f.lam_fac), gm1(g.f.gm1), invR(g.f.invR), E_inf(g.f.E_inf),
+          viscous(g.f.viscous != 0) {}
+};
+template <> struct FluxK<double> {
+    double gam, inv_gm1, inv_h, S, mu_inf, lam_fac, gm1, invR, E_inf;
+    bool viscous;
+    __device__ __forceinline__ explicit FluxK(const GridParams &g)
+        : gam(g.gamma), inv_gm1(1.0 / (g.gamma - 1.0)), inv_h(g.inv_h), S(g.S), mu_inf(g.mu_inf),
+          lam_fac(g.cp / g.Pr), gm1(g.gamma - 1.0), invR(1.0 / g.R),
+          E_inf(g.p_inf / (g.gamma - 1.0) + 0.5), viscous(g.mu_inf > 0.0) {}
+};
+
 // Numerical flux through the face between box cells a and a + s_D.
-template <int DIM, typename T, int D>
-__device__ __forceinline__ void face_flux(const GridParams &g, const T *__restrict__ sW, int a,
-                                          T (&F)[DIM + 2]) {
-    using B = Box<DIM, T>;
+template <typename B, typename T, int D>
+__device__ __forceinline__ void face_flux(const FluxK<T> &k, const T *__restrict__ sW, int a,
+                                          T (&F)[B::DIM + 2]) {
+    constexpr int DIM = B::DIM;
     constexpr int s = D == 0 ? B::SX : (D == 1 ? B::SY : B::SZ);
     constexpr int NC = DIM + 2;
     const int b = a + s;
-    const T gam = (T)g.gamma;
-    const T inv_gm1 = (T)(1.0 / (g.gamma - 1.0));
+    const T gam = k.gam;
+    const T inv_gm1 = k.inv_gm1;
 
     // MUSCL reconstruction of (rho, u.., p) with the van Leer limiter
     T wl[NC], wr[NC];
@@ -115,17 +148,17 @@ __device__ __forceinline__ void face_flux(const GridParams &g, const T *__restri
     F[NC - 1] = T(0.5) * ((EL + wl[NC - 1]) * unL + (ER + wr[NC - 1]) * unR) -
                 T(0.5) * smax * (ER - EL);
 
-    if (g.mu_inf <= 0.0) return;
+    if (!k.viscous) return;
 
     // viscous stress and heat flux; face values from the two adjacent cells,
     // tangential derivatives from the average of the two cells' central
     // differences
-    const T inv_h = (T)g.inv_h;
+    const T inv_h = k.inv_h;
     const T *Tc = sW + (DIM + 2) * B::PN;
     const T Tf = T(0.5) * (Tc[a] + Tc[b]);
-    const T Sv = (T)g.S;
-    const T mu = fdiv<T>((T)g.mu_inf * Tf * psqrt<T>(Tf) * (T(1) + Sv), Tf + Sv);
-    const T lam = mu * (T)(g.cp / g.Pr);
+    const T Sv = k.S;
+    const T mu = fdiv<T>(k.mu_inf * Tf * psqrt<T>(Tf) * (T(1) + Sv), Tf + Sv);
+    const T lam = mu * k.lam_fac;
     T grad[DIM][DIM];
 #pragma unroll
     for (int m = 0; m < DIM; ++m) {
@@ -158,11 +191,10 @@ __device__ __forceinline__ void face_flux(const GridParams &g, const T *__restri
 
 // One direction: evaluate all faces of the tile normal to axis D, then add
 // each cell's flux difference to its accumulator.
-template <int DIM, typename T, int D>
-__device__ __forceinline__ void direction_pass(const GridParams &g, const T *__restrict__ sW,
-                                               T *__restrict__ sF,
-                                               T (&acc)[Box<DIM, T>::CPT][DIM + 2]) {
-    using B = Box<DIM, T>;
+template <typename B, typename T, int D>
+__device__ __forceinline__ void direction_pass(const FluxK<T> &k, const T *__restrict__ sW,
+                                               T *__restrict__ sF, T (&acc)[B::CPT][B::DIM + 2]) {
+    constexpr int DIM = B::DIM;
     constexpr int NC = DIM + 2;
     constexpr int dx = D == 0, dy = D == 1, dz = (D == 2 && DIM == 3);
     constexpr int FX = B::BX + dx, FY = B::BY + dy, FZ = B::BZ + dz;
@@ -175,7 +207,7 @@ __device__ __forceinline__ void direction_pass(const GridParams &g, const T *__r
         const int a = (fx - dx + 2) + B::PX * (fy - dy + 2) +
                       (DIM == 3 ? B::PX * B::PY * (fz - dz + 2) : 0);
         T F[NC];
-        face_flux<DIM, T, D>(g, sW, a, F);
+        face_flux<B, T, D>(k, sW, a, F);
 #pragma unroll
         for (int c = 0; c < NC; ++c) sF[c * B::NFMAX + f] = F[c];
     }
@@ -202,28 +234,26 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-// MODE 0: out = L(Uin).  MODE 1: out = U1 = Uin + dt L(Uin).
-// MODE 2: out = U* = Un/2 + (Uin + dt L(Uin))/2 with Uin = U1, plus the
-// per-CTA maximum of s_j(U*) over the cells outside the band.
-template <int DIM, typename T, int MODE>
-__global__ void __launch_bounds__(NT)
-stage_kernel(const GridParams g, const T *__restrict__ Uin, const T *__restrict__ Un,
-             T *__restrict__ out, double *__restrict__ blockmax, const double *__restrict__ dt_ptr,
-             int *__restrict__ err, const unsigned *__restrict__ band_bits, double dt_fixed) {
-    using B = Box<DIM, T>;
+// One tile of one stage.  MODE 0: out = L(Uin).  MODE 1: out = U1 = Uin +
+// dt L(Uin).  MODE 2: out = U* = Un/2 + (Uin + dt L(Uin))/2 with Uin = U1,
+// and the maximum of s_j(U*) over the tile's cells outside the band is
+// returned to thread 0 (every thread must call; the function synchronises).
+template <typename B, typename T, int MODE>
+__device__ __forceinline__ double stage_tile(const GridParams &g, int ox, int oy, int oz,
+                                             const T *__restrict__ Uin, const T *__restrict__ Un,
+                                             T *__restrict__ out, const T dt,
+                                             const unsigned *__restrict__ band_bits,
+                                             unsigned char *smem_raw, double *s_red, bool &bad) {
+    constexpr int DIM = B::DIM;
     constexpr int NC = DIM + 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sW = reinterpret_cast<T *>(smem_raw);
     T *sF = sW + B::NW * B::PN;
-    __shared__ double s_red[NT / 32];
 
     const int tid = threadIdx.x;
-    const int ox = blockIdx.x * B::BX, oy = blockIdx.y * B::BY;
-    const int oz = DIM == 3 ? blockIdx.z * B::BZ : 0;
     const long long N = g.N;
-    const T dt = MODE == 0 ? T(0) : (T)(dt_fixed > 0.0 ? dt_fixed : *dt_ptr);
-    const T gm1 = (T)(g.gamma - 1.0);
-    const T invR = (T)(1.0 / g.R);
+    const FluxK<T> k(g);
+    const T gm1 = k.gm1;
+    const T invR = k.invR;
 
     // ---- load tile + halo, to primitives
     // Tiles whose halo lies inside the domain index directly; the others map
@@ -231,7 +261,7 @@ stage_kernel(const GridParams g, const T *__restrict__ Uin, const T *__restrict_
     const bool interior = ox >= 2 && oy >= 2 && ox + B::BX + 2 <= g.n[0] &&
                           oy + B::BY + 2 <= g.n[1] &&
                           (DIM == 2 || (oz >= 2 && oz + B::BZ + 2 <= g.n[2]));
-    const T p_inf_E = (T)(g.p_inf / (g.gamma - 1.0) + 0.5);
+    const T p_inf_E = k.E_inf;
     for (int q = tid; q < B::PN; q += NT) {
         const int lx = q % B::PX;
         const int r = q / B::PX;
@@ -285,13 +315,13 @@ stage_kernel(const GridParams g, const T *__restrict__ Uin, const T *__restrict_
     for (int i = 0; i < B::CPT; ++i)
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[i][c] = T(0);
-    direction_pass<DIM, T, 0>(g, sW, sF, acc);
-    direction_pass<DIM, T, 1>(g, sW, sF, acc);
-    if constexpr (DIM == 3) direction_pass<DIM, T, 2>(g, sW, sF, acc);
+    direction_pass<B, T, 0>(k, sW, sF, acc);
+    direction_pass<B, T, 1>(k, sW, sF, acc);
+    if constexpr (DIM == 3) direction_pass<B, T, 2>(k, sW, sF, acc);
 
     // ---- outputs
-    const T inv_h = (T)g.inv_h;
-    double smax = 0.0;
+    const T inv_h = k.inv_h;
+    T smax_t = T(0);   // in the compute type: one conversion per tile, not per cell
     bool ok = true;
 #pragma unroll
     for (int i = 0; i < B::CPT; ++i) {
@@ -320,21 +350,69 @@ stage_kernel(const GridParams g, const T *__restrict__ Uin, const T *__restrict_
             }
             if (!band_bit(band_bits, j)) {
                 const T sj = step_rate<DIM, T>(g, us, ok);
-                smax = fmax(smax, (double)sj);
+                smax_t = fmax(smax_t, sj);
             }
         }
     }
 
     if (MODE == 2) {
-        smax = warp_max(smax);
-        const int bad = __syncthreads_or(!ok);
+        double smax = warp_max((double)smax_t);
+        bad = __syncthreads_or(!ok) != 0;
         if ((tid & 31) == 0) s_red[tid >> 5] = smax;
         __syncthreads();
-        if (tid == 0) {
-            double m = s_red[0];
-            for (int w = 1; w < NT / 32; ++w) m = fmax(m, s_red[w]);
-            blockmax[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = m;
-            if (bad) record_error(err, ERR_NONFINITE);
+        double m = s_red[0];
+        for (int w = 1; w < NT / 32; ++w) m = fmax(m, s_red[w]);
+        return m;
+    }
+    return 0.0;
+}
+
+template <int DIM, typename T, int MODE>
+__global__ void __launch_bounds__(NT)
+stage_kernel(const GridParams g, const T *__restrict__ Uin, const T *__restrict__ Un,
+             T *__restrict__ out, double *__restrict__ blockmax, const double *__restrict__ dt_ptr,
+             int *__restrict__ err, const unsigned *__restrict__ band_bits, double dt_fixed) {
+    using B = Box<DIM, T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double s_red[NT / 32];
+    const int ox = blockIdx.x * B::BX, oy = blockIdx.y * B::BY;
+    const int oz = DIM == 3 ? blockIdx.z * B::BZ : 0;
+    const T dt = MODE == 0 ? T(0) : (T)(dt_fixed > 0.0 ? dt_fixed : *dt_ptr);
+    bool bad = false;
+    const double m = stage_tile<B, T, MODE>(g, ox, oy, oz, Uin, Un, out, dt, band_bits, smem_raw,
+                                            s_red, bad);
+    if (MODE == 2 && threadIdx.x == 0) {
+        blockmax[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = m;
+        if (bad) record_error(err, ERR_NONFINITE);
+    }
+}
+
+// The same stages over a batch of 2D grids: one persistent launch walks a
+// list of (case, tile) work items; every case keeps its own parameters,
+// state, step size and error word.  MODE 2 writes one maximum per item.
+// FP32: six CTAs per SM (40 registers), as the single-grid 2D kernel gets.
+template <typename T, int S, int MODE>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 6 : 1)
+batch_stage_kernel(const BatchCase *__restrict__ cases, const int2 *__restrict__ items,
+                   int n_items, double *__restrict__ item_max, double dt_fixed) {
+    using B = typename Shape2<T, S>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double s_red[NT / 32];
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int2 w = items[it];
+        const BatchCase &bc = cases[w.x];
+        const GridParams g = bc.g;
+        const int ntx = (g.n[0] + B::BX - 1) / B::BX;
+        const int ox = (w.y % ntx) * B::BX, oy = (w.y / ntx) * B::BY;
+        const T dt = MODE == 0 ? T(0) : (T)(dt_fixed > 0.0 ? dt_fixed : *bc.dt);
+        const T *Uin = (const T *)(MODE == 2 ? bc.U1 : bc.Un);
+        T *out = (T *)(MODE == 2 ? bc.Us : bc.U1);
+        bool bad = false;
+        const double m = stage_tile<B, T, MODE>(g, ox, oy, 0, Uin, (const T *)bc.Un, out, dt,
+                                                bc.band_bits, smem_raw, s_red, bad);
+        if (MODE == 2 && threadIdx.x == 0) {
+            item_max[it] = m;
+            if (bad) record_error(bc.err, ERR_NONFINITE);
         }
     }
 }
@@ -425,7 +503,63 @@ cudaError_t dispatch(const GridParams &g, int fp_bytes, const void *Uin, const v
     return launch_one<2, double, MODE>(g, Uin, Un, out, fb, dt_fixed, s);
 }
 
+template <typename T, int S, int MODE>
+cudaError_t batch_stage_t(const BatchCase *cases, const int2 *items, int n_items,
+                          double *item_max, double dt_fixed, int n_sm, cudaStream_t s) {
+    using B = typename Shape2<T, S>::type;
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<T, S, MODE>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)B::SMEM);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, batch_stage_kernel<T, S, MODE>, NT, B::SMEM);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+    }
+    long long ctas = (long long)per_sm * (n_sm > 0 ? n_sm : 1);
+    if (ctas > n_items) ctas = n_items;
+    if (ctas < 1) return cudaSuccess;
+    batch_stage_kernel<T, S, MODE><<<(unsigned)ctas, NT, B::SMEM, s>>>(cases, items, n_items,
+                                                                        item_max, dt_fixed);
+    return cudaGetLastError();
+}
+
+template <typename T, int MODE>
+cudaError_t batch_stage_shape(int shape, const BatchCase *cases, const int2 *items, int n_items,
+                              double *item_max, double dt_fixed, int n_sm, cudaStream_t s) {
+    switch (shape) {
+    case 0: return batch_stage_t<T, 0, MODE>(cases, items, n_items, item_max, dt_fixed, n_sm, s);
+    case 1: return batch_stage_t<T, 1, MODE>(cases, items, n_items, item_max, dt_fixed, n_sm, s);
+    case 2: return batch_stage_t<T, 2, MODE>(cases, items, n_items, item_max, dt_fixed, n_sm, s);
+    case 3: return batch_stage_t<T, 3, MODE>(cases, items, n_items, item_max, dt_fixed, n_sm, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 }  // namespace
+
+void batch_tile_shape(int shape, int *bx, int *by) {
+    static const int X[kBatchShapes] = {16, 32, 64, 8}, Y[kBatchShapes] = {16, 8, 4, 32};
+    *bx = X[shape];
+    *by = Y[shape];
+}
+
+cudaError_t launch_batch_stage(int mode, int shape, int fp_bytes, const BatchCase *cases,
+                               const int2 *items, int n_items, double *item_max, double dt_fixed,
+                               int n_sm, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    if (mode == 1)
+        return fp_bytes == 4
+                   ? batch_stage_shape<float, 1>(shape, cases, items, n_items, item_max, dt_fixed, n_sm, s)
+                   : batch_stage_shape<double, 1>(shape, cases, items, n_items, item_max, dt_fixed, n_sm, s);
+    if (mode == 2)
+        return fp_bytes == 4
+                   ? batch_stage_shape<float, 2>(shape, cases, items, n_items, item_max, dt_fixed, n_sm, s)
+                   : batch_stage_shape<double, 2>(shape, cases, items, n_items, item_max, dt_fixed, n_sm, s);
+    return cudaErrorInvalidValue;
+}
 
 size_t fluid_stage_blocks(const GridParams &g, int fp_bytes) {
     dim3 d;

@@ -44,10 +44,7 @@ constexpr size_t SMEM_TMA_OFF = (SMEM_BASE + 127) / 128 * 128;
 constexpr size_t SMEM = SMEM_TMA_OFF + sizeof(float) * STAGE + 16;   // + mbarrier
 constexpr long long TMA_WAIT_LIMIT = 1ll << 20;          // bounded mbarrier waits
 
-struct FC {
-    float gamma, inv_gm1, gm1, invR, mu_inf, S, onepS, lam_fac, inv_h, qinv_h, kvisc, E_inf;
-    int viscous;
-};
+using FC = FloatConsts;
 
 // step-size rate of one cell from its conserved state, single precision
 // throughout (same formula as the shared step_rate helper)
@@ -68,23 +65,7 @@ __device__ __forceinline__ float rate_f(const FC &c, const float *u, bool &ok) {
     return s;
 }
 
-FC make_fc(const GridParams &g) {
-    FC c;
-    c.gamma = (float)g.gamma;
-    c.inv_gm1 = (float)(1.0 / (g.gamma - 1.0));
-    c.gm1 = (float)(g.gamma - 1.0);
-    c.invR = (float)(1.0 / g.R);
-    c.mu_inf = (float)g.mu_inf;
-    c.S = (float)g.S;
-    c.onepS = (float)(1.0 + g.S);
-    c.lam_fac = (float)(g.cp / g.Pr);
-    c.inv_h = (float)g.inv_h;
-    c.qinv_h = (float)(0.25 * g.inv_h);
-    c.kvisc = (float)g.kvisc;
-    c.E_inf = (float)(g.p_inf / (g.gamma - 1.0) + 0.5);
-    c.viscous = g.mu_inf > 0.0;
-    return c;
-}
+FC make_fc(const GridParams &g) { return float_consts(g); }
 
 // ---- packed pairs: the x-face (.x) and the y-face (.y) of one thread ------
 // Both faces run the same arithmetic once their velocity components are

@@ -51,23 +51,34 @@ size_t zmarch_blocks(const GridParams &g);
 template <int DIM, typename T>
 __device__ __forceinline__ T step_rate(const GridParams &g, const T *u, bool &ok);
 
-template <>
-__device__ __forceinline__ float step_rate<3, float>(const GridParams &g, const float *u, bool &ok) {
+// FP32 grids: single precision throughout, from the host-rounded constants.
+template <int DIM>
+__device__ __forceinline__ float step_rate_f(const GridParams &g, const float *u, bool &ok) {
+    const FloatConsts &c = g.f;
     const float rho = u[0], inv = __fdividef(1.0f, rho);
-    const float vx = u[1] * inv, vy = u[2] * inv, vz = u[3] * inv;
-    const float p = (float)(g.gamma - 1.0) * (u[4] - 0.5f * rho * (vx * vx + vy * vy + vz * vz));
-    const float c2 = __fdividef((float)g.gamma * p, rho);
+    float ke = 0.0f, sabs = 0.0f;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const float v = u[1 + d] * inv;
+        ke += v * v;
+        sabs += fabsf(v);
+    }
+    const float p = c.gm1 * (u[DIM + 1] - 0.5f * rho * ke);
+    const float c2 = c.gamma * p * inv;
     const float snd = c2 * rsqrtf(c2);
     float mu = 0.0f;
-    if (g.mu_inf > 0.0) {
-        const float Tt = p * inv * (float)(1.0 / g.R), S = (float)g.S;
-        mu = __fdividef((float)g.mu_inf * Tt * (Tt * rsqrtf(Tt)) * (1.0f + S), Tt + S);
+    if (c.viscous) {
+        const float Tt = p * inv * c.invR;
+        mu = __fdividef(c.mu_inf * Tt * (Tt * rsqrtf(Tt)) * c.onepS, Tt + c.S);
     }
-    const float ih = (float)g.inv_h;
-    const float s = (fabsf(vx) + fabsf(vy) + fabsf(vz) + 3.0f * snd) * ih +
-                    6.0f * __fdividef((float)g.kvisc * mu, rho) * ih * ih;
+    const float s = (sabs + (float)DIM * snd) * c.inv_h +
+                    (float)(2 * DIM) * (c.kvisc * mu * inv) * c.inv_h * c.inv_h;
     if (!(rho > 0.0f && p > 0.0f && s <= 3.0e38f)) ok = false;
     return s;
+}
+template <>
+__device__ __forceinline__ float step_rate<3, float>(const GridParams &g, const float *u, bool &ok) {
+    return step_rate_f<3>(g, u, ok);
 }
 
 template <int DIM, typename T>
@@ -101,7 +112,7 @@ __device__ __forceinline__ double step_rate<2, double>(const GridParams &g, cons
 }
 template <>
 __device__ __forceinline__ float step_rate<2, float>(const GridParams &g, const float *u, bool &ok) {
-    return step_rate_generic<2, float>(g, u, ok);
+    return step_rate_f<2>(g, u, ok);
 }
 
 __device__ __forceinline__ bool band_bit(const unsigned *bits, long long j) {
@@ -151,6 +162,44 @@ cudaError_t launch_interpolate_op(const GridParams &g, int fp_bytes, const void 
                                   const MarkerBuffers &m, double *out, cudaStream_t s);
 cudaError_t launch_spread_op(const GridParams &g, int fp_bytes, const double *R, int nc,
                              const MarkerBuffers &m, void *out, cudaStream_t s);
+
+// ---- batches of 2D grids (batch.cu drives; kernels in flux.cu, markers.cu) --
+// One case of a batch as the batched kernels see it.  Two tables exist, one
+// per step parity, so that Un and Us swap without rewriting the table.
+struct BatchCase {
+    GridParams g;
+    const void *Un;              // state at the start of the step
+    void *Us;                    // state at the end of the step (stage 2 output, forced in place)
+    void *U1;                    // stage-1 output
+    double *dt;                  // this case's step size
+    int *err;                    // this case's error word
+    const unsigned *band_bits;   // this case's band mask
+    MarkerBuffers m;             // this case's markers
+    int item0, nitems;           // its (case, tile) stage items, for the tile shape in use
+    int band0, nband;            // its (case, band tile) spread items
+};
+
+constexpr int kBatchShapes = 4;   // 2D tile shapes of the batched stage kernel
+void batch_tile_shape(int shape, int *bx, int *by);
+// mode 1 or 2 as launch_stage1/2; items are (case, tile) pairs in the
+// shape's tile numbering; mode 2 writes item_max[item]
+cudaError_t launch_batch_stage(int mode, int shape, int fp_bytes, const BatchCase *cases,
+                               const int2 *items, int n_items, double *item_max, double dt_fixed,
+                               int n_sm, cudaStream_t s);
+// interpolation + forcing: items are (case, marker); warps = markers per CTA
+cudaError_t launch_batch_interp(int fp_bytes, const BatchCase *cases, const int2 *items,
+                                int n_items, int warps, cudaStream_t s);
+// spreading + forced update: items are (case, index into the case's band
+// list); band_max[item] receives the step-size maximum of the forced cells
+cudaError_t launch_batch_spread(int fp_bytes, size_t smem, const BatchCase *cases,
+                                const int2 *items, int n_items, double *band_max, int n_sm,
+                                cudaStream_t s);
+size_t batch_spread_smem(const GridParams &g, int fp_bytes);
+// per-case sums, time update and next step size (one CTA per case)
+// sums[0..4] and t of every case into out[c * 6 + 0..5]
+cudaError_t launch_batch_gather(const BatchCase *cases, int ncases, double *out, cudaStream_t s);
+cudaError_t launch_batch_finish(const BatchCase *cases, int ncases, const double *item_max,
+                                const double *band_max, double dt_fixed, cudaStream_t s);
 
 // ---- quadrature (quadrature.cu) --------------------------------------------
 struct QuadBuffers {

@@ -296,6 +296,35 @@ __device__ __forceinline__ R lane_weight(const R *fr, const int *ck, int l, int 
     return w;
 }
 
+// The interpolated fields of cell j: rho, rho u.., rho e = rho E - |rho u|^2/(2 rho).
+template <int DIM, typename R>
+__device__ __forceinline__ void interp_fields(const R *__restrict__ U, long long N, long long j,
+                                              R (&v)[DIM + 2]) {
+    const R rho = U[j];
+    R ke = R(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const R md = U[(1 + d) * N + j];
+        v[1 + d] = md;
+        ke += md * md;
+    }
+    v[0] = rho;
+    v[DIM + 1] = U[(DIM + 1) * N + j] - R(0.5) * rdiv<R>(ke, rho);
+}
+
+// rho_L and the forcing of marker k from its interpolated sums (lane 0):
+// G = dt F = rho_L U_b - I[rho u], H = dt Q = rho_L c_v T_w - I[rho e].
+template <int DIM, typename R>
+__device__ __forceinline__ void store_forcing(const GridParams &g, const MarkerBuffers &m, int k,
+                                              const R (&acc)[DIM + 2]) {
+    const double rk = (double)acc[0];
+    m.rhoL[k] = rk;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+        m.G[(long long)k * DIM + d] = rk * m.Ub[(long long)k * DIM + d] - (double)acc[1 + d];
+    m.H[k] = rk * g.cv * m.Tw[k] - (double)acc[DIM + 1];
+}
+
 template <int DIM, typename T>
 __global__ void __launch_bounds__(256)
 interp_force_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuffers m,
@@ -325,16 +354,7 @@ interp_force_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuf
             R v[NF];
             if (in) {
                 const long long j = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
-                const R rho = U[j];
-                R ke = R(0);
-#pragma unroll
-                for (int d = 0; d < DIM; ++d) {
-                    const R md = U[(1 + d) * N + j];
-                    v[1 + d] = md;
-                    ke += md * md;
-                }
-                v[0] = rho;
-                v[NF - 1] = U[(DIM + 1) * N + j] - R(0.5) * rdiv<R>(ke, rho);
+                interp_fields<DIM, R>(U, N, j, v);
             } else {
 #pragma unroll
                 for (int f = 0; f < NF; ++f) v[f] = R(0);
@@ -365,16 +385,54 @@ interp_force_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuf
             }
 #pragma unroll
             for (int f = 0; f < NF; ++f) acc[f] = warp_sum_r<R>(acc[f]);
-            if (lane == 0) {
-                const double rk = (double)acc[0];
-                m.rhoL[k] = rk;
-#pragma unroll
-                for (int d = 0; d < DIM; ++d)
-                    m.G[(long long)k * DIM + d] = rk * m.Ub[(long long)k * DIM + d] - (double)acc[1 + d];
-                m.H[k] = rk * g.cv * m.Tw[k] - (double)acc[NF - 1];
-            }
+            if (lane == 0) store_forcing<DIM, R>(g, m, k, acc);
         }
         __syncthreads();
+    }
+}
+
+// Batched form: one warp per (case, marker) item, the 3^DIM support cells
+// read straight from the case's state.  The support lies inside the grid, so
+// each term equals the staged kernel's and the warp sums run in the same
+// order: the results are bitwise those of interp_force_kernel.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(512)
+batch_interp_kernel(const BatchCase *__restrict__ cases, const int2 *__restrict__ items,
+                    int n_items) {
+    using R = T;
+    constexpr int NF = DIM + 2;
+    constexpr int NS = DIM == 3 ? 27 : 9;
+    const int lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    for (int it = blockIdx.x * nw + (threadIdx.x >> 5); it < n_items; it += gridDim.x * nw) {
+        const int2 w = items[it];
+        const BatchCase &bc = cases[w.x];
+        const GridParams &g = bc.g;
+        const MarkerBuffers &m = bc.m;
+        const R *U = (const R *)bc.Us;
+        const int k = w.y;
+        R fr[3] = {R(0), R(0), R(0)};
+        int ck[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            ck[d] = m.cell[(long long)k * 3 + d];
+            fr[d] = marker_frac<R>(m, k, d);
+        }
+        R acc[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc[f] = R(0);
+        if (lane < NS) {
+            int cell[3];
+            const R wgt = lane_weight<DIM, R>(fr, ck, lane, cell);
+            const long long j = cell[0] + (long long)g.n[0] * (cell[1] + (long long)g.n[1] * cell[2]);
+            R v[NF];
+            interp_fields<DIM, R>(U, g.N, j, v);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) acc[f] = wgt * v[f];
+        }
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc[f] = warp_sum_r<R>(acc[f]);
+        if (lane == 0) store_forcing<DIM, R>(g, m, k, acc);
     }
 }
 
@@ -451,158 +509,193 @@ __device__ __forceinline__ void apply_forcing(const GridParams &g, T *__restrict
     U[(DIM + 1) * N + j] = (T)En;
 }
 
+// Shared memory of the spreading kernels: staged candidate markers (dynamic)
+// and the small per-tile tables (static, declared by the kernel).
+template <typename R>
+struct SpreadSmem {
+    R *fr, *g, *h;                // [3][SP_MAXC] offsets, [3][SP_MAXC] eps~ G, [SP_MAXC] eps~ H
+    int *cell, *head, *len;       // [SP_MAXC] owner cell in box, [bn], [bn]
+    int *cnt, *start, *warp;      // [NT3 + 1], [NT3], [33]
+};
+
+template <typename R>
+__device__ __forceinline__ SpreadSmem<R> spread_smem(unsigned char *raw, const GridParams &g,
+                                                     int *cnt, int *start, int *warp) {
+    const int bn = (g.tile[0] + 2) * (g.tile[1] + 2) * (g.dim == 3 ? g.tile[2] + 2 : 1);
+    SpreadSmem<R> sm;
+    sm.fr = reinterpret_cast<R *>(raw);
+    sm.g = sm.fr + 3 * SP_MAXC;
+    sm.h = sm.g + 3 * SP_MAXC;
+    sm.cell = reinterpret_cast<int *>(sm.h + SP_MAXC);
+    sm.head = sm.cell + SP_MAXC;
+    sm.len = sm.head + bn;
+    sm.cnt = cnt;
+    sm.start = start;
+    sm.warp = warp;
+    return sm;
+}
+
+// Spreading and the forced update of the cells of marker tile t; smax
+// collects the step-size rates of the forced cells.  Every thread calls it.
+template <int DIM, typename T>
+__device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__ U,
+                                            const MarkerBuffers &m,
+                                            const unsigned *__restrict__ keys,
+                                            const int *__restrict__ perm, int t,
+                                            const SpreadSmem<T> &sm, double &smax, bool &ok) {
+    using R = T;
+    constexpr int NT3 = DIM == 3 ? 27 : 9;
+    const int bx = g.tile[0] + 2, by = g.tile[1] + 2, bz = DIM == 3 ? g.tile[2] + 2 : 1;
+    const int bn = bx * by * bz;
+    R *s_fr = sm.fr, *s_g = sm.g, *s_h = sm.h;
+    int *s_cell = sm.cell, *s_head = sm.head, *s_len = sm.len;
+    int *s_cnt = sm.cnt, *s_start = sm.start, *s_warp = sm.warp;
+    const int tid = threadIdx.x;
+    const int cpt = g.cells_per_tile;
+    const int tx = t % g.ntile[0], ty = (t / g.ntile[0]) % g.ntile[1],
+              tz = t / (g.ntile[0] * g.ntile[1]);
+    const int o[3] = {tx * g.tile[0], ty * g.tile[1], DIM == 3 ? tz * g.tile[2] : 0};
+    // 1. bin ranges of the neighbour tiles (z, y, x order)
+    if (tid < NT3) {
+        const int ux = tx + tid % 3 - 1, uy = ty + (tid / 3) % 3 - 1,
+                  uz = tz + (DIM == 3 ? tid / 9 - 1 : 0);
+        int st = 0, cnt = 0;
+        if (ux >= 0 && uy >= 0 && uz >= 0 && ux < g.ntile[0] && uy < g.ntile[1] &&
+            uz < g.ntile[2]) {
+            const int u = ux + g.ntile[0] * (uy + g.ntile[1] * uz);
+            st = m.tile_off[u];
+            cnt = m.tile_off[u + 1] - st;
+        }
+        s_start[tid] = st;
+        s_cnt[tid + 1] = cnt;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        s_cnt[0] = 0;
+        for (int i = 1; i <= NT3; ++i) s_cnt[i] += s_cnt[i - 1];
+    }
+    __syncthreads();
+    const int total = s_cnt[NT3];
+    // 2. stage, in order, the markers whose owner cell lies in the tile
+    //    grown by one cell (their supports reach the tile)
+    int kept = 0;
+    for (int base = 0; base < total; base += SP_T) {
+        const int i = base + tid;
+        int keep = 0, p = 0, lc = 0;
+        if (i < total) {
+            int nt = 0;
+            while (s_cnt[nt + 1] <= i) ++nt;
+            p = s_start[nt] + (i - s_cnt[nt]);
+            const unsigned key = keys[p];
+            const int tu = (int)(key / (unsigned)cpt);
+            const int cin = (int)(key - (unsigned)tu * (unsigned)cpt);
+            const int cu[3] = {(tu % g.ntile[0]) * g.tile[0] + cin % g.tile[0],
+                               ((tu / g.ntile[0]) % g.ntile[1]) * g.tile[1] +
+                                   (cin / g.tile[0]) % g.tile[1],
+                               (tu / (g.ntile[0] * g.ntile[1])) * g.tile[2] +
+                                   cin / (g.tile[0] * g.tile[1])};
+            const int d0 = cu[0] - o[0] + 1, d1 = cu[1] - o[1] + 1,
+                      d2 = DIM == 3 ? cu[2] - o[2] + 1 : 0;
+            keep = d0 >= 0 && d0 < bx && d1 >= 0 && d1 < by && d2 >= 0 && d2 < bz;
+            lc = d0 + bx * (d1 + by * d2);
+        }
+        int tot;
+        const int pos = block_exclusive_scan(keep, s_warp, tot) + kept;
+        if (keep && pos < SP_MAXC) {
+            const int k = perm[p];
+            const double e = m.eps[k];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                s_fr[d * SP_MAXC + pos] = marker_frac<R>(m, k, d);
+                s_g[d * SP_MAXC + pos] = d < DIM ? (R)(m.G[(long long)k * DIM + d] * e) : R(0);
+            }
+            s_h[pos] = (R)(m.H[k] * e);
+            s_cell[pos] = lc;
+        }
+        kept += tot;
+    }
+    const bool overflow = kept > SP_MAXC;
+    // 3. runs of candidates per owner cell (contiguous in bin order)
+    if (!overflow) {
+        for (int q = tid; q < bn; q += SP_T) s_head[q] = -1;
+        __syncthreads();
+        for (int i = tid; i < kept; i += SP_T) {
+            const int c = s_cell[i];
+            if (i == 0 || s_cell[i - 1] != c) {
+                int j = i + 1;
+                while (j < kept && s_cell[j] == c) ++j;
+                s_head[c] = i;
+                s_len[c] = j - i;
+            }
+        }
+    }
+    __syncthreads();
+    // 4. gather per cell in the fixed order, then the forced update
+    for (int q = tid; q < cpt; q += SP_T) {
+        const int l[3] = {q % g.tile[0], (q / g.tile[0]) % g.tile[1],
+                          DIM == 3 ? q / (g.tile[0] * g.tile[1]) : 0};
+        const int c[3] = {o[0] + l[0], o[1] + l[1], o[2] + l[2]};
+        if (c[0] >= g.n[0] || c[1] >= g.n[1] || (DIM == 3 && c[2] >= g.n[2])) continue;
+        R f[DIM], qh = R(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) f[d] = R(0);
+        bool band = false;
+        if (!overflow) {
+            const int zr = DIM == 3 ? 1 : 0;
+            for (int oz = -zr; oz <= zr; ++oz)
+                for (int oy = -1; oy <= 1; ++oy)
+                    for (int ox = -1; ox <= 1; ++ox) {
+                        const int lc = (l[0] + 1 + ox) +
+                                       bx * ((l[1] + 1 + oy) + by * (DIM == 3 ? l[2] + 1 + oz : 0));
+                        const int h0 = s_head[lc];
+                        if (h0 < 0) continue;
+                        const int h1 = h0 + s_len[lc];
+                        const int oo[3] = {-ox, -oy, -oz};   // this cell seen from the owner cell
+                        for (int i = h0; i < h1; ++i) {
+                            R w = R(1);
+#pragma unroll
+                            for (int d = 0; d < DIM; ++d)
+                                w *= phi_r<R>(cell_offset<R>(oo[d], s_fr[d * SP_MAXC + i]));
+#pragma unroll
+                            for (int d = 0; d < DIM; ++d) f[d] += s_g[d * SP_MAXC + i] * w;
+                            qh += s_h[i] * w;
+                            band = true;
+                        }
+                    }
+        } else {
+            band = gather_markers<DIM, R>(g, m, keys, perm, c, [&](int k, R w) {
+                const double e = m.eps[k];
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) f[d] += (R)(m.G[(long long)k * DIM + d] * e) * w;
+                qh += (R)(m.H[k] * e) * w;
+            });
+        }
+        if (!band) continue;
+        const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+        apply_forcing<DIM, T, R>(g, U, j, f, qh);
+        T u[DIM + 2];
+#pragma unroll
+        for (int cc = 0; cc < DIM + 2; ++cc) u[cc] = U[cc * g.N + j];
+        smax = fmax(smax, (double)step_rate<DIM, T>(g, u, ok));
+    }
+    __syncthreads();
+}
+
 template <int DIM, typename T>
 __global__ void __launch_bounds__(SP_T)
 spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m,
                     const unsigned *__restrict__ keys, const int *__restrict__ perm) {
-    using R = T;
     constexpr int NT3 = DIM == 3 ? 27 : 9;
     extern __shared__ __align__(16) unsigned char smem_sp[];
-    const int bx = g.tile[0] + 2, by = g.tile[1] + 2, bz = DIM == 3 ? g.tile[2] + 2 : 1;
-    const int bn = bx * by * bz;
-    R *s_fr = reinterpret_cast<R *>(smem_sp);              // [3][SP_MAXC]  marker offsets
-    R *s_g = s_fr + 3 * SP_MAXC;                           // [3][SP_MAXC]  eps~ G
-    R *s_h = s_g + 3 * SP_MAXC;                            // [SP_MAXC]     eps~ H
-    int *s_cell = reinterpret_cast<int *>(s_h + SP_MAXC);  // [SP_MAXC]     owner cell in box
-    int *s_head = s_cell + SP_MAXC;                        // [bn]
-    int *s_len = s_head + bn;                              // [bn]
     __shared__ int s_cnt[NT3 + 1], s_start[NT3], s_warp[33];
     __shared__ double s_max[SP_T / 32];
+    const SpreadSmem<T> sm = spread_smem<T>(smem_sp, g, s_cnt, s_start, s_warp);
     const int tid = threadIdx.x;
     const int n_band = m.counts[1];
-    const int cpt = g.cells_per_tile;
     double smax = 0.0;   // step-size rate of the forced cells, for the next dt
     bool ok = true;
-    for (int it = blockIdx.x; it < n_band; it += gridDim.x) {
-        const int t = m.band_list[it];
-        const int tx = t % g.ntile[0], ty = (t / g.ntile[0]) % g.ntile[1],
-                  tz = t / (g.ntile[0] * g.ntile[1]);
-        const int o[3] = {tx * g.tile[0], ty * g.tile[1], DIM == 3 ? tz * g.tile[2] : 0};
-        // 1. bin ranges of the neighbour tiles (z, y, x order)
-        if (tid < NT3) {
-            const int ux = tx + tid % 3 - 1, uy = ty + (tid / 3) % 3 - 1,
-                      uz = tz + (DIM == 3 ? tid / 9 - 1 : 0);
-            int st = 0, cnt = 0;
-            if (ux >= 0 && uy >= 0 && uz >= 0 && ux < g.ntile[0] && uy < g.ntile[1] &&
-                uz < g.ntile[2]) {
-                const int u = ux + g.ntile[0] * (uy + g.ntile[1] * uz);
-                st = m.tile_off[u];
-                cnt = m.tile_off[u + 1] - st;
-            }
-            s_start[tid] = st;
-            s_cnt[tid + 1] = cnt;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            s_cnt[0] = 0;
-            for (int i = 1; i <= NT3; ++i) s_cnt[i] += s_cnt[i - 1];
-        }
-        __syncthreads();
-        const int total = s_cnt[NT3];
-        // 2. stage, in order, the markers whose owner cell lies in the tile
-        //    grown by one cell (their supports reach the tile)
-        int kept = 0;
-        for (int base = 0; base < total; base += SP_T) {
-            const int i = base + tid;
-            int keep = 0, p = 0, lc = 0;
-            if (i < total) {
-                int nt = 0;
-                while (s_cnt[nt + 1] <= i) ++nt;
-                p = s_start[nt] + (i - s_cnt[nt]);
-                const unsigned key = keys[p];
-                const int tu = (int)(key / (unsigned)cpt);
-                const int cin = (int)(key - (unsigned)tu * (unsigned)cpt);
-                const int cu[3] = {(tu % g.ntile[0]) * g.tile[0] + cin % g.tile[0],
-                                   ((tu / g.ntile[0]) % g.ntile[1]) * g.tile[1] +
-                                       (cin / g.tile[0]) % g.tile[1],
-                                   (tu / (g.ntile[0] * g.ntile[1])) * g.tile[2] +
-                                       cin / (g.tile[0] * g.tile[1])};
-                const int d0 = cu[0] - o[0] + 1, d1 = cu[1] - o[1] + 1,
-                          d2 = DIM == 3 ? cu[2] - o[2] + 1 : 0;
-                keep = d0 >= 0 && d0 < bx && d1 >= 0 && d1 < by && d2 >= 0 && d2 < bz;
-                lc = d0 + bx * (d1 + by * d2);
-            }
-            int tot;
-            const int pos = block_exclusive_scan(keep, s_warp, tot) + kept;
-            if (keep && pos < SP_MAXC) {
-                const int k = perm[p];
-                const double e = m.eps[k];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    s_fr[d * SP_MAXC + pos] = marker_frac<R>(m, k, d);
-                    s_g[d * SP_MAXC + pos] = d < DIM ? (R)(m.G[(long long)k * DIM + d] * e) : R(0);
-                }
-                s_h[pos] = (R)(m.H[k] * e);
-                s_cell[pos] = lc;
-            }
-            kept += tot;
-        }
-        const bool overflow = kept > SP_MAXC;
-        // 3. runs of candidates per owner cell (contiguous in bin order)
-        if (!overflow) {
-            for (int q = tid; q < bn; q += SP_T) s_head[q] = -1;
-            __syncthreads();
-            for (int i = tid; i < kept; i += SP_T) {
-                const int c = s_cell[i];
-                if (i == 0 || s_cell[i - 1] != c) {
-                    int j = i + 1;
-                    while (j < kept && s_cell[j] == c) ++j;
-                    s_head[c] = i;
-                    s_len[c] = j - i;
-                }
-            }
-        }
-        __syncthreads();
-        // 4. gather per cell in the fixed order, then the forced update
-        for (int q = tid; q < cpt; q += SP_T) {
-            const int l[3] = {q % g.tile[0], (q / g.tile[0]) % g.tile[1],
-                              DIM == 3 ? q / (g.tile[0] * g.tile[1]) : 0};
-            const int c[3] = {o[0] + l[0], o[1] + l[1], o[2] + l[2]};
-            if (c[0] >= g.n[0] || c[1] >= g.n[1] || (DIM == 3 && c[2] >= g.n[2])) continue;
-            R f[DIM], qh = R(0);
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) f[d] = R(0);
-            bool band = false;
-            if (!overflow) {
-                const int zr = DIM == 3 ? 1 : 0;
-                for (int oz = -zr; oz <= zr; ++oz)
-                    for (int oy = -1; oy <= 1; ++oy)
-                        for (int ox = -1; ox <= 1; ++ox) {
-                            const int lc = (l[0] + 1 + ox) +
-                                           bx * ((l[1] + 1 + oy) + by * (DIM == 3 ? l[2] + 1 + oz : 0));
-                            const int h0 = s_head[lc];
-                            if (h0 < 0) continue;
-                            const int h1 = h0 + s_len[lc];
-                            const int oo[3] = {-ox, -oy, -oz};   // this cell seen from the owner cell
-                            for (int i = h0; i < h1; ++i) {
-                                R w = R(1);
-#pragma unroll
-                                for (int d = 0; d < DIM; ++d)
-                                    w *= phi_r<R>(cell_offset<R>(oo[d], s_fr[d * SP_MAXC + i]));
-#pragma unroll
-                                for (int d = 0; d < DIM; ++d) f[d] += s_g[d * SP_MAXC + i] * w;
-                                qh += s_h[i] * w;
-                                band = true;
-                            }
-                        }
-            } else {
-                band = gather_markers<DIM, R>(g, m, keys, perm, c, [&](int k, R w) {
-                    const double e = m.eps[k];
-#pragma unroll
-                    for (int d = 0; d < DIM; ++d) f[d] += (R)(m.G[(long long)k * DIM + d] * e) * w;
-                    qh += (R)(m.H[k] * e) * w;
-                });
-            }
-            if (!band) continue;
-            const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
-            apply_forcing<DIM, T, R>(g, U, j, f, qh);
-            T u[DIM + 2];
-#pragma unroll
-            for (int cc = 0; cc < DIM + 2; ++cc) u[cc] = U[cc * g.N + j];
-            smax = fmax(smax, (double)step_rate<DIM, T>(g, u, ok));
-        }
-        __syncthreads();
-    }
+    for (int it = blockIdx.x; it < n_band; it += gridDim.x)
+        spread_tile<DIM, T>(g, U, m, keys, perm, m.band_list[it], sm, smax, ok);
 #pragma unroll
     for (int o2 = 16; o2 > 0; o2 >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o2));
     const int bad = __syncthreads_or(!ok);
@@ -613,6 +706,42 @@ spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m
         for (int w = 1; w < SP_T / 32; ++w) mx = fmax(mx, s_max[w]);
         m.bandmax[blockIdx.x] = mx;
         if (bad) record_error(m.err, ERR_NONFINITE);
+    }
+}
+
+
+// Batched form: items are (case, position in the case's band list); one
+// step-size maximum per item.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(SP_T)
+batch_spread_kernel(const BatchCase *__restrict__ cases, const int2 *__restrict__ items,
+                    int n_items, double *__restrict__ band_max) {
+    constexpr int NT3 = DIM == 3 ? 27 : 9;
+    extern __shared__ __align__(16) unsigned char smem_sp[];
+    __shared__ int s_cnt[NT3 + 1], s_start[NT3], s_warp[33];
+    __shared__ double s_max[SP_T / 32];
+    const int tid = threadIdx.x;
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const int2 w = items[it];
+        const BatchCase &bc = cases[w.x];
+        const GridParams g = bc.g;
+        const MarkerBuffers m = bc.m;
+        const SpreadSmem<T> sm = spread_smem<T>(smem_sp, g, s_cnt, s_start, s_warp);
+        double smax = 0.0;
+        bool ok = true;
+        spread_tile<DIM, T>(g, (T *)bc.Us, m, m.keys[m.sorted], m.perm[m.sorted],
+                            m.band_list[w.y], sm, smax, ok);
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o2));
+        const int bad = __syncthreads_or(!ok);
+        if ((tid & 31) == 0) s_max[tid >> 5] = smax;
+        __syncthreads();
+        if (tid == 0) {
+            double mx = s_max[0];
+            for (int w2 = 1; w2 < SP_T / 32; ++w2) mx = fmax(mx, s_max[w2]);
+            band_max[it] = mx;
+            if (bad) record_error(bc.err, ERR_NONFINITE);
+        }
     }
 }
 
@@ -648,10 +777,14 @@ band_mask_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__re
 
 constexpr int FIN_T = 1024;
 
-__global__ void __launch_bounds__(FIN_T)
-finish_kernel(const GridParams g, int ns, const MarkerBuffers m, const double *__restrict__ blockmax,
-              int nb, int nbs, double *__restrict__ dt_ptr, int *__restrict__ err, double dt_fixed) {
-    __shared__ double s[5][FIN_T / 32];
+// One CTA of FIN_T threads: the force/heat sums of one grid, its time
+// update and its next step size from the stage-2 maxima (blockmax[0..nb))
+// and the forced-cell maxima (bandmax[0..nbs)).
+__device__ __forceinline__ void finish_grid(const GridParams &g, int ns, const MarkerBuffers &m,
+                                            const double *__restrict__ blockmax, int nb,
+                                            const double *__restrict__ bandmax, int nbs,
+                                            double *__restrict__ dt_ptr, int *__restrict__ err,
+                                            double dt_fixed, double (*s)[FIN_T / 32]) {
     const int dim = g.dim;
     double a[5] = {0, 0, 0, 0, 0};   // sums of eps~ G (dim), eps~ H; a[4] = max rate
     for (int k = threadIdx.x; k < ns; k += FIN_T) {
@@ -660,7 +793,7 @@ finish_kernel(const GridParams g, int ns, const MarkerBuffers m, const double *_
         a[3] += e * __ldg(m.H + k);
     }
     for (int b = threadIdx.x; b < nb; b += FIN_T) a[4] = fmax(a[4], __ldg(blockmax + b));
-    for (int b = threadIdx.x; b < nbs; b += FIN_T) a[4] = fmax(a[4], __ldg(m.bandmax + b));
+    for (int b = threadIdx.x; b < nbs; b += FIN_T) a[4] = fmax(a[4], __ldg(bandmax + b));
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
 #pragma unroll
@@ -688,6 +821,34 @@ finish_kernel(const GridParams g, int ns, const MarkerBuffers m, const double *_
         if (!good) record_error(err, ERR_NONFINITE);
         *dt_ptr = good ? g.cfl / mx : 0.0;
     }
+}
+
+__global__ void __launch_bounds__(FIN_T)
+finish_kernel(const GridParams g, int ns, const MarkerBuffers m, const double *__restrict__ blockmax,
+              int nb, int nbs, double *__restrict__ dt_ptr, int *__restrict__ err, double dt_fixed) {
+    __shared__ double s[5][FIN_T / 32];
+    finish_grid(g, ns, m, blockmax, nb, m.bandmax, nbs, dt_ptr, err, dt_fixed, s);
+}
+
+// Batched form: CTA c finishes case c over its own stage and band items.
+__global__ void __launch_bounds__(FIN_T)
+batch_finish_kernel(const BatchCase *__restrict__ cases, const double *__restrict__ item_max,
+                    const double *__restrict__ band_max, double dt_fixed) {
+    __shared__ double s[5][FIN_T / 32];
+    const BatchCase &bc = cases[blockIdx.x];
+    finish_grid(bc.g, bc.m.ns, bc.m, item_max + bc.item0, bc.nitems, band_max + bc.band0,
+                bc.nband, bc.dt, bc.err, dt_fixed, s);
+}
+
+// The force sums, the step size they belong to and the time of every case
+// of a batch, gathered for one read: out[c * 6 + i].
+__global__ void batch_gather_kernel(const BatchCase *__restrict__ cases, int ncases,
+                                    double *__restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ncases) return;
+    const MarkerBuffers &m = cases[c].m;
+    for (int i = 0; i < 5; ++i) out[c * 6 + i] = m.sums[i];
+    out[c * 6 + 5] = *m.t;
 }
 
 // ---------------------------------------------------------------------------
@@ -845,6 +1006,59 @@ cudaError_t launch_spread_apply(const GridParams &g, int fp_bytes, void *U,
 cudaError_t launch_finish(const GridParams &g, const MarkerBuffers &m, const FluidBuffers &fb,
                           int nb, int nbs, double dt_fixed, cudaStream_t s) {
     finish_kernel<<<1, FIN_T, 0, s>>>(g, m.ns, m, fb.blockmax, nb, nbs, fb.dt, fb.err, dt_fixed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_interp(int fp_bytes, const BatchCase *cases, const int2 *items,
+                                int n_items, int warps, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    if (warps < 1 || warps > 16) return cudaErrorInvalidValue;
+    const int nb = (n_items + warps - 1) / warps;
+    if (fp_bytes == 4)
+        batch_interp_kernel<2, float><<<nb, 32 * warps, 0, s>>>(cases, items, n_items);
+    else
+        batch_interp_kernel<2, double><<<nb, 32 * warps, 0, s>>>(cases, items, n_items);
+    return cudaGetLastError();
+}
+
+size_t batch_spread_smem(const GridParams &g, int fp_bytes) {
+    return fp_bytes == 4 ? spread_smem_bytes<float>(g) : spread_smem_bytes<double>(g);
+}
+
+template <typename T>
+static cudaError_t batch_spread_t(size_t smem, const BatchCase *cases, const int2 *items,
+                                  int n_items, double *band_max, int ctas, cudaStream_t s) {
+    static size_t configured = 0;
+    if (smem > 48 * 1024 && configured < smem) {
+        cudaError_t e = cudaFuncSetAttribute(batch_spread_kernel<2, T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    batch_spread_kernel<2, T><<<ctas, SP_T, smem, s>>>(cases, items, n_items, band_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_spread(int fp_bytes, size_t smem, const BatchCase *cases,
+                                const int2 *items, int n_items, double *band_max, int n_sm,
+                                cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    int ctas = 4 * (n_sm > 0 ? n_sm : 1);
+    if (ctas > n_items) ctas = n_items;
+    return fp_bytes == 4 ? batch_spread_t<float>(smem, cases, items, n_items, band_max, ctas, s)
+                         : batch_spread_t<double>(smem, cases, items, n_items, band_max, ctas, s);
+}
+
+cudaError_t launch_batch_finish(const BatchCase *cases, int ncases, const double *item_max,
+                                const double *band_max, double dt_fixed, cudaStream_t s) {
+    if (ncases <= 0) return cudaSuccess;
+    batch_finish_kernel<<<ncases, FIN_T, 0, s>>>(cases, item_max, band_max, dt_fixed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_gather(const BatchCase *cases, int ncases, double *out, cudaStream_t s) {
+    if (ncases <= 0) return cudaSuccess;
+    batch_gather_kernel<<<(ncases + 127) / 128, 128, 0, s>>>(cases, ncases, out);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,11 @@ class MotionC(ctypes.Structure):
     _fields_ = [("amp", ctypes.c_double), ("freq", ctypes.c_double), ("axis", ctypes.c_int)]
 
 
+class BatchTuningC(ctypes.Structure):
+    _fields_ = [("tile_shape", ctypes.c_int), ("markers_per_block", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+
 _vp = ctypes.c_void_p
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
@@ -80,7 +85,25 @@ SIGNATURES = [
     ("ibm_profile", ctypes.c_int, [_vp, ctypes.c_int]),
     ("ibm_profile_read", ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     ("ibm_rhs_dt_noalloc", ctypes.c_int, [ctypes.POINTER(GridDescC), _vp, _vp, _vp, _vp]),
+    ("ibm_batch_workspace_bytes", ctypes.c_size_t, [ctypes.c_int, ctypes.POINTER(GridDescC), _ip]),
+    ("ibm_create_batch", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(GridDescC), _ip, _vp,
+                                        ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
+    ("ibm_batch_destroy", ctypes.c_int, [_vp]),
+    ("ibm_batch_case", _vp, [_vp, ctypes.c_int]),
+    ("ibm_batch_step", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double]),
+    ("ibm_batch_sync", ctypes.c_int, [_vp, _ip]),
+    ("ibm_batch_forces", ctypes.c_int, [_vp, _dp]),
+    ("ibm_batch_get_tuning", ctypes.c_int, [_vp, ctypes.POINTER(BatchTuningC)]),
+    ("ibm_batch_set_tuning", ctypes.c_int, [_vp, ctypes.POINTER(BatchTuningC)]),
+    ("ibm_batch_autotune", ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp]),
+    ("ibm_batch_profile", ctypes.c_int, [_vp, ctypes.c_int]),
+    ("ibm_batch_profile_read", ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
+    ("ibm_batch_last_error", ctypes.c_char_p, [_vp]),
 ]
+
+BATCH_TILE_SHAPES = [(16, 16), (32, 8), (64, 4), (8, 32)]
+BATCH_WARPS = [1, 2, 4, 8, 16]
+BATCH_FORCE_FIELDS = ["Fx", "Fy", "heat_rate", "Cd", "Cl", "Nu", "dt", "t"]
 
 PROF_GROUPS = ["stage1", "stage2", "markers", "interp_force", "spread_apply", "finish"]
 
@@ -289,6 +312,90 @@ def ibm_rhs_dt_noalloc(desc: GridDescC, U_ptr: int, L_ptr: int, dt_ptr: int, str
                                     _vp(stream_ptr)), None)
 
 
+def _bcheck(st: int, handle=None):
+    if st != IBM_OK:
+        msg = lib().ibm_batch_last_error(handle)
+        raise IbmError(st, msg.decode() if msg else "")
+
+
+def _desc_array(descs):
+    arr = (GridDescC * len(descs))()
+    for i, d in enumerate(descs):
+        arr[i] = d
+    return arr
+
+
+def ibm_batch_workspace_bytes(descs, max_markers) -> int:
+    mm = np.ascontiguousarray(max_markers, dtype=np.int32)
+    return int(lib().ibm_batch_workspace_bytes(len(descs), _desc_array(descs), _ptr(mm, _ip)))
+
+
+def ibm_create_batch(descs, max_markers, workspace_ptr: int, nbytes: int, stream_ptr: int):
+    mm = np.ascontiguousarray(max_markers, dtype=np.int32)
+    h = _vp()
+    st = lib().ibm_create_batch(len(descs), _desc_array(descs), _ptr(mm, _ip), _vp(workspace_ptr),
+                                ctypes.c_size_t(nbytes), _vp(stream_ptr), ctypes.byref(h))
+    _bcheck(st, None)
+    return h
+
+
+def ibm_batch_destroy(h):
+    _bcheck(lib().ibm_batch_destroy(h), None)
+
+
+def ibm_batch_case(h, c: int):
+    p = lib().ibm_batch_case(h, int(c))
+    if not p:
+        raise IbmError(1, "no case %d in this batch" % c)
+    return _vp(p)
+
+
+def ibm_batch_step(h, nsteps: int, dt_fixed: float = 0.0):
+    _bcheck(lib().ibm_batch_step(h, int(nsteps), ctypes.c_double(dt_fixed)), h)
+
+
+def ibm_batch_sync(h):
+    bad = ctypes.c_int(-1)
+    _bcheck(lib().ibm_batch_sync(h, ctypes.byref(bad)), h)
+
+
+def ibm_batch_forces(h, ncases: int) -> np.ndarray:
+    """(ncases, 8) array: Fx, Fy, heat rate, Cd, Cl, Nu, dt, t per case."""
+    out = np.zeros((ncases, 8))
+    _bcheck(lib().ibm_batch_forces(h, _ptr(out)), h)
+    return out
+
+
+def ibm_batch_get_tuning(h) -> dict:
+    t = BatchTuningC()
+    _bcheck(lib().ibm_batch_get_tuning(h, ctypes.byref(t)), h)
+    return {"tile_shape": t.tile_shape, "markers_per_block": t.markers_per_block,
+            "use_graph": t.use_graph}
+
+
+def ibm_batch_set_tuning(h, tile_shape: int, markers_per_block: int, use_graph: int):
+    t = BatchTuningC(int(tile_shape), int(markers_per_block), int(use_graph))
+    _bcheck(lib().ibm_batch_set_tuning(h, ctypes.byref(t)), h)
+
+
+def ibm_batch_profile(h, enable: bool):
+    _bcheck(lib().ibm_batch_profile(h, int(bool(enable))), h)
+
+
+def ibm_batch_profile_read(h) -> dict:
+    ms = (ctypes.c_double * len(PROF_GROUPS))()
+    n = (ctypes.c_longlong * len(PROF_GROUPS))()
+    _bcheck(lib().ibm_batch_profile_read(h, ms, n), h)
+    return {name: (ms[i], n[i]) for i, name in enumerate(PROF_GROUPS)}
+
+
+def ibm_batch_autotune(h, reps: int = 5) -> dict:
+    sms = np.zeros(len(BATCH_TILE_SHAPES))
+    ims = np.zeros(len(BATCH_WARPS))
+    _bcheck(lib().ibm_batch_autotune(h, int(reps), _ptr(sms), _ptr(ims)), h)
+    return {"stage_ms": sms, "interp_ms": ims}
+
+
 # ---------------------------------------------------------------------------
 # convenience owner of device memory
 # ---------------------------------------------------------------------------
@@ -317,9 +424,27 @@ class Grid:
                                  self.stream.cuda_stream)
         self.n_kept = 0
 
+    @classmethod
+    def _borrowed(cls, h, g: cases.GridDesc, device, stream, energy_reading: int = 0):
+        """A Grid view of a handle owned elsewhere (a batch case)."""
+        import torch
+        self = cls.__new__(cls)
+        self.torch = torch
+        self.g = g
+        self.device = torch.device(device)
+        self.stream = stream
+        self.dtype = torch.float32 if g.fp_bytes == 4 else torch.float64
+        self.desc = make_desc(g, energy_reading)
+        self.ws = None
+        self.h = h
+        self.n_kept = 0
+        self._owned = False
+        return self
+
     def close(self):
         if getattr(self, "h", None) is not None:
-            ibm_destroy(self.h)
+            if getattr(self, "_owned", True):
+                ibm_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -411,3 +536,71 @@ class Grid:
         ibm_spread(self.h, R.data_ptr(), nc, out.data_ptr())
         self.stream.synchronize()
         return out
+
+
+class Batch:
+    """Many independent 2D grids advanced together (one launch per stage).
+
+    `cases[c]` is a Grid view of case c: set its state and markers and read
+    its state, forces and time through it.  The batch owns the memory."""
+
+    def __init__(self, gs, max_markers, device="cuda", stream=None, energy_reading: int = 0):
+        import torch
+        self.torch = torch
+        self.gs = list(gs)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.descs = [make_desc(g, energy_reading) for g in self.gs]
+        self.max_markers = [int(m) for m in max_markers]
+        nbytes = ibm_batch_workspace_bytes(self.descs, self.max_markers)
+        if nbytes == 0:
+            # let the library say why (it checks the description first)
+            ibm_create_batch(self.descs, self.max_markers, 0, 0, 0)
+            raise IbmError(1, "invalid batch description")
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        self.ws_ptr = (self.ws.data_ptr() + 255) // 256 * 256
+        self.nbytes = nbytes
+        self.h = ibm_create_batch(self.descs, self.max_markers, self.ws_ptr, nbytes,
+                                  self.stream.cuda_stream)
+        self.cases = [Grid._borrowed(ibm_batch_case(self.h, c), g, self.device, self.stream,
+                                     energy_reading)
+                      for c, g in enumerate(self.gs)]
+
+    def __len__(self):
+        return len(self.cases)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            for c in self.cases:
+                c.h = None
+            ibm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, nsteps: int = 1, dt_fixed: float = 0.0):
+        ibm_batch_step(self.h, nsteps, dt_fixed)
+
+    def sync(self):
+        ibm_batch_sync(self.h)
+
+    def forces(self) -> np.ndarray:
+        return ibm_batch_forces(self.h, len(self.cases))
+
+    def tuning(self) -> dict:
+        return ibm_batch_get_tuning(self.h)
+
+    def set_tuning(self, tile_shape=None, markers_per_block=None, use_graph=None):
+        t = self.tuning()
+        ibm_batch_set_tuning(self.h,
+                             t["tile_shape"] if tile_shape is None else tile_shape,
+                             t["markers_per_block"] if markers_per_block is None
+                             else markers_per_block,
+                             t["use_graph"] if use_graph is None else int(bool(use_graph)))
+
+    def autotune(self, reps: int = 5) -> dict:
+        return ibm_batch_autotune(self.h, reps)
