@@ -237,7 +237,8 @@ __device__ __forceinline__ double warp_max(double v) {
 // One tile of one stage.  MODE 0: out = L(Uin).  MODE 1: out = U1 = Uin +
 // dt L(Uin).  MODE 2: out = U* = Un/2 + (Uin + dt L(Uin))/2 with Uin = U1,
 // and the maximum of s_j(U*) over the tile's cells outside the band is
-// returned to thread 0 (every thread must call; the function synchronises).
+// returned to thread 0 (every thread must call; the function synchronises;
+// a later call may reuse s_red only after its own first barrier).
 template <typename B, typename T, int MODE>
 __device__ __forceinline__ double stage_tile(const GridParams &g, int ox, int oy, int oz,
                                              const T *__restrict__ Uin, const T *__restrict__ Un,
@@ -356,10 +357,13 @@ __device__ __forceinline__ double stage_tile(const GridParams &g, int ox, int oy
     }
 
     if (MODE == 2) {
-        double smax = warp_max((double)smax_t);
+        // the tile's maximum in the compute type (exact), widened once
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) smax_t = fmax(smax_t, __shfl_xor_sync(0xffffffffu, smax_t, o));
         bad = __syncthreads_or(!ok) != 0;
-        if ((tid & 31) == 0) s_red[tid >> 5] = smax;
+        if ((tid & 31) == 0) s_red[tid >> 5] = (double)smax_t;
         __syncthreads();
+        if (tid != 0) return 0.0;
         double m = s_red[0];
         for (int w = 1; w < NT / 32; ++w) m = fmax(m, s_red[w]);
         return m;

@@ -771,6 +771,36 @@ band_mask_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__re
     }
 }
 
+// Keep in the band list only the tiles that hold a band cell: a tile next to
+// an occupied one is reached by a marker's support only where that marker's
+// owner cell lies on the shared tile face, and the spreading kernels would
+// otherwise pay a full pass over each of the others for nothing.  One warp
+// per band tile clears band_flag where no bit is set; the lists are then
+// rebuilt.
+template <int DIM>
+__global__ void __launch_bounds__(256)
+band_refine_kernel(const GridParams g, const MarkerBuffers m) {
+    const int n_band = m.counts[1];
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_band; it += nw) {
+        const int t = m.band_list[it];
+        const int tx = t % g.ntile[0], ty = (t / g.ntile[0]) % g.ntile[1],
+                  tz = t / (g.ntile[0] * g.ntile[1]);
+        bool any = false;
+        for (int q = lane; q < g.cells_per_tile && !any; q += 32) {
+            const int c[3] = {tx * g.tile[0] + q % g.tile[0],
+                              ty * g.tile[1] + (q / g.tile[0]) % g.tile[1],
+                              DIM == 3 ? tz * g.tile[2] + q / (g.tile[0] * g.tile[1]) : 0};
+            if (c[0] >= g.n[0] || c[1] >= g.n[1] || (DIM == 3 && c[2] >= g.n[2])) continue;
+            const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+            any = (m.band_bits[j >> 5] >> (j & 31)) & 1u;
+        }
+        any = __any_sync(0xffffffffu, any);
+        if (lane == 0 && !any) m.band_flag[t] = 0;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // forces/heat sums (fixed-order reduction) and the time update
 // ---------------------------------------------------------------------------
@@ -1066,10 +1096,17 @@ cudaError_t launch_band_mask(const GridParams &g, const MarkerBuffers &m, int gr
                              cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(m.band_bits, 0, sizeof(unsigned) * (size_t)(g.N / 32 + 1), s);
     if (e != cudaSuccess || m.ns <= 0) return e;
-    if (g.dim == 3)
+    if (g.dim == 3) {
         band_mask_kernel<3><<<grid_ctas, 256, 0, s>>>(g, m, m.keys[m.sorted], m.perm[m.sorted]);
-    else
+        band_refine_kernel<3><<<grid_ctas, 256, 0, s>>>(g, m);
+    } else {
         band_mask_kernel<2><<<grid_ctas, 256, 0, s>>>(g, m, m.keys[m.sorted], m.perm[m.sorted]);
+        band_refine_kernel<2><<<grid_ctas, 256, 0, s>>>(g, m);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    tile_lists_kernel<<<1, SORT_T, 0, s>>>(g.n_tiles, m.occ_flag, m.band_flag, m.occ_list,
+                                           m.band_list, m.counts);
     return cudaGetLastError();
 }
 
