@@ -556,7 +556,7 @@ def run_batched(args, rank, world, local):
                             "interp_ms_per_warps": list(map(float, tune_ms["interp_ms"]))},
             "roofline": {"bound": "hbm", "kernel": "batch_" + dom, "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None,
+                         "traffic": traffic_for("batch_" + dom),
                          "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)"
                                         if peak_kind == "measured" else "fallback 6.8 TB/s",
                          "algorithmic_bytes_per_launch": alg[dom]},
