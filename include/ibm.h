@@ -151,9 +151,43 @@ ibm_status ibm_step(ibm_grid *g, int nsteps, double dt_fixed);
 ibm_status ibm_forces_and_nusselt(ibm_grid *g, double force[3], double *heat_rate, double *Cd,
                                   double *Cl, double *Nu);
 
-/* Adjoint of the step with respect to marker positions and wall
- * temperatures.  Not provided by this build: returns IBM_ERR_UNSUPPORTED. */
+/* ---- discrete adjoint ----------------------------------------------------
+ * Gradient of J = dJ_dCd * Cd + dJ_dNu * Nu, with Cd and Nu those of the
+ * LAST recorded step (as ibm_forces_and_nusselt reports them), with respect
+ * to the kept markers' positions and wall temperatures: the exact derivative
+ * of the discrete map that the recorded ibm_step calls computed (Sec. 2.1-2.2,
+ * App. B), under these conventions: the step sizes of the recorded run are
+ * held fixed; bins, kept markers and the band do not move; the limiter and
+ * the max/abs of the Rusanov flux take the branch of the forward run; the
+ * weights eps~ = A~^{-1} 1 are differentiated exactly (one extra CG solve).
+ * Static markers only.  The forward states are recomputed from checkpoints
+ * taken every `every` steps. */
+
+/* Bytes of the adjoint workspace for max_steps recorded steps with a
+ * checkpoint every `every` steps: ceil(max_steps/every) + every + 6 states,
+ * (dim+2) x N doubles and a few doubles per marker (0 if invalid). */
+size_t ibm_adjoint_workspace_bytes(const ibm_grid_desc *desc, int max_markers, int max_steps,
+                                   int every);
+
+/* Start recording into a 256-byte aligned device workspace of at least
+ * ibm_adjoint_workspace_bytes bytes (caller-owned): every following ibm_step
+ * stores its step size and, every `every` steps, its starting state.  A new
+ * state or new markers restart the recording.  More than max_steps steps
+ * give IBM_ERR_WORKSPACE (before any work); moving markers
+ * IBM_ERR_UNSUPPORTED. */
+ibm_status ibm_record(ibm_grid *g, int max_steps, int every, void *dev_workspace, size_t bytes);
+
+/* The reverse sweep over all recorded steps.  dJ_dX: n_kept*dim doubles,
+ * dJ_dTw: n_kept doubles (host, kept-marker order; either may be NULL).
+ * The handle's state, time and last marker forcing are left unchanged.
+ * Synchronizes.  Errors: IBM_ERR_STATE (nothing recorded), IBM_ERR_ARG (Nu
+ * weighted but undefined), IBM_ERR_NOCONV (the weights' adjoint solve). */
 ibm_status ibm_backward(ibm_grid *g, double dJ_dCd, double dJ_dNu, double *dJ_dX, double *dJ_dTw);
+
+/* out = J_L(U)^T V: the transpose of the Jacobian of the flux operator
+ * L(U) of ibm_rhs applied to V (all (dim+2) x N device arrays of the grid's
+ * type).  Needs ibm_record's workspace (FP64 scratch).  Asynchronous. */
+ibm_status ibm_rhs_vjp(ibm_grid *g, const void *U, const void *V, void *out);
 
 /* Wait for the handle's stream and report any recorded device error. */
 ibm_status ibm_sync(ibm_grid *g);

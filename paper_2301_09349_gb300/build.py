@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libibm_gb300.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-UNITS = ["flux.cu", "flux_zm.cu", "markers.cu", "quadrature.cu", "api.cu", "noalloc.cu",
+UNITS = ["flux.cu", "flux_zm.cu", "markers.cu", "quadrature.cu", "api.cu", "noalloc.cu", "adjoint.cu",
          "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]

@@ -384,6 +384,7 @@ ibm_status ibm_set_state(ibm_grid *g, const void *U) {
     CU(cudaMemsetAsync(g->mb.t, 0, sizeof(double), g->stream), "reset time");
     CU(cudaMemsetAsync(g->mb.steps, 0, sizeof(long long), g->stream), "reset steps");
     g->has_state = true;
+    g->rec_steps = 0;
     return IBM_OK;
 }
 
@@ -397,6 +398,7 @@ ibm_status ibm_set_state_host(ibm_grid *g, const void *U_host) {
     CU(cudaMemsetAsync(g->mb.t, 0, sizeof(double), g->stream), "reset time");
     CU(cudaMemsetAsync(g->mb.steps, 0, sizeof(long long), g->stream), "reset steps");
     g->has_state = true;
+    g->rec_steps = 0;
     return IBM_OK;
 }
 
@@ -505,6 +507,7 @@ ibm_status ibm_set_markers(ibm_grid *g, int n, const double *X0, const double *U
     g->kept = keep;
     g->Tw_h = Twh;
     ++g->marker_gen;
+    g->rec_steps = 0;
     g->moving = motion != nullptr;
     if (motion) g->motion = *motion;
     ibm_status st = rebuild_markers(g, 0);
@@ -534,6 +537,13 @@ ibm_status ibm_step(ibm_grid *g, int nsteps, double dt_fixed) {
     if (!g) return IBM_ERR_ARG;
     if (nsteps < 0 || !isfinite(dt_fixed)) return fail(g, IBM_ERR_ARG, "invalid step arguments");
     if (!g->has_state) return fail(g, IBM_ERR_STATE, "ibm_set_state must come first");
+    if (g->recording) {
+        if (g->moving && g->mb.ns > 0)
+            return fail(g, IBM_ERR_UNSUPPORTED, "the adjoint records static markers only");
+        if ((long long)g->rec_steps + nsteps > g->adj.max_steps)
+            return fail(g, IBM_ERR_WORKSPACE, "more steps than the adjoint workspace records (" +
+                                                  std::to_string(g->adj.max_steps) + ")");
+    }
     const int fpb = g->desc.fp_bytes;
     const int ctas = persistent_ctas(g);
     long rec;
@@ -542,6 +552,11 @@ ibm_status ibm_step(ibm_grid *g, int nsteps, double dt_fixed) {
         void *Un = g->U[g->cur];
         void *Us = g->U[1 - g->cur];
         void *U1 = g->L;
+        if (g->recording && g->rec_steps % g->adj.every == 0)
+            CU(cudaMemcpyAsync((char *)g->adj.ckpt +
+                                   (size_t)(g->rec_steps / g->adj.every) * align_up(state_bytes(g->desc), 256),
+                               Un, state_bytes(g->desc), cudaMemcpyDeviceToDevice, g->stream),
+               "checkpoint");
         CU(prof_begin(g, IBM_PROF_STAGE1, 1, &rec), "profile");
         CU(launch_stage1(g->gp, fpb, Un, U1, g->fb, dt_fixed, g->stream), "stage 1");
         CU(prof_end(g, rec), "profile");
@@ -569,6 +584,12 @@ ibm_status ibm_step(ibm_grid *g, int nsteps, double dt_fixed) {
         CU(launch_finish(g->gp, g->mb, g->fb, nb, g->mb.ns > 0 ? ctas : 0, dt_fixed, g->stream),
            "finish");
         CU(prof_end(g, rec), "profile");
+        if (g->recording) {
+            CU(cudaMemcpyAsync(g->adj.dt_hist + g->rec_steps, g->mb.sums + 4, sizeof(double),
+                               cudaMemcpyDeviceToDevice, g->stream),
+               "record dt");
+            ++g->rec_steps;
+        }
         g->cur = 1 - g->cur;
     }
     return IBM_OK;
@@ -617,9 +638,6 @@ ibm_status ibm_forces_and_nusselt(ibm_grid *g, double force[3], double *heat_rat
     return IBM_OK;
 }
 
-ibm_status ibm_backward(ibm_grid *g, double, double, double *, double *) {
-    return fail(g, IBM_ERR_UNSUPPORTED, "the adjoint step is not provided by this build");
-}
 
 ibm_status ibm_get_markers(ibm_grid *g, double *X, double *eps_t, int *input_index) {
     if (!g) return IBM_ERR_ARG;

@@ -34,6 +34,9 @@ struct ibm_grid {
     bool has_state = false;
     bool moving = false;
     long long marker_gen = 0;   // bumped by every ibm_set_markers
+    bool recording = false;     // ibm_record: checkpoints taken by ibm_step
+    int rec_steps = 0;          // steps recorded since ibm_record / the last new state
+    ibmk::AdjBuffers adj{};
     bool in_batch = false;      // owned by an ibm_batch (ibm_destroy refuses it)
     ibm_motion motion{};
     std::vector<int> kept;

@@ -201,6 +201,42 @@ cudaError_t launch_batch_gather(const BatchCase *cases, int ncases, double *out,
 cudaError_t launch_batch_finish(const BatchCase *cases, int ncases, const double *item_max,
                                 const double *band_max, double dt_fixed, cudaStream_t s);
 
+// ---- discrete adjoint (adjoint.cu) -------------------------------------------
+// Device buffers of ibm_record / ibm_backward, carved from the caller's
+// adjoint workspace.  States are (dim+2) x N elements of the grid's type.
+struct AdjBuffers {
+    int max_steps = 0, every = 0, n_ckpt = 0, cap = 0;
+    void *ckpt = nullptr;        // n_ckpt states: U at steps 0, every, 2 every, ...
+    double *dt_hist = nullptr;   // step size of every recorded step
+    void *seg = nullptr;         // every states: one replayed segment
+    void *A = nullptr;           // U1 of the step being reversed
+    void *B = nullptr;           // U* of the step being reversed
+    void *lam = nullptr;         // adjoint state
+    void *mu = nullptr;          // adjoint of U1
+    void *jtv = nullptr;         // transpose-Jacobian product of L
+    void *lfq = nullptr;         // (dim+1) x N: adjoints of the spread sources
+    double *lamW = nullptr;      // (dim+2) x N FP64 accumulators (primitive adjoints)
+    double *lamX = nullptr;      // cap x 3 marker-position gradient
+    double *lamTw = nullptr;     // cap wall-temperature gradient
+    double *lamEps = nullptr;    // cap adjoint of eps~
+    double *mr = nullptr;        // cap x 5: adjoints of rho_L, I[rho u] (3), I[rho e]
+    double *z = nullptr;         // cap: A~ z = lamEps
+    double *save = nullptr;      // cap x 5: rho_L, G (3), H of the last forward step
+};
+
+// out = J_L(U)^T V (lamW: FP64 scratch, zero on entry and exit)
+cudaError_t launch_rhs_vjp(const GridParams &g, int fp_bytes, const void *U, const void *V,
+                           double *lamW, void *out, cudaStream_t s);
+// one step reversed: a.A = U1, a.B = U* and the marker forcing of the step
+// must be current; a.lam holds the adjoint of U^{n+1} and receives that of
+// U^n; cd, nu: the direct terms of J (last step only)
+cudaError_t launch_reverse_step(const GridParams &g, int fp_bytes, const MarkerBuffers &m,
+                                const AdjBuffers &a, const void *Un, double dt, double cd,
+                                double nu, int n_sm, cudaStream_t s);
+// dJ/dX through eps~: a.z = A~^{-1} dJ/deps~ must be current
+cudaError_t launch_eps_adjoint_x(const GridParams &g, const MarkerBuffers &m, const AdjBuffers &a,
+                                 int n_sm, cudaStream_t s);
+
 // ---- quadrature (quadrature.cu) --------------------------------------------
 struct QuadBuffers {
     int width;               // row capacity of the ELL storage
@@ -217,5 +253,7 @@ struct QuadBuffers {
 int quad_row_width(int dim);
 cudaError_t launch_quadrature(const GridParams &g, const MarkerBuffers &m, const QuadBuffers &qb,
                               double tol, int maxit, int warm, cudaStream_t s);
+cudaError_t launch_quadrature_solve(int ns, const QuadBuffers &qb, const double *rhs, double *x,
+                                    double tol, int maxit, int *err, cudaStream_t s);
 
 }  // namespace ibmk

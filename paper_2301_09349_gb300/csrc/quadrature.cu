@@ -110,7 +110,8 @@ __device__ __forceinline__ void spmv(int ns, const QuadBuffers &q, const double 
 
 template <int NTH>
 __global__ void __launch_bounds__(NTH)
-pcg_kernel(int ns, const QuadBuffers q, double *x, double tol, int maxit, int warm, int *err) {
+pcg_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rhs, double tol,
+           int maxit, int warm, int *err) {
     __shared__ double s_red[32];
     double *r = q.r, *z = q.z, *p = q.p, *qv = q.q;
     if (!warm)
@@ -124,7 +125,7 @@ pcg_kernel(int ns, const QuadBuffers q, double *x, double tol, int maxit, int wa
         __syncthreads();
         double lm = 0.0;
         for (int k = threadIdx.x; k < ns; k += NTH) {
-            r[k] = 1.0 - qv[k];
+            r[k] = (rhs ? rhs[k] : 1.0) - qv[k];
             lm = fmax(lm, fabs(r[k]));
         }
         rmax = block_max<NTH>(lm, s_red);
@@ -169,7 +170,7 @@ pcg_kernel(int ns, const QuadBuffers q, double *x, double tol, int maxit, int wa
         spmv<NTH>(ns, q, x, qv);
         __syncthreads();
         double lm = 0.0;
-        for (int k = threadIdx.x; k < ns; k += NTH) lm = fmax(lm, fabs(1.0 - qv[k]));
+        for (int k = threadIdx.x; k < ns; k += NTH) lm = fmax(lm, fabs((rhs ? rhs[k] : 1.0) - qv[k]));
         rmax = block_max<NTH>(lm, s_red);
         converged = rmax <= tol;
     }
@@ -194,8 +195,18 @@ cudaError_t launch_quadrature(const GridParams &g, const MarkerBuffers &m, const
     else assemble_kernel<2><<<nb, 128, 0, s>>>(g, m, qb, keys, perm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (m.ns <= 2048) pcg_kernel<256><<<1, 256, 0, s>>>(m.ns, qb, m.eps, tol, maxit, warm, m.err);
-    else pcg_kernel<1024><<<1, 1024, 0, s>>>(m.ns, qb, m.eps, tol, maxit, warm, m.err);
+    if (m.ns <= 2048) pcg_kernel<256><<<1, 256, 0, s>>>(m.ns, qb, m.eps, nullptr, tol, maxit, warm, m.err);
+    else pcg_kernel<1024><<<1, 1024, 0, s>>>(m.ns, qb, m.eps, nullptr, tol, maxit, warm, m.err);
+    return cudaGetLastError();
+}
+
+// A~ x = rhs with the matrix assembled by the last launch_quadrature (the
+// adjoint of the weights); x starts from zero.
+cudaError_t launch_quadrature_solve(int ns, const QuadBuffers &qb, const double *rhs, double *x,
+                                    double tol, int maxit, int *err, cudaStream_t s) {
+    if (ns <= 0) return cudaSuccess;
+    if (ns <= 2048) pcg_kernel<256><<<1, 256, 0, s>>>(ns, qb, x, rhs, tol, maxit, 0, err);
+    else pcg_kernel<1024><<<1, 1024, 0, s>>>(ns, qb, x, rhs, tol, maxit, 0, err);
     return cudaGetLastError();
 }
 

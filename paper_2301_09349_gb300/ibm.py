@@ -85,6 +85,10 @@ SIGNATURES = [
     ("ibm_profile", ctypes.c_int, [_vp, ctypes.c_int]),
     ("ibm_profile_read", ctypes.c_int, [_vp, _dp, ctypes.POINTER(ctypes.c_longlong)]),
     ("ibm_rhs_dt_noalloc", ctypes.c_int, [ctypes.POINTER(GridDescC), _vp, _vp, _vp, _vp]),
+    ("ibm_adjoint_workspace_bytes", ctypes.c_size_t, [ctypes.POINTER(GridDescC), ctypes.c_int,
+                                                      ctypes.c_int, ctypes.c_int]),
+    ("ibm_record", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t]),
+    ("ibm_rhs_vjp", ctypes.c_int, [_vp, _vp, _vp, _vp]),
     ("ibm_batch_workspace_bytes", ctypes.c_size_t, [ctypes.c_int, ctypes.POINTER(GridDescC), _ip]),
     ("ibm_create_batch", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(GridDescC), _ip, _vp,
                                         ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
@@ -238,6 +242,21 @@ def ibm_backward(h, dJ_dCd: float, dJ_dNu: float, n_kept: int, dim: int):
     dT = np.zeros(max(n_kept, 1))
     _check(lib().ibm_backward(h, dJ_dCd, dJ_dNu, _ptr(dX), _ptr(dT)), h)
     return dX[: n_kept * dim].reshape(n_kept, dim), dT[:n_kept]
+
+
+def ibm_adjoint_workspace_bytes(desc: GridDescC, max_markers: int, max_steps: int,
+                                every: int) -> int:
+    return int(lib().ibm_adjoint_workspace_bytes(ctypes.byref(desc), int(max_markers),
+                                                 int(max_steps), int(every)))
+
+
+def ibm_record(h, max_steps: int, every: int, workspace_ptr: int, nbytes: int):
+    _check(lib().ibm_record(h, int(max_steps), int(every), _vp(workspace_ptr),
+                            ctypes.c_size_t(nbytes)), h)
+
+
+def ibm_rhs_vjp(h, U_ptr: int, V_ptr: int, out_ptr: int):
+    _check(lib().ibm_rhs_vjp(h, _vp(U_ptr), _vp(V_ptr), _vp(out_ptr)), h)
 
 
 def ibm_sync(h):
@@ -422,6 +441,7 @@ class Grid:
         self.nbytes = nbytes
         self.h = ibm_create_grid(self.desc, max_markers, self.ws_ptr, nbytes,
                                  self.stream.cuda_stream)
+        self.max_markers = max_markers
         self.n_kept = 0
 
     @classmethod
@@ -526,6 +546,29 @@ class Grid:
         ibm_interpolate(self.h, field.data_ptr(), nc, out.data_ptr())
         self.stream.synchronize()
         return out[: self.n_kept]
+
+    # -- discrete adjoint ------------------------------------------------
+    def record(self, max_steps: int, every: int = 50):
+        """allocate the adjoint workspace and start recording steps"""
+        nb = ibm_adjoint_workspace_bytes(self.desc, self.max_markers, max_steps, every)
+        if nb == 0:
+            raise IbmError(1, "invalid adjoint workspace request")
+        self.adj_ws = self.torch.empty(nb + 256, dtype=self.torch.uint8, device=self.device)
+        ptr = (self.adj_ws.data_ptr() + 255) // 256 * 256
+        ibm_record(self.h, max_steps, every, ptr, nb)
+
+    def backward(self, dJ_dCd: float, dJ_dNu: float):
+        """(dJ/dX (n_kept, dim), dJ/dT_w (n_kept)) over the recorded steps"""
+        return ibm_backward(self.h, dJ_dCd, dJ_dNu, self.n_kept, self.g.dim)
+
+    def rhs_vjp(self, U, V):
+        U = U.to(self.device, self.dtype).contiguous()
+        V = V.to(self.device, self.dtype).contiguous()
+        out = self.torch.empty_like(U)
+        self._order()
+        ibm_rhs_vjp(self.h, U.data_ptr(), V.data_ptr(), out.data_ptr())
+        self.stream.synchronize()
+        return out
 
     def spread(self, R):
         R = R.to(self.device, self.torch.float64).contiguous()

@@ -1,0 +1,163 @@
+"""GPU: the discrete adjoint (ibm_record / ibm_backward / ibm_rhs_vjp)
+against the oracle's adjoint (oracle/adjoint.py: the oracle's step restated
+in PyTorch FP64 and differentiated by reverse mode, itself pinned to the C
+oracle and to finite differences in tests/test_oracle_adjoint.py).
+
+Tolerances.  FP64 grids: the CUDA reverse sweep and the oracle's autograd
+evaluate the same derivative with different rounding order, and the GPU's
+weights come from CG to 1e-12 rather than a dense solve, so gradients agree
+to ~1e-9 of their largest entry (gate 1e-7).  FP32 grids: the forward
+trajectory itself carries FP32 rounding (~1e-7 relative per step, amplified
+by the flux cancellation), the reverse sweep runs in FP32 with FP64
+accumulators; gate 2e-3 of the largest entry.
+"""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2301_09349_gb300 import cases as C
+from paper_2301_09349_gb300 import ibm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup(oracle):
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2301_09349_gb300 import build
+    build.build()
+    oracle.set_threads(os.cpu_count() or 1)
+
+
+def adj():
+    from oracle import adjoint
+    return adjoint
+
+
+MIXED = (C.BC_FREESTREAM, C.BC_ZEROGRAD, C.BC_SLIP, C.BC_SLIP, C.BC_PERIODIC, C.BC_PERIODIC)
+
+
+@pytest.mark.parametrize("dim,fp,tol", [(2, 8, 1e-11), (3, 8, 1e-11), (2, 4, 2e-4), (3, 4, 2e-4)])
+@pytest.mark.parametrize("bc", ["mixed", "periodic", "default"])
+def test_rhs_vjp_matches_oracle(dim, fp, tol, bc):
+    n = (13, 11) if dim == 2 else (9, 7, 6)
+    bcs = {"mixed": MIXED, "periodic": (C.BC_PERIODIC,) * 6, "default": None}[bc]
+    g = C.small_grid(dim, n, h=0.1, fp_bytes=fp, Re=60.0, Mach=0.4, bc=bcs)
+    U = C.random_state(g, seed=23, amp=0.05)
+    rng = np.random.default_rng(5)
+    V = rng.standard_normal(U.shape)
+    dt_ = np.float32 if fp == 4 else np.float64
+    U = U.astype(dt_)
+    V = V.astype(dt_)
+    grid = ibm.Grid(g)
+    grid.record(1, 1)
+    out = grid.rhs_vjp(torch.from_numpy(U), torch.from_numpy(V)).cpu().numpy()
+    ref = adj().rhs_vjp(g, U.astype(np.float64), V.astype(np.float64))
+    err = np.linalg.norm(out - ref) / np.linalg.norm(ref)
+    assert err < tol, err
+
+
+def cylinder(fp, n=(40, 32), h=0.1):
+    g = C.small_grid(2, n, h=h, fp_bytes=fp, Re=100.0, Mach=0.3)
+    X = C.circle_markers(int(np.ceil(np.pi / h)), 0.5, (0.05, -0.03))
+    return g, X, np.linspace(1.2, 1.6, len(X)), 3
+
+
+def gpu_gradient(g, X, Tw, seed, steps, every, a, b, energy_reading=0):
+    grid = ibm.Grid(g, max_markers=len(X), energy_reading=energy_reading)
+    grid.set_markers(X, Tw)
+    U0 = C.initial_state(g, seed)
+    U0 = U0.astype(np.float32 if g.fp_bytes == 4 else np.float64)
+    grid.set_state(U0)
+    grid.record(steps, every)
+    dts = []
+    for _ in range(steps):
+        grid.step(1)
+        dts.append(grid.time()[0])
+    f = grid.forces()
+    J = a * f["Cd"] + b * f["Nu"]
+    Xk, _, idx = grid.markers()
+    U_end = grid.get_state().cpu().numpy()
+    gX, gT = grid.backward(a, b)
+    # the handle's state and forcing are left as they were
+    assert np.array_equal(grid.get_state().cpu().numpy(), U_end)
+    f2 = grid.forces()
+    assert f2["Cd"] == f["Cd"] and f2["heat_rate"] == f["heat_rate"]
+    return J, gX, gT, Xk, np.asarray(Tw)[idx], U0.astype(np.float64), dts
+
+
+def compare(g, X, Tw, seed, steps, every, a, b, tol, energy_reading=0):
+    J, gX, gT, Xk, Twk, U0, dts = gpu_gradient(g, X, Tw, seed, steps, every, a, b,
+                                               energy_reading)
+    Jo, oX, oT = adj().gradient(g, Xk, Twk, U0, dts, a, b, energy_reading=energy_reading)
+    assert abs(J - Jo) <= max(tol, 1e-9) * abs(Jo)
+    ex = np.abs(gX - oX).max() / np.abs(oX).max()
+    et = np.abs(gT - oT).max() / np.abs(oT).max()
+    assert ex < tol and et < tol, (ex, et)
+    return ex, et
+
+
+def test_backward_fp64_2d_matches_oracle():
+    g, X, Tw, seed = cylinder(8)
+    compare(g, X, Tw, seed, steps=3, every=2, a=1.0, b=0.3, tol=1e-7)
+
+
+def test_backward_fp64_2d_energy_reading_total():
+    g, X, Tw, seed = cylinder(8)
+    compare(g, X, Tw, seed, steps=2, every=1, a=0.5, b=1.0, tol=1e-7, energy_reading=1)
+
+
+def test_backward_fp64_2d_many_steps_with_checkpoints():
+    g, X, Tw, seed = cylinder(8, n=(36, 28), h=0.125)
+    compare(g, X, Tw, seed, steps=12, every=5, a=1.0, b=0.2, tol=1e-7)
+
+
+def test_backward_fp64_3d_matches_oracle(oracle):
+    g = C.small_grid(3, (12, 12, 12), h=0.125, fp_bytes=8, Re=80.0, Mach=0.4)
+    X = C.fibonacci_sphere_markers(120, 0.4)
+    compare(g, X, np.full(len(X), 1.5), 9, steps=2, every=1, a=0.5, b=1.0, tol=1e-7)
+
+
+def test_backward_fp32_2d_matches_oracle():
+    g, X, Tw, seed = cylinder(4)
+    compare(g, X, Tw, seed, steps=3, every=2, a=1.0, b=0.3, tol=2e-3)
+
+
+def test_backward_fp32_3d_matches_oracle():
+    g = C.small_grid(3, (16, 16, 12), h=0.125, fp_bytes=4, Re=80.0, Mach=0.4)
+    X = C.fibonacci_sphere_markers(150, 0.45)
+    compare(g, X, np.full(len(X), 0.7), 11, steps=2, every=2, a=1.0, b=0.5, tol=2e-3)
+
+
+def test_adjoint_errors():
+    g, X, Tw, seed = cylinder(8)
+    grid = ibm.Grid(g, max_markers=len(X))
+    grid.set_markers(X, Tw)
+    grid.set_state(C.initial_state(g, seed))
+    with pytest.raises(ibm.IbmError) as e:
+        grid.backward(1.0, 0.0)
+    assert e.value.status == 7
+    nb = ibm.ibm_adjoint_workspace_bytes(grid.desc, len(X), 4, 2)
+    assert nb > 0 and ibm.ibm_adjoint_workspace_bytes(grid.desc, len(X), 0, 2) == 0
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    ptr = (ws.data_ptr() + 255) // 256 * 256
+    with pytest.raises(ibm.IbmError) as e:
+        ibm.ibm_record(grid.h, 4, 2, ptr, nb - 1024)
+    assert e.value.status == 5
+    ibm.ibm_record(grid.h, 4, 2, ptr, nb)
+    with pytest.raises(ibm.IbmError) as e:
+        grid.step(5)
+    assert e.value.status == 5
+    grid.step(2)
+    gX, gT = grid.backward(1.0, 0.0)
+    assert np.all(np.isfinite(gX)) and np.all(np.isfinite(gT))
+    mov = ibm.Grid(g, max_markers=len(X))
+    mov.set_markers(X, Tw, motion=C.Motion(0.05, 1.0, 1))
+    mov.set_state(C.initial_state(g, seed))
+    with pytest.raises(ibm.IbmError) as e:
+        mov.record(4, 2)
+    assert e.value.status == 8
