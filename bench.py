@@ -22,6 +22,11 @@ persistent launch per stage over (case, tile) work items, the step replayed
 from a CUDA graph, tile shape and markers per block autotuned; the plain
 per-case loop of single-grid steps is timed beside it on the same cases.
 With N > 1 the cases are dealt out to the ranks (weak scaling).
+
+--workload adjoint records K steps of the 128^3 FP32 sphere (Ma 0.5,
+Re 100, 804 markers) with a checkpoint every --every steps, then times the
+discrete adjoint (ibm_backward: gradient of C_d + Nu with respect to every
+marker position and wall temperature) over all K steps.
 """
 from __future__ import annotations
 
@@ -55,7 +60,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target seconds of oracle work for the cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="sphere", choices=["sphere", "batched"])
+    p.add_argument("--workload", default="sphere", choices=["sphere", "batched", "adjoint"])
+    p.add_argument("--every", type=int, default=50, help="adjoint checkpoint interval")
     return p.parse_args()
 
 
@@ -582,9 +588,70 @@ def run_batched(args, rank, world, local):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# discrete adjoint
+# ---------------------------------------------------------------------------
+
+ADJ_METRIC = ("reversed cell-steps/s of the discrete adjoint (gradient of C_d + Nu w.r.t. "
+              "marker positions and wall temperatures) at 1 GB300")
+
+
+def run_adjoint(args, rank, world, local):
+    import torch
+    from paper_2301_09349_gb300 import build, ibm
+    build.build()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return 0
+    c = C.adjoint_sphere()
+    g = c.grid
+    stream = torch.cuda.Stream()
+    grid = ibm.Grid(g, max_markers=len(c.X), stream=stream)
+    n_kept = grid.set_markers(c.X, c.Tw)
+    grid.set_state(C.initial_state(g, c.seed).astype(np.float32))
+    S = args.steps
+    grid.record(S, args.every)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    grid.step(S)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    f = grid.forces()
+    uuid = str(torch.cuda.get_device_properties(local).uuid)
+    clocks = ClockSampler(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    gX, gT = grid.backward(1.0, 1.0)        # synchronizing
+    bwd_s = time.perf_counter() - t0
+    clk = clocks.stop()
+    N = g.ncells
+    line = {
+        "metric": ADJ_METRIC, "value": N * S / bwd_s, "unit": UNIT, "n_gpus": 1,
+        "steps": S, "warmup": 0, "ms_per_step": 1e3 * bwd_s / S, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded free stream + 1e-3 density noise; Fibonacci markers)",
+        "config": {"workload": "3D sphere 128^3 FP32, Ma 0.5, Re 100, T_w 1.5, %d markers "
+                               "(%d kept), %d recorded steps, checkpoint every %d"
+                               % (len(c.X), n_kept, S, args.every)},
+        "forward_ms_per_step_recording": fwd_ms / S,
+        "backward_over_forward": (1e3 * bwd_s) / fwd_ms,
+        "J": {"Cd": f["Cd"], "Nu": f["Nu"]},
+        "gradient_norms": {"dJ_dX": float(np.linalg.norm(gX)), "dJ_dTw": float(np.linalg.norm(gT))},
+        "clocks": clk,
+        "timing": "host wall clock around the synchronizing ibm_backward call",
+    }
+    print(json.dumps(line), flush=True)
+    grid.close()
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.workload == "adjoint":
+        return run_adjoint(args, rank, world, local)
     if args.workload == "batched":
         if args.impl == "reference":
             return run_reference_batched(args, rank, world)

@@ -329,8 +329,10 @@ __device__ __forceinline__ void face_vjp(const AdjK<R> &k, const R (&w)[4][DIM +
 }
 
 // lamW (primitive adjoints) += J_L(U)^T V restricted to the faces normal to D
+constexpr int FT = 128;   // flux-reverse CTA: ~150 live registers per face
+
 template <int DIM, int D, typename T>
-__global__ void __launch_bounds__(AT)
+__global__ void __launch_bounds__(FT, 3)
 adj_flux_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ V,
                 double *__restrict__ lamW) {
     using R = T;
@@ -432,49 +434,53 @@ adj_flux_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict
 // out = (dW/dU)^T lamW at every cell (then lamW is cleared):
 // rho-bar = W_rho - sum_m W_um u_m / rho + W_p (gamma-1) |u|^2/2,
 // m-bar = W_u / rho - W_p (gamma-1) u, E-bar = W_p (gamma-1).
+// The sums were accumulated in FP64; this per-cell chain runs in the grid's
+// type (double arithmetic is slow on this GPU).
 template <int DIM, typename T>
 __global__ void __launch_bounds__(AT)
 adj_prim_kernel(const GridParams g, const T *__restrict__ U, double *__restrict__ lamW,
                 T *__restrict__ out) {
+    using R = T;
     constexpr int NC = DIM + 2;
     const long long N = g.N;
-    const double gm1 = g.gamma - 1.0;
+    const AdjK<R> k(g);
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N;
          j += (long long)gridDim.x * blockDim.x) {
-        const double rho = (double)U[j];
-        double v[DIM], ke = 0.0;
+        const R rho = U[j], inv = R(1) / rho;
+        R v[DIM], ke = R(0);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            v[d] = (double)U[(1 + d) * N + j] / rho;
+            v[d] = U[(1 + d) * N + j] * inv;
             ke += v[d] * v[d];
         }
-        double wbv[NC];
+        R wbv[NC];
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-            wbv[q] = lamW[q * N + j];
+            wbv[q] = (R)lamW[q * N + j];
             lamW[q * N + j] = 0.0;
         }
-        const double pb = wbv[NC - 1];
-        double rb = wbv[0] + pb * gm1 * 0.5 * ke;
+        const R pb = wbv[NC - 1] * k.gm1;
+        R rb = wbv[0] + pb * R(0.5) * ke;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            rb -= wbv[1 + d] * v[d] / rho;
-            out[(1 + d) * N + j] = (T)(wbv[1 + d] / rho - pb * gm1 * v[d]);
+            rb -= wbv[1 + d] * v[d] * inv;
+            out[(1 + d) * N + j] = wbv[1 + d] * inv - pb * v[d];
         }
-        out[j] = (T)rb;
-        out[(NC - 1) * N + j] = (T)(pb * gm1);
+        out[j] = rb;
+        out[(NC - 1) * N + j] = pb;
     }
 }
 
 // mu = lam/2 + (dt/2) jtv  (mode 0);  lam = lam/2 + mu + dt jtv  (mode 1)
 template <typename T>
-__global__ void adj_combine_kernel(long long M, int mode, double dt, T *__restrict__ lam,
+__global__ void adj_combine_kernel(long long M, int mode, double dt_d, T *__restrict__ lam,
                                    T *__restrict__ mu, const T *__restrict__ jtv) {
+    const T dt = (T)dt_d, half = T(0.5);
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < M;
          q += (long long)gridDim.x * blockDim.x) {
-        const double l = (double)lam[q], j = (double)jtv[q];
-        if (mode == 0) mu[q] = (T)(0.5 * l + 0.5 * dt * j);
-        else lam[q] = (T)(0.5 * l + (double)mu[q] + dt * j);
+        const T l = lam[q], j = jtv[q];
+        if (mode == 0) mu[q] = half * l + half * dt * j;
+        else lam[q] = half * l + mu[q] + dt * j;
     }
 }
 
@@ -760,10 +766,10 @@ cudaError_t rhs_vjp_t(const GridParams &g, const void *U, const void *V, double 
     const T *u = (const T *)U, *v = (const T *)V;
     for (int D = 0; D < DIM; ++D) {
         const long long faces = g.N / g.n[D] * (g.n[D] + 1);
-        const int nb = grid_for(faces);
-        if (D == 0) adj_flux_kernel<DIM, 0, T><<<nb, AT, 0, s>>>(g, u, v, lamW);
-        else if (D == 1) adj_flux_kernel<DIM, 1, T><<<nb, AT, 0, s>>>(g, u, v, lamW);
-        else adj_flux_kernel<DIM, (DIM == 3 ? 2 : 0), T><<<nb, AT, 0, s>>>(g, u, v, lamW);
+        const int nb = grid_for(faces, FT);
+        if (D == 0) adj_flux_kernel<DIM, 0, T><<<nb, FT, 0, s>>>(g, u, v, lamW);
+        else if (D == 1) adj_flux_kernel<DIM, 1, T><<<nb, FT, 0, s>>>(g, u, v, lamW);
+        else adj_flux_kernel<DIM, (DIM == 3 ? 2 : 0), T><<<nb, FT, 0, s>>>(g, u, v, lamW);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -133,6 +133,43 @@ def test_backward_fp32_3d_matches_oracle():
     compare(g, X, np.full(len(X), 0.7), 11, steps=2, every=2, a=1.0, b=0.5, tol=2e-3)
 
 
+def test_backward_matches_gpu_finite_differences():
+    """Central differences of the GPU's own J (FP64, the recorded step sizes
+    held fixed).  T_w does not enter the weights, so its differences are
+    clean at 1e-6; a marker shift also moves eps~, whose CG solution carries
+    ~1e-9 relative noise, so X is differenced at 1e-4."""
+    g, X, Tw, seed = cylinder(8)
+    a, b = 1.0, 0.3
+    _, gX, gT, Xk, Twk, U0, dts = gpu_gradient(g, X, Tw, seed, 3, 2, a, b)
+
+    def J_of(Xp, Twp):
+        gr = ibm.Grid(g, max_markers=len(Xp))
+        gr.set_markers(Xp, Twp, dedup=False)
+        gr.set_state(U0)
+        for dt in dts:
+            gr.step(1, dt_fixed=dt)
+        f = gr.forces()
+        return a * f["Cd"] + b * f["Nu"]
+
+    rng = np.random.default_rng(7)
+    for _ in range(6):
+        k, ax = int(rng.integers(len(Xk))), int(rng.integers(2))
+        d = 1e-4
+        Xp, Xm = Xk.copy(), Xk.copy()
+        Xp[k, ax] += d
+        Xm[k, ax] -= d
+        fd = (J_of(Xp, Twk) - J_of(Xm, Twk)) / (2 * d)
+        assert abs(gX[k, ax] - fd) <= 2e-3 * np.abs(gX).max(), (k, ax, gX[k, ax], fd)
+    for _ in range(4):
+        k = int(rng.integers(len(Xk)))
+        d = 1e-6
+        Tp, Tm = Twk.copy(), Twk.copy()
+        Tp[k] += d
+        Tm[k] -= d
+        fd = (J_of(Xk, Tp) - J_of(Xk, Tm)) / (2 * d)
+        assert abs(gT[k] - fd) <= 1e-5 * np.abs(gT).max(), (k, gT[k], fd)
+
+
 def test_adjoint_errors():
     g, X, Tw, seed = cylinder(8)
     grid = ibm.Grid(g, max_markers=len(X))
