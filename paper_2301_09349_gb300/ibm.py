@@ -647,3 +647,40 @@ class Batch:
 
     def autotune(self, reps: int = 5) -> dict:
         return ibm_batch_autotune(self.h, reps)
+
+
+def cd_nu_objective():
+    """torch.autograd.Function computing J = a C_d + b Nu after `steps` IBM
+    steps from the state U0, as a function of the marker positions X (n, dim)
+    and wall temperatures Tw (n) (float64 CPU tensors, static markers).  The
+    forward pass runs set_markers / set_state / record / step on `grid`; the
+    backward pass is ibm_backward.  Markers dropped by the one-per-cell dedup
+    get zero gradient."""
+    import torch
+
+    class CdNuObjective(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, X, Tw, grid, U0, steps, a, b, every):
+            Xn = X.detach().cpu().numpy().astype(np.float64)
+            Tn = Tw.detach().cpu().numpy().astype(np.float64)
+            grid.set_markers(Xn, Tn)
+            grid.set_state(U0)
+            grid.record(int(steps), int(every))
+            grid.step(int(steps))
+            f = grid.forces()
+            ctx.grid, ctx.a, ctx.b, ctx.n, ctx.dim = grid, float(a), float(b), len(Xn), Xn.shape[1]
+            return torch.tensor(ctx.a * f["Cd"] + ctx.b * f["Nu"], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            gXk, gTk = ctx.grid.backward(ctx.a, ctx.b)
+            _, _, idx = ctx.grid.markers()
+            gX = np.zeros((ctx.n, ctx.dim))
+            gT = np.zeros(ctx.n)
+            gX[idx] = gXk
+            gT[idx] = gTk
+            s = float(gJ)
+            return (torch.from_numpy(gX * s), torch.from_numpy(gT * s),
+                    None, None, None, None, None, None)
+
+    return CdNuObjective

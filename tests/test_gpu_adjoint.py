@@ -170,6 +170,30 @@ def test_backward_matches_gpu_finite_differences():
         assert abs(gT[k] - fd) <= 1e-5 * np.abs(gT).max(), (k, gT[k], fd)
 
 
+def test_autograd_function_returns_the_adjoint_gradient():
+    g, X, Tw, seed = cylinder(8)
+    U0 = C.initial_state(g, seed)
+    grid = ibm.Grid(g, max_markers=len(X))
+    Xt = torch.tensor(X, requires_grad=True)
+    Tt = torch.tensor(Tw, requires_grad=True)
+    J = ibm.cd_nu_objective().apply(Xt, Tt, grid, U0, 3, 1.0, 0.3, 2)
+    (2.0 * J).backward()
+    ref = ibm.Grid(g, max_markers=len(X))
+    ref.set_markers(X, Tw)
+    ref.set_state(U0)
+    ref.record(3, 2)
+    ref.step(3)
+    f = ref.forces()
+    assert float(J) == 1.0 * f["Cd"] + 0.3 * f["Nu"]
+    gX, gT = ref.backward(1.0, 0.3)
+    _, _, idx = ref.markers()
+    # the flux transpose sums with FP64 atomics: equal to rounding, not bitwise
+    assert np.allclose(Xt.grad.numpy()[idx], 2.0 * gX, rtol=1e-10, atol=1e-12 * np.abs(gX).max())
+    assert np.allclose(Tt.grad.numpy()[idx], 2.0 * gT, rtol=1e-10, atol=1e-12 * np.abs(gT).max())
+    dropped = np.setdiff1d(np.arange(len(X)), idx)
+    assert np.all(Xt.grad.numpy()[dropped] == 0.0)
+
+
 def test_adjoint_errors():
     g, X, Tw, seed = cylinder(8)
     grid = ibm.Grid(g, max_markers=len(X))
