@@ -189,6 +189,13 @@ ibm_status ibm_backward(ibm_grid *g, double dJ_dCd, double dJ_dNu, double *dJ_dX
  * type).  Needs ibm_record's workspace (FP64 scratch).  Asynchronous. */
 ibm_status ibm_rhs_vjp(ibm_grid *g, const void *U, const void *V, void *out);
 
+/* Surface pressure coefficient at every kept marker from the current state:
+ * C_p,k = (I[p]_k - p_inf) / (rho_inf U_inf^2 / 2), with p = (gamma - 1)
+ * (rho E - |rho u|^2/(2 rho)) interpolated by the weights of Eq. interp
+ * (the paper plots C_p around the body, Sec. 3).  cp: n_kept host doubles.
+ * Synchronizes. */
+ibm_status ibm_surface_pressure(ibm_grid *g, double *cp);
+
 /* Wait for the handle's stream and report any recorded device error. */
 ibm_status ibm_sync(ibm_grid *g);
 

@@ -257,6 +257,17 @@ def forces(g, eps_t, G, H, Tw, dt):
     return f, heat.value, Cd.value, Cl.value, Nu.value
 
 
+def surface_pressure(g, X, U):
+    """C_p,k = (I[p]_k - p_inf) / (1/2): the pressure p = (gamma - 1)(rho E -
+    |rho u|^2/(2 rho)) of every cell, interpolated to the markers (Eq. interp)."""
+    U = _f64(U).reshape(g.ncomp, -1)
+    rho = U[0]
+    msq = (U[1: g.dim + 1] ** 2).sum(axis=0)
+    p = (g.gamma - 1.0) * (U[g.dim + 1] - 0.5 * msq / rho)
+    p_inf = 1.0 / (g.gamma * g.Mach * g.Mach)
+    return 2.0 * (interp(g, X, p.reshape((1,) + U.shape[1:]))[:, 0] - p_inf)
+
+
 def motion(X0, amp, freq, axis, t):
     X0 = _f64(X0)
     ns, dim = X0.shape

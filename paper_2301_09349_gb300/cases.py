@@ -215,6 +215,28 @@ def oscillating_cylinder(scale_div: int = 1, seed: int = 3) -> Case:
                 Motion(amp=0.2, freq=0.2, axis=1), 5000, seed)
 
 
+# Natural shedding Strouhal number f_0 D / U_inf of the fixed cylinder at Re
+# 100, Ma 0.3: as in the paper (Sec. 5) it comes from a preliminary run of the
+# fixed cylinder on the same kind of grid, here studies.fixed_cylinder_strouhal
+# at h = D/16 (0.1801); it sets the streamwise forcing frequency f_c = 2 f_0.
+ST0_RE100 = 0.180
+
+
+def streamwise_oscillating_cylinder(scale_div: int = 1, f0: float = ST0_RE100,
+                                    seed: int = 6) -> Case:
+    """2D cylinder oscillating in the streamwise direction (Sec. 5):
+    x(t) = x(0) + A sin(2 pi f_c t), A = 0.14 D, f_c = 2 f_0; Ma 0.3, Re 100,
+    T_w = T_inf (temperature ratio 1); 1024x512 over [-8,24]x[-8,8], FP32.
+    `scale_div` divides the resolution for reduced-size tests."""
+    n = (1024 // scale_div, 512 // scale_div, 1)
+    h = (1.0 / 32.0) * scale_div
+    g = GridDesc(dim=2, n=n, lo=(-8.0, -8.0, 0.0), h=h, fp_bytes=4, Re=100.0, Mach=0.3,
+                 bc=_bc_for(2, 0.3), tile=(16, 16, 1))
+    X = circle_markers(int(math.ceil(math.pi / h)))
+    return Case(f"streamwise_oscillating_cylinder_{n[0]}x{n[1]}", g, X, np.full(len(X), 1.0),
+                None, Motion(amp=0.14, freq=2.0 * f0, axis=0), 5000, seed)
+
+
 def adjoint_sphere(seed: int = 5) -> Case:
     """3D sphere 128^3 over [-3,5]x[-4,4]^2, Fibonacci markers at one-cell
     spacing (804), Ma 0.5, Re 100."""

@@ -140,6 +140,7 @@ void layout(ibm_grid *g, const ibm_grid_desc &d, int cap, char *base, size_t *to
     m.rhoL = c.take<double>(cap);
     m.G = c.take<double>((size_t)cap * dim);
     m.H = c.take<double>(cap);
+    m.cp = c.take<double>(cap);
     m.keys[0] = c.take<unsigned>(cap);
     m.keys[1] = c.take<unsigned>(cap);
     m.perm[0] = c.take<int>(cap);
@@ -678,6 +679,20 @@ ibm_status ibm_get_marker_forcing(ibm_grid *g, double *rhoL, double *F, double *
     if (Q)
         for (int i = 0; i < ns; ++i) Q[i] *= a;
     return IBM_OK;
+}
+
+ibm_status ibm_surface_pressure(ibm_grid *g, double *cp) {
+    if (!g) return IBM_ERR_ARG;
+    if (!g->has_state) return fail(g, IBM_ERR_STATE, "no state set");
+    const int ns = g->mb.ns;
+    if (ns > 0 && !cp) return fail(g, IBM_ERR_ARG, "null output");
+    if (ns > 0) {
+        CU(launch_surface_pressure(g->gp, g->desc.fp_bytes, g->U[g->cur], g->mb, g->stream),
+           "surface pressure");
+        CU(cudaMemcpyAsync(cp, g->mb.cp, sizeof(double) * ns, cudaMemcpyDeviceToHost, g->stream),
+           "read cp");
+    }
+    return check_device(g);
 }
 
 ibm_status ibm_get_bins(ibm_grid *g, int *tile_off, int *perm, unsigned *keys, int *n_tiles) {

@@ -130,6 +130,7 @@ struct MarkerBuffers {
     double *frac_d;          // ns*3 offsets (X - lo)/h - cell, in [0, 1)
     float *frac_f;           // the same offsets in single precision
     double *rhoL, *G, *H;    // last forcing: rho_L, dt*F (ns*dim), dt*Q
+    double *cp;              // ns surface pressure coefficients (ibm_surface_pressure)
     unsigned *keys[2];       // radix-sort ping-pong
     int *perm[2];
     int sorted;              // which of keys/perm holds the sorted order
@@ -158,6 +159,9 @@ cudaError_t launch_spread_apply(const GridParams &g, int fp_bytes, void *U,
 // band maxima (nbs = 0 when the spread kernel did not run)
 cudaError_t launch_finish(const GridParams &g, const MarkerBuffers &m, const FluidBuffers &fb,
                           int nb, int nbs, double dt_fixed, cudaStream_t s);
+// cp[k] = (I[p]_k - p_inf) / (rho_inf U_inf^2 / 2) at every marker
+cudaError_t launch_surface_pressure(const GridParams &g, int fp_bytes, const void *U,
+                                    const MarkerBuffers &m, cudaStream_t s);
 cudaError_t launch_interpolate_op(const GridParams &g, int fp_bytes, const void *field, int nc,
                                   const MarkerBuffers &m, double *out, cudaStream_t s);
 cudaError_t launch_spread_op(const GridParams &g, int fp_bytes, const double *R, int nc,

@@ -794,6 +794,42 @@ __global__ void batch_gather_kernel(const BatchCase *__restrict__ cases, int nca
 // operators for the diagnostic entry points
 // ---------------------------------------------------------------------------
 
+// C_p at the markers: p = (gamma - 1)(rho E - |rho u|^2 / (2 rho)) interpolated
+// with the weights of Eq. interp (FP64, one warp per marker, lane per cell).
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256)
+surface_pressure_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuffers m) {
+    constexpr int NS = DIM == 3 ? 27 : 9;
+    const int lane = threadIdx.x & 31;
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (k >= m.ns) return;
+    double acc = 0.0;
+    if (lane < NS) {
+        double fr[3] = {0.0, 0.0, 0.0};
+        int ck[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            ck[d] = m.cell[(long long)k * 3 + d];
+            fr[d] = m.frac_d[(long long)k * 3 + d];
+        }
+        int cell[3];
+        const double w = lane_weight<DIM, double>(fr, ck, lane, cell);
+        const long long j = cell[0] + (long long)g.n[0] * (cell[1] + (long long)g.n[1] * cell[2]);
+        const double rho = (double)U[j];
+        double msq = 0.0;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const double md = (double)U[(1 + d) * g.N + j];
+            msq += md * md;
+        }
+        const double p = (g.gamma - 1.0) * ((double)U[(DIM + 1) * g.N + j] - 0.5 * msq / rho);
+        acc = w * p;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) m.cp[k] = 2.0 * (acc - g.p_inf);
+}
+
 template <int DIM, typename T>
 __global__ void interpolate_op_kernel(const GridParams g, const T *__restrict__ field, int nc,
                                       const MarkerBuffers m, double *__restrict__ out) {
@@ -1016,6 +1052,20 @@ cudaError_t launch_band_mask(const GridParams &g, const MarkerBuffers &m, int gr
     if (e != cudaSuccess) return e;
     tile_lists_kernel<<<1, SORT_T, 0, s>>>(g.n_tiles, m.occ_flag, m.band_flag, m.occ_list,
                                            m.band_list, m.counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_surface_pressure(const GridParams &g, int fp_bytes, const void *U,
+                                    const MarkerBuffers &m, cudaStream_t s) {
+    if (m.ns <= 0) return cudaSuccess;
+    const int nb = (m.ns * 32 + 255) / 256;
+    if (g.dim == 3) {
+        if (fp_bytes == 4) surface_pressure_kernel<3, float><<<nb, 256, 0, s>>>(g, (const float *)U, m);
+        else surface_pressure_kernel<3, double><<<nb, 256, 0, s>>>(g, (const double *)U, m);
+    } else {
+        if (fp_bytes == 4) surface_pressure_kernel<2, float><<<nb, 256, 0, s>>>(g, (const float *)U, m);
+        else surface_pressure_kernel<2, double><<<nb, 256, 0, s>>>(g, (const double *)U, m);
+    }
     return cudaGetLastError();
 }
 

@@ -89,6 +89,7 @@ SIGNATURES = [
                                                       ctypes.c_int, ctypes.c_int]),
     ("ibm_record", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t]),
     ("ibm_rhs_vjp", ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    ("ibm_surface_pressure", ctypes.c_int, [_vp, _dp]),
     ("ibm_batch_workspace_bytes", ctypes.c_size_t, [ctypes.c_int, ctypes.POINTER(GridDescC), _ip]),
     ("ibm_create_batch", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(GridDescC), _ip, _vp,
                                         ctypes.c_size_t, _vp, ctypes.POINTER(_vp)]),
@@ -257,6 +258,12 @@ def ibm_record(h, max_steps: int, every: int, workspace_ptr: int, nbytes: int):
 
 def ibm_rhs_vjp(h, U_ptr: int, V_ptr: int, out_ptr: int):
     _check(lib().ibm_rhs_vjp(h, _vp(U_ptr), _vp(V_ptr), _vp(out_ptr)), h)
+
+
+def ibm_surface_pressure(h, n_kept: int) -> np.ndarray:
+    cp = np.zeros(max(n_kept, 1))
+    _check(lib().ibm_surface_pressure(h, _ptr(cp)), h)
+    return cp[:n_kept]
 
 
 def ibm_sync(h):
@@ -515,6 +522,10 @@ class Grid:
 
     def markers(self):
         return ibm_get_markers(self.h, self.n_kept, self.g.dim)
+
+    def surface_pressure(self):
+        """C_p at the kept markers from the current state"""
+        return ibm_surface_pressure(self.h, self.n_kept)
 
     def marker_forcing(self):
         return ibm_get_marker_forcing(self.h, self.n_kept, self.g.dim)

@@ -1,0 +1,87 @@
+"""GPU: the method variants and diagnostics - surface pressure coefficient,
+the streamwise-oscillating cylinder of Sec. 5, the self-convergence of C_d
+(App. C) and the fixed cylinder's shedding Strouhal number."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_2301_09349_gb300 import cases as C
+from paper_2301_09349_gb300 import ibm, studies
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _setup(oracle):
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2301_09349_gb300 import build
+    build.build()
+    oracle.set_threads(os.cpu_count() or 1)
+
+
+@pytest.mark.parametrize("fp,tol", [(8, 1e-12), (4, 1e-6)])
+def test_surface_pressure_matches_oracle(oracle, fp, tol):
+    c = C.heated_cylinder()
+    g = c.grid
+    if fp == 4:
+        import dataclasses
+        g = dataclasses.replace(g, fp_bytes=4)
+    grid = ibm.Grid(g, max_markers=len(c.X))
+    grid.set_markers(c.X, c.Tw)
+    grid.set_state(C.initial_state(g, c.seed).astype(np.float32 if fp == 4 else np.float64))
+    grid.step(3)
+    cp = grid.surface_pressure()
+    Xk, _, _ = grid.markers()
+    ref = oracle.surface_pressure(g, Xk, grid.get_state().cpu().numpy().astype(np.float64))
+    p_inf = 1.0 / (g.gamma * g.Mach ** 2)
+    assert np.max(np.abs(cp - ref)) <= tol * 2.0 * p_inf
+
+
+def test_streamwise_oscillating_cylinder_matches_oracle(oracle):
+    c = C.streamwise_oscillating_cylinder(scale_div=4)
+    g = c.grid
+    U0 = C.initial_state(g, c.seed).astype(np.float32)
+    grid = ibm.Grid(g, max_markers=len(c.X))
+    nk = grid.set_markers(c.X, c.Tw, motion=c.motion)
+    grid.set_state(U0)
+    run = oracle.Run(g, c.X, c.Tw, motion=c.motion)
+    assert nk == len(run.X)
+    U = U0.astype(np.float64)
+    for s in range(5):
+        grid.step(1)
+        dtg = grid.time()[0]
+        Ug = grid.get_state().cpu().numpy()
+        U = run.step(U, dt_fixed=dtg)
+        for gr in ([0], [1, 2], [3]):
+            e = np.linalg.norm(Ug[gr] - U[gr]) / np.linalg.norm(U[gr])
+            assert e < 1e-5, (s, gr, e)
+    Xg, _, _ = grid.markers()
+    assert np.max(np.abs(Xg - run.X)) < 1e-12       # markers moved along x only
+    assert np.max(np.abs(Xg[:, 1] - run.X0[:, 1])) == 0.0
+    fo = run.forces()
+    fg = grid.forces()
+    assert abs(fg["Cd"] - fo[2]) <= 2e-3 * abs(fo[2])
+
+
+def test_self_convergence_of_drag():
+    rows, orders = studies.self_convergence(divs=(8, 16, 32, 64), T=2.0)
+    cds = [r[2] for r in rows]
+    assert all(np.isfinite(cds)) and all(0.5 < cd < 20.0 for cd in cds)
+    # successive differences shrink under refinement (the observed orders are
+    # recorded in the design notes)
+    d = np.abs(np.diff(cds))
+    assert d[-1] < d[0], (rows, orders)
+    # measured 1.39 and 1.50 on a GB300: between first and second order, rising
+    assert all(o > 1.2 for o in orders), orders
+    print("self-convergence", rows, orders)
+
+
+def test_fixed_cylinder_sheds_at_a_plausible_strouhal_number():
+    St, t, cl = studies.fixed_cylinder_strouhal()
+    assert np.max(np.abs(cl[t > 150.0])) > 0.05       # shedding has developed
+    assert 0.15 < St < 0.21, St                       # measured 0.180 at D/16
+    print("Strouhal", St)
