@@ -79,6 +79,9 @@ typedef struct {
     int tile[3];           /* marker-binning tile in cells per axis (tile[2] = 1 in 2D) */
     double D;              /* reference length for Cd, Cl, Nu */
     int energy_reading;    /* 0: heat source on internal energy (Eq. e_centralF2); 1: on total energy */
+    int forcing_per_stage; /* 0: forcing once after the SSP-RK2 predictor (App. B, default);
+                              1: after each stage; the step's reported sources are then
+                              G1/2 + G2, the first stage's reaching U^{n+1} with weight 1/2 */
 } ibm_grid_desc;
 
 /* Prescribed rigid motion of all markers (Sec. 5):

@@ -752,15 +752,49 @@ void or_spread_apply(const or_desc *g, int ns, const double *X, const double *ep
 
 /* One IBM step: predictor (f = q = 0), interpolate and force, spread and
  * re-solve with the sources (App. B).  Returns dt; G, H (dt F, dt Q) and
- * rhoL per marker are returned for diagnostics. */
+ * rhoL per marker are returned for diagnostics.
+ *
+ * Variant forcing_per_stage = 1: the direct forcing is applied after EACH
+ * SSP-RK2 stage instead of once after the predictor:
+ *   U1 = U + dt L(U);            U1 <- forced(U1)   (sources G1, H1)
+ *   U* = U/2 + (U1 + dt L(U1))/2; U^{n+1} = forced(U*) (sources G2, H2).
+ * The forcing of the first stage reaches U^{n+1} with weight 1/2, so the
+ * sources of the step (what the body exerts over dt) are G = G1/2 + G2 and
+ * H = H1/2 + H2; rhoL is the second stage's. */
 double or_step(const or_desc *g, int ns, const double *X, const double *Ub, const double *Tw,
                const double *eps_t, const double *U, double *Unew, double dt_fixed,
                double *G, double *H, double *rhoL) {
-    double dt = or_fluid_predictor(g, U, Unew, dt_fixed);
-    if (ns > 0) {
-        or_interp_force(g, ns, X, Ub, Tw, Unew, rhoL, G, H);
-        or_spread_apply(g, ns, X, eps_t, G, H, Unew);
+    if (!g->forcing_per_stage || ns == 0) {
+        double dt = or_fluid_predictor(g, U, Unew, dt_fixed);
+        if (ns > 0) {
+            or_interp_force(g, ns, X, Ub, Tw, Unew, rhoL, G, H);
+            or_spread_apply(g, ns, X, eps_t, G, H, Unew);
+        }
+        return dt;
     }
+    long N = n_cells(g), M = N * n_comp(g);
+    int dim = g->dim;
+    double dt = dt_fixed > 0.0 ? dt_fixed : or_dt(g, U);
+    double *L = (double *)malloc(sizeof(double) * (size_t)M);
+    double *U1 = (double *)malloc(sizeof(double) * (size_t)M);
+    double *G1 = (double *)malloc(sizeof(double) * (size_t)ns * dim);
+    double *H1 = (double *)malloc(sizeof(double) * (size_t)ns);
+    double *r1 = (double *)malloc(sizeof(double) * (size_t)ns);
+    or_rhs(g, U, L);
+    for (long q = 0; q < M; ++q) U1[q] = U[q] + dt * L[q];
+    or_interp_force(g, ns, X, Ub, Tw, U1, r1, G1, H1);
+    or_spread_apply(g, ns, X, eps_t, G1, H1, U1);
+    or_rhs(g, U1, L);
+    for (long q = 0; q < M; ++q) Unew[q] = 0.5 * U[q] + 0.5 * (U1[q] + dt * L[q]);
+    or_interp_force(g, ns, X, Ub, Tw, Unew, rhoL, G, H);
+    or_spread_apply(g, ns, X, eps_t, G, H, Unew);
+    for (long k = 0; k < (long)ns * dim; ++k) G[k] += 0.5 * G1[k];
+    for (int k = 0; k < ns; ++k) H[k] += 0.5 * H1[k];
+    free(L);
+    free(U1);
+    free(G1);
+    free(H1);
+    free(r1);
     return dt;
 }
 

@@ -27,6 +27,7 @@ typedef struct {
     int tile[3];      /* binning tile (cells per axis) */
     double D;         /* reference length */
     int energy_reading; /* 0: forcing on internal energy (default); 1: on total energy */
+    int forcing_per_stage; /* 0: forcing once after the predictor (default); 1: after each stage */
 } or_desc;
 
 /* --- regularised delta (Sec. 2.2) --- */

@@ -31,6 +31,7 @@ class OrDesc(ctypes.Structure):
         ("Re", ctypes.c_double), ("Mach", ctypes.c_double), ("S", ctypes.c_double),
         ("cfl", ctypes.c_double), ("bc", ctypes.c_int * 6), ("tile", ctypes.c_int * 3),
         ("D", ctypes.c_double), ("energy_reading", ctypes.c_int),
+        ("forcing_per_stage", ctypes.c_int),
     ]
 
 
@@ -87,6 +88,7 @@ def desc(g, energy_reading: int = 0) -> OrDesc:
         d.bc[i] = int(g.bc[i])
     d.D = g.D
     d.energy_reading = energy_reading
+    d.forcing_per_stage = int(getattr(g, "forcing_per_stage", 0))
     return d
 
 

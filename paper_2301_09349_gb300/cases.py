@@ -46,6 +46,7 @@ class GridDesc:
     bc: tuple = (BC_FREESTREAM, BC_ZEROGRAD, BC_SLIP, BC_SLIP, BC_SLIP, BC_SLIP)
     tile: tuple = (8, 8, 8)
     D: float = 1.0             # reference length (body diameter)
+    forcing_per_stage: int = 0  # 1: force after each SSP-RK2 stage, not once per step
 
     @property
     def ncomp(self) -> int:

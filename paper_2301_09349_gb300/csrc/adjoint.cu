@@ -955,6 +955,8 @@ ibm_status ibm_record(ibm_grid *g, int max_steps, int every, void *dev_workspace
         return afail(g, IBM_ERR_ARG, "adjoint workspace must be non-null and 256-byte aligned");
     if (g->moving && g->mb.ns > 0)
         return afail(g, IBM_ERR_UNSUPPORTED, "the adjoint takes static markers only");
+    if (g->desc.forcing_per_stage)
+        return afail(g, IBM_ERR_UNSUPPORTED, "the adjoint reverses the once-per-step forcing only");
     const size_t need = adj_layout(g->desc, g->max_markers, max_steps, every, nullptr, nullptr);
     if (bytes < need)
         return afail(g, IBM_ERR_WORKSPACE,

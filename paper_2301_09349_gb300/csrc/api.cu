@@ -65,6 +65,8 @@ const char *check_desc(const ibm_grid_desc *d) {
     size_t staged = (size_t)(d->tile[0] + 2) * (d->tile[1] + 2) * (d->dim == 3 ? d->tile[2] + 2 : 1);
     if (staged * (d->dim + 2) * sizeof(double) > 160 * 1024) return "tile too large for staging";
     if (d->energy_reading != 0 && d->energy_reading != 1) return "energy_reading must be 0 or 1";
+    if (d->forcing_per_stage != 0 && d->forcing_per_stage != 1)
+        return "forcing_per_stage must be 0 or 1";
     return nullptr;
 }
 
@@ -97,6 +99,7 @@ GridParams make_params(const ibm_grid_desc &d) {
     g.n_tiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
     g.cells_per_tile = g.tile[0] * g.tile[1] * g.tile[2];
     g.energy_reading = d.energy_reading;
+    g.forcing_per_stage = d.forcing_per_stage;
     g.f = float_consts(g);
     return g;
 }
@@ -151,7 +154,7 @@ void layout(ibm_grid *g, const ibm_grid_desc &d, int cap, char *base, size_t *to
     m.occ_list = c.take<int>(gp.n_tiles);
     m.band_list = c.take<int>(gp.n_tiles);
     m.counts = c.take<int>(4);
-    m.sums = c.take<double>(8);
+    m.sums = c.take<double>(16);
     m.bandmax = c.take<double>(kMaxPersistentCtas);
     m.band_bits = c.take<unsigned>((size_t)(gp.N / 32 + 1));
     m.t = c.take<double>(1);
@@ -349,7 +352,7 @@ ibm_status ibm_create_grid(const ibm_grid_desc *desc, int max_markers, void *dev
     if (e == cudaSuccess) e = cudaMemsetAsync(g->fb.counter, 0, 4 * sizeof(unsigned), g->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->err_d, 0, 4 * sizeof(int), g->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->scratch_d, 0, 8 * sizeof(double), g->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->mb.sums, 0, 8 * sizeof(double), g->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->mb.sums, 0, 16 * sizeof(double), g->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->mb.t, 0, sizeof(double), g->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->mb.steps, 0, sizeof(long long), g->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->mb.counts, 0, 4 * sizeof(int), g->stream);
@@ -503,7 +506,7 @@ ibm_status ibm_set_markers(ibm_grid *g, int n, const double *X0, const double *U
         CU(cudaMemsetAsync(g->mb.G, 0, bx, g->stream), "clear G");
         CU(cudaMemsetAsync(g->mb.H, 0, sizeof(double) * ns, g->stream), "clear H");
     }
-    CU(cudaMemsetAsync(g->mb.sums, 0, 8 * sizeof(double), g->stream), "clear sums");
+    CU(cudaMemsetAsync(g->mb.sums, 0, 16 * sizeof(double), g->stream), "clear sums");
     g->mb.ns = ns;
     g->kept = keep;
     g->Tw_h = Twh;
@@ -568,6 +571,16 @@ ibm_status ibm_step(ibm_grid *g, int nsteps, double dt_fixed) {
                "motion");
             ibm_status st = rebuild_markers(g, 1);
             if (st != IBM_OK) return st;
+            CU(prof_end(g, rec), "profile");
+        }
+        if (g->desc.forcing_per_stage && g->mb.ns > 0) {
+            // variant: the first stage is forced too; its sources are summed now
+            CU(prof_begin(g, IBM_PROF_INTERP, 2, &rec), "profile");
+            CU(launch_interp_force(g->gp, fpb, U1, g->mb, ctas, g->stream), "interp/force (stage 1)");
+            CU(launch_partial_sums(g->gp, g->mb, g->stream), "stage-1 sums");
+            CU(prof_end(g, rec), "profile");
+            CU(prof_begin(g, IBM_PROF_SPREAD, 1, &rec), "profile");
+            CU(launch_spread_apply(g->gp, fpb, U1, g->mb, ctas, g->stream), "spread/apply (stage 1)");
             CU(prof_end(g, rec), "profile");
         }
         CU(prof_begin(g, IBM_PROF_STAGE2, 1, &rec), "profile");

@@ -144,6 +144,10 @@ const char *check_batch(int ncases, const ibm_grid_desc *descs, const int *max_m
             *st = IBM_ERR_UNSUPPORTED;
             return "batches hold 2D grids only";
         }
+        if (descs[c].forcing_per_stage) {
+            *st = IBM_ERR_UNSUPPORTED;
+            return "batches force once per step (forcing_per_stage = 0)";
+        }
         if (descs[c].fp_bytes != descs[0].fp_bytes) {
             *st = IBM_ERR_UNSUPPORTED;
             return "all cases of a batch need the same fp_bytes";

@@ -47,6 +47,7 @@ struct GridParams {
     int n_tiles;
     int cells_per_tile;
     int energy_reading;
+    int forcing_per_stage;
     FloatConsts f;        // FP32 copies of the constants above
 };
 

@@ -138,7 +138,8 @@ struct MarkerBuffers {
     int *occ_flag, *band_flag;  // n_tiles
     int *occ_list, *band_list;  // n_tiles
     int *counts;             // [0] occupied tiles, [1] band tiles
-    double *sums;            // [0..2] sum eps~ G, [3] sum eps~ H, [4] dt of those sums
+    double *sums;            // [0..2] sum eps~ G, [3] sum eps~ H, [4] dt of those sums;
+                             // [8..11] the first stage's sums (forcing per stage)
     double *bandmax;         // per-CTA step-size maxima of the spread kernel
     unsigned *band_bits;     // one bit per cell inside some marker support
     double *t;               // simulated time
@@ -155,6 +156,8 @@ cudaError_t launch_interp_force(const GridParams &g, int fp_bytes, const void *U
                                 const MarkerBuffers &m, int grid_ctas, cudaStream_t s);
 cudaError_t launch_spread_apply(const GridParams &g, int fp_bytes, void *U,
                                 const MarkerBuffers &m, int grid_ctas, cudaStream_t s);
+// sums[8..11] = sum eps~ G, sum eps~ H of the current G, H (fixed order)
+cudaError_t launch_partial_sums(const GridParams &g, const MarkerBuffers &m, cudaStream_t s);
 // force/heat sums, the time update and the next dt from the stage-2 and
 // band maxima (nbs = 0 when the spread kernel did not run)
 cudaError_t launch_finish(const GridParams &g, const MarkerBuffers &m, const FluidBuffers &fb,

@@ -748,7 +748,8 @@ __device__ __forceinline__ void finish_grid(const GridParams &g, int ns, const M
         for (int i = 0; i < 4; ++i) {
             double t = 0.0;
             for (int j = 0; j < FIN_T / 32; ++j) t += s[i][j];
-            m.sums[i] = t;
+            // forcing per stage: the first stage's sources count with weight 1/2
+            m.sums[i] = g.forcing_per_stage ? t + 0.5 * m.sums[8 + i] : t;
         }
         double mx = s[4][0];
         for (int j = 1; j < FIN_T / 32; ++j) mx = fmax(mx, s[4][j]);
@@ -760,6 +761,35 @@ __device__ __forceinline__ void finish_grid(const GridParams &g, int ns, const M
         if (!good) record_error(err, ERR_NONFINITE);
         *dt_ptr = good ? g.cfl / mx : 0.0;
     }
+}
+
+// sum eps~ G and sum eps~ H of the current marker forcing into sums[8..11],
+// in the finish kernel's fixed order
+__global__ void __launch_bounds__(FIN_T)
+partial_sums_kernel(const GridParams g, const MarkerBuffers m) {
+    __shared__ double s[4][FIN_T / 32];
+    const int dim = g.dim;
+    double a[4] = {0, 0, 0, 0};
+    for (int k = threadIdx.x; k < m.ns; k += FIN_T) {
+        const double e = __ldg(m.eps + k);
+        for (int d = 0; d < dim; ++d) a[d] += e * __ldg(m.G + (long long)k * dim + d);
+        a[3] += e * __ldg(m.H + k);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
+    }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int i = 0; i < 4; ++i) s[i][w] = a[i];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 4; ++i) {
+            double t = 0.0;
+            for (int j = 0; j < FIN_T / 32; ++j) t += s[i][j];
+            m.sums[8 + i] = t;
+        }
 }
 
 __global__ void __launch_bounds__(FIN_T)
@@ -1022,6 +1052,12 @@ cudaError_t launch_batch_spread(int fp_bytes, size_t smem, const BatchCase *case
     if (ctas > n_items) ctas = n_items;
     return fp_bytes == 4 ? batch_spread_t<float>(smem, cases, items, n_items, band_max, ctas, s)
                          : batch_spread_t<double>(smem, cases, items, n_items, band_max, ctas, s);
+}
+
+cudaError_t launch_partial_sums(const GridParams &g, const MarkerBuffers &m, cudaStream_t s) {
+    if (m.ns <= 0) return cudaSuccess;
+    partial_sums_kernel<<<1, FIN_T, 0, s>>>(g, m);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_batch_finish(const BatchCase *cases, int ncases, const double *item_max,

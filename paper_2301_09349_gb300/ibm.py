@@ -39,6 +39,7 @@ class GridDescC(ctypes.Structure):
         ("Pr", ctypes.c_double), ("Re", ctypes.c_double), ("Mach", ctypes.c_double),
         ("sutherland_S", ctypes.c_double), ("cfl", ctypes.c_double), ("bc", ctypes.c_int * 6),
         ("tile", ctypes.c_int * 3), ("D", ctypes.c_double), ("energy_reading", ctypes.c_int),
+        ("forcing_per_stage", ctypes.c_int),
     ]
 
 
@@ -163,6 +164,7 @@ def make_desc(g: cases.GridDesc, energy_reading: int = 0) -> GridDescC:
         d.bc[i] = int(g.bc[i])
     d.D = g.D
     d.energy_reading = energy_reading
+    d.forcing_per_stage = int(getattr(g, "forcing_per_stage", 0))
     return d
 
 

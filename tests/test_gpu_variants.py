@@ -85,3 +85,62 @@ def test_fixed_cylinder_sheds_at_a_plausible_strouhal_number():
     assert np.max(np.abs(cl[t > 150.0])) > 0.05       # shedding has developed
     assert 0.15 < St < 0.21, St                       # measured 0.180 at D/16
     print("Strouhal", St)
+
+
+def _run_pair(oracle, g, case, steps, tol, share_eps):
+    U0 = C.initial_state(g, case.seed).astype(np.float32 if g.fp_bytes == 4 else np.float64)
+    grid = ibm.Grid(g, max_markers=len(case.X))
+    nk = grid.set_markers(case.X, case.Tw, motion=case.motion)
+    grid.set_state(U0)
+    run = oracle.Run(g, case.X, case.Tw, motion=case.motion)
+    assert nk == len(run.X)
+    if share_eps:
+        run.eps = grid.markers()[1].copy()
+    U = U0.astype(np.float64)
+    for s in range(steps):
+        grid.step(1)
+        dtg = grid.time()[0]
+        U = run.step(U, dt_fixed=dtg if g.fp_bytes == 4 else 0.0)
+        Ug = grid.get_state().cpu().numpy()
+        for gr in ([0], list(range(1, g.dim + 1)), [g.dim + 1]):
+            e = np.linalg.norm(Ug[gr] - U[gr]) / np.linalg.norm(U[gr])
+            assert e < tol, (s, gr, e)
+    fo = run.forces()
+    fg = grid.forces()
+    return fg, fo
+
+
+def test_forcing_per_stage_fp64_matches_oracle(oracle):
+    import dataclasses
+    c = C.heated_cylinder()
+    g = dataclasses.replace(c.grid, forcing_per_stage=1)
+    fg, fo = _run_pair(oracle, g, c, 10, 1e-11, share_eps=True)
+    assert abs(fg["Cd"] - fo[2]) <= 1e-9 * abs(fo[2])
+    assert abs(fg["heat_rate"] - fo[1]) <= 1e-9 * abs(fo[1])
+    # a different step from the default placement of the forcing
+    g0 = dataclasses.replace(g, forcing_per_stage=0)
+    a = ibm.Grid(g0, max_markers=len(c.X))
+    a.set_markers(c.X, c.Tw)
+    a.set_state(C.initial_state(g0, c.seed))
+    a.step(10)
+    assert abs(a.forces()["Cd"] - fg["Cd"]) > 1e-6 * abs(fg["Cd"])
+
+
+def test_forcing_per_stage_fp32_moving_cylinder(oracle):
+    import dataclasses
+    c = C.oscillating_cylinder(scale_div=4)
+    g = dataclasses.replace(c.grid, forcing_per_stage=1)
+    fg, fo = _run_pair(oracle, g, c, 4, 1e-5, share_eps=False)
+    assert abs(fg["Cd"] - fo[2]) <= 2e-3 * abs(fo[2])
+
+
+def test_forcing_per_stage_is_refused_by_batch_and_adjoint():
+    import dataclasses
+    g = dataclasses.replace(C.small_grid(2, (32, 32), h=0.1, fp_bytes=8), forcing_per_stage=1)
+    with pytest.raises(ibm.IbmError) as e:
+        ibm.Batch([g], [0])
+    assert e.value.status == 8
+    grid = ibm.Grid(g, max_markers=4)
+    with pytest.raises(ibm.IbmError) as e:
+        grid.record(4, 2)
+    assert e.value.status == 8

@@ -277,3 +277,50 @@ def test_motion_law(oracle):
     Xp, _ = oracle.motion(X0, 0.2, 0.2, 1, 0.7 + e)
     Xm, _ = oracle.motion(X0, 0.2, 0.2, 1, 0.7 - e)
     np.testing.assert_allclose(Ub, (Xp - Xm) / (2 * e), atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# variant: forcing after each SSP-RK2 stage
+# ---------------------------------------------------------------------------
+
+def test_per_stage_forcing_single_marker_hits_targets_exactly(oracle):
+    """the last stage's forcing with one marker makes I[u] = U_b, I[T] = T_w"""
+    import dataclasses
+    g = dataclasses.replace(grid2(), forcing_per_stage=1)
+    X = C.random_markers(g, 1, seed=31)
+    U = C.random_state(g, seed=32, amp=0.02)
+    Ub = np.array([[0.05, -0.02]])
+    Tw = np.array([1.21])
+    rc, eps, _, _ = oracle.quadrature(g, X)
+    dt, Un, G, H, rhoL = oracle.step(g, X, Ub, Tw, eps, U)
+    Un = Un.reshape(g.ncomp, -1)
+    rho_e = Un[-1] - 0.5 * (Un[1] ** 2 + Un[2] ** 2) / Un[0]
+    I = oracle.interp(g, X, np.stack([Un[0], Un[1], Un[2], rho_e]))
+    cv = (1.0 / (g.gamma * g.Mach ** 2)) / (g.gamma - 1.0)
+    np.testing.assert_allclose(I[0, 1:3] / I[0, 0], Ub[0], atol=1e-13)
+    np.testing.assert_allclose(I[0, 3] / I[0, 0] / cv, Tw[0], rtol=1e-13)
+    # and it differs from the once-per-step variant
+    _, Ud, _, _, _ = oracle.step(g, X, Ub, Tw, eps, U)
+    g0 = dataclasses.replace(g, forcing_per_stage=0)
+    _, U0, _, _, _ = oracle.step(g0, X, Ub, Tw, eps, U)
+    assert np.abs(Ud - U0).max() > 1e-8
+
+
+def test_per_stage_forcing_reported_force_is_the_momentum_given(oracle):
+    """With periodic boundaries sum_j L_j = 0, so the momentum the step adds
+    is h^d (sum f1 / 2 + sum f2): the body force of the step's sources
+    G = G1/2 + G2 must be minus that over dt (conservation, not a retyping)."""
+    import dataclasses
+    g = dataclasses.replace(grid2(n=(24, 20), h=0.125, bc=(C.BC_PERIODIC,) * 6, Re=50.0),
+                            forcing_per_stage=1)
+    X = C.circle_markers(12, 0.4, (0.01, 0.02))
+    rc, keep = oracle.dedup(g, X)
+    X = X[keep]
+    Tw = np.full(len(X), 1.3)
+    rc, eps, _, _ = oracle.quadrature(g, X)
+    U = C.random_state(g, seed=33, amp=0.02)
+    dt, Un, G, H, rhoL = oracle.step(g, X, None, Tw, eps, U)
+    f, heat, Cd, Cl, Nu = oracle.forces(g, eps, G, H, Tw, dt)
+    hd = g.h ** 2
+    dmom = hd * (Un.reshape(4, -1)[1:3] - U.reshape(4, -1)[1:3]).sum(1) / dt
+    np.testing.assert_allclose(f[:2], -dmom, rtol=1e-9, atol=1e-12)
