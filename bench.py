@@ -355,6 +355,9 @@ def run_ours(args, rank, world, local):
             rate, det = oracle_rate(c, args.cpu_seconds, 1, 0, threads)
             line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads,
                                     "kind": "oracle", "sample": det["sample"]}
+            rate1, det1 = oracle_rate(c, max(2.0, args.cpu_seconds / 5.0), 1, 0, 1)
+            line["cpu_baseline_single_thread"] = {"value": rate1, "unit": UNIT, "cores": 1,
+                                                  "kind": "oracle", "sample": det1["sample"]}
         print(json.dumps(line), flush=True)
     grid.close()
     if dist is not None:

@@ -94,3 +94,18 @@ def test_null_batch_is_an_argument_error(lib):
     assert lib.ibm_batch_set_tuning(None, None) == 1
     assert lib.ibm_batch_get_tuning(None, None) == 1
     assert lib.ibm_batch_case(None, 0) is None
+
+
+def test_batched_cases_are_dealt_to_ranks_exactly_once():
+    import importlib.util
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    names = [c.name for c in cases.batched_cylinders()]
+    for world in (1, 2, 3, 8):
+        dealt = [c.name for r in range(world) for c in bench.batch_cases(r, world)]
+        assert sorted(dealt) == sorted(names)
+        sizes = [len(bench.batch_cases(r, world)) for r in range(world)]
+        assert max(sizes) - min(sizes) <= 1
