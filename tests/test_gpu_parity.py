@@ -342,6 +342,29 @@ def test_long_run_1000_steps(oracle):
     assert np.all(err < 1e-3), err
 
 
+@pytest.mark.skipif(os.environ.get("IBM_LONG_RUNS") != "1",
+                    reason="1000 oracle steps at 128^3 (~3 min of host time); IBM_LONG_RUNS=1")
+def test_long_run_1000_steps_128(oracle):
+    """The 1000-step gate at 128^3 with markers at one-cell spacing: the GPU
+    (FP32, its own step sizes) and the FP64 oracle (its own step sizes) from
+    the same initial state."""
+    c = C.heated_sphere(n=128)
+    g = c.grid
+    U0 = C.initial_state(g, c.seed).astype(np.float32)
+    grid = ibm.Grid(g, max_markers=len(c.X))
+    grid.set_markers(c.X, c.Tw)
+    grid.set_state(U0)
+    grid.step(1000)
+    Ug = grid.get_state().cpu().numpy()
+    run = oracle.Run(g, c.X, c.Tw)
+    U = U0.astype(np.float64)
+    for _ in range(1000):
+        U = run.step(U)
+    err = rel_l2(Ug, U.reshape(Ug.shape))
+    print("1000 steps at 128^3: rel L2 (rho, momentum, E) =", err)
+    assert np.all(err < 1e-3), err
+
+
 # ---------------------------------------------------------------------------
 # error reporting (host-made faults only)
 # ---------------------------------------------------------------------------
