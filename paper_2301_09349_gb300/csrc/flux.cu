@@ -42,7 +42,11 @@ struct BoxT {
     static constexpr int NF1 = BX * (BY + 1) * BZ;
     static constexpr int NF2 = DIM == 3 ? BX * BY * (BZ + 1) : 0;
     static constexpr int NFMAX = cmax(NF0, cmax(NF1, NF2));
-    static constexpr size_t SMEM = sizeof(T) * (size_t)(NW * PN + NC * NFMAX);
+    // 2D FP32 tiles evaluate x- and y-faces together (pair layout: all x-face
+    // rows, then all y-face rows)
+    static constexpr bool PAIRS = DIM == 2 && sizeof(T) == 4;
+    static constexpr int NFP = PAIRS ? NF0 + NF1 : 0;
+    static constexpr size_t SMEM = sizeof(T) * (size_t)(NW * PN + NC * cmax(NFMAX, NFP));
 };
 
 // Tile of the single-grid kernels.
@@ -189,6 +193,147 @@ __device__ __forceinline__ void face_flux(const FluxK<T> &k, const T *__restrict
     F[NC - 1] -= work + lam * (Tc[b] - Tc[a]) * inv_h;
 }
 
+// ---- 2D FP32: the x-face (.x) and the y-face (.y) of a thread as one pair --
+// Both faces run the same arithmetic with their velocities ordered (normal,
+// tangential); every pair operation is one packed FP32x2 instruction.
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) {
+    return __fadd2_rn(a, make_float2(-b.x, -b.y));
+}
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_s(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 p_rcp(float2 a) {
+    return make_float2(__fdividef(1.0f, a.x), __fdividef(1.0f, a.y));
+}
+__device__ __forceinline__ float2 p_rsqrt(float2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+__device__ __forceinline__ float2 p_abs(float2 a) { return make_float2(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ float2 p_max(float2 a, float2 b) {
+    return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y));
+}
+__device__ __forceinline__ float2 p_vl(float2 a, float2 b) {
+    const float2 ab = p_mul(a, b);
+    const float2 q = p_mul(p_add(ab, ab), p_rcp(p_add(a, b)));
+    return make_float2(ab.x > 0.0f ? q.x : 0.0f, ab.y > 0.0f ? q.y : 0.0f);
+}
+
+// x-face between box cells ax, ax+1 and y-face between ay, ay+PX; outputs in
+// (rho, rho u, rho v, rho E) order.  The same flux as face_flux: MUSCL/van
+// Leer states, Rusanov, central viscous stress and heat flux.
+template <int PX, int PN>
+__device__ __forceinline__ void face_pair2d(const FluxK<float> &k, const float *__restrict__ sW,
+                                            int ax, int ay, float (&Fx)[4], float (&Fy)[4]) {
+    constexpr int fx[4] = {0, 1, 2, 3};   // rho, normal, tangential, p
+    constexpr int fy[4] = {0, 2, 1, 3};
+    float2 wl[4], wr[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        const float *X = sW + fx[m] * PN;
+        const float *Y = sW + fy[m] * PN;
+        const float2 x0 = make_float2(X[ax - 1], Y[ay - PX]);
+        const float2 x1 = make_float2(X[ax], Y[ay]);
+        const float2 x2 = make_float2(X[ax + 1], Y[ay + PX]);
+        const float2 x3 = make_float2(X[ax + 2], Y[ay + 2 * PX]);
+        const float2 d0 = p_sub(x1, x0), d1 = p_sub(x2, x1), d2 = p_sub(x3, x2);
+        wl[m] = p_fma(p_s(0.5f), p_vl(d0, d1), x1);
+        wr[m] = p_fma(p_s(-0.5f), p_vl(d1, d2), x2);
+    }
+    const float2 keL = p_fma(wl[1], wl[1], p_mul(wl[2], wl[2]));
+    const float2 keR = p_fma(wr[1], wr[1], p_mul(wr[2], wr[2]));
+    const float2 EL = p_fma(wl[3], p_s(k.inv_gm1), p_mul(p_mul(p_s(0.5f), wl[0]), keL));
+    const float2 ER = p_fma(wr[3], p_s(k.inv_gm1), p_mul(p_mul(p_s(0.5f), wr[0]), keR));
+    const float2 unL = wl[1], unR = wr[1];
+    const float2 c2L = p_mul(p_mul(p_s(k.gam), wl[3]), p_rcp(wl[0]));
+    const float2 c2R = p_mul(p_mul(p_s(k.gam), wr[3]), p_rcp(wr[0]));
+    const float2 sL = p_fma(c2L, p_rsqrt(c2L), p_abs(unL));
+    const float2 sR = p_fma(c2R, p_rsqrt(c2R), p_abs(unR));
+    const float2 hs = p_mul(p_s(-0.5f), p_max(sL, sR));   // -smax/2
+    const float2 mLn = p_mul(wl[0], unL), mRn = p_mul(wr[0], unR);
+    const float2 mLt = p_mul(wl[0], wl[2]), mRt = p_mul(wr[0], wr[2]);
+    float2 F0 = p_fma(hs, p_sub(wr[0], wl[0]), p_mul(p_s(0.5f), p_add(mLn, mRn)));
+    float2 Fn = p_fma(hs, p_sub(mRn, mLn),
+                      p_mul(p_s(0.5f), p_add(p_fma(mLn, unL, wl[3]), p_fma(mRn, unR, wr[3]))));
+    float2 Ft = p_fma(hs, p_sub(mRt, mLt), p_mul(p_s(0.5f), p_fma(mLt, unL, p_mul(mRt, unR))));
+    float2 FE = p_fma(hs, p_sub(ER, EL),
+                      p_mul(p_s(0.5f), p_fma(p_add(EL, wl[3]), unL, p_mul(p_add(ER, wr[3]), unR))));
+    if (k.viscous) {
+        const float *T = sW + 4 * PN;
+        const int bx = ax + 1, by = ay + PX;
+        const float2 Ta = make_float2(T[ax], T[ay]), Tb = make_float2(T[bx], T[by]);
+        const float2 Tf = p_mul(p_s(0.5f), p_add(Ta, Tb));
+        const float2 mu = p_mul(p_mul(p_mul(p_s(k.mu_inf), Tf), p_mul(Tf, p_rsqrt(Tf))),
+                                p_mul(p_s(1.0f + k.S), p_rcp(p_add(Tf, p_s(k.S)))));
+        const float2 lam = p_mul(mu, p_s(k.lam_fac));
+        const float *Xn = sW + PN, *Yn = sW + 2 * PN;     // normal velocity: u / v
+        const float *Xt = sW + 2 * PN, *Yt = sW + PN;     // tangential velocity: v / u
+        const float2 ih = p_s(k.inv_h), qh = p_s(0.25f * k.inv_h);
+        const float2 na = make_float2(Xn[ax], Yn[ay]), nb = make_float2(Xn[bx], Yn[by]);
+        const float2 ta = make_float2(Xt[ax], Yt[ay]), tb = make_float2(Xt[bx], Yt[by]);
+        const float2 dn_n = p_mul(p_sub(nb, na), ih);
+        const float2 dn_t = p_mul(p_sub(tb, ta), ih);
+        const float2 dn_T = p_mul(p_sub(Tb, Ta), ih);
+        // along the tangent (y for the x-face, x for the y-face)
+        const float2 d1_n = p_mul(p_add(p_sub(make_float2(Xn[ax + PX], Yn[ay + 1]),
+                                              make_float2(Xn[ax - PX], Yn[ay - 1])),
+                                        p_sub(make_float2(Xn[bx + PX], Yn[by + 1]),
+                                              make_float2(Xn[bx - PX], Yn[by - 1]))), qh);
+        const float2 d1_t = p_mul(p_add(p_sub(make_float2(Xt[ax + PX], Yt[ay + 1]),
+                                              make_float2(Xt[ax - PX], Yt[ay - 1])),
+                                        p_sub(make_float2(Xt[bx + PX], Yt[by + 1]),
+                                              make_float2(Xt[bx - PX], Yt[by - 1]))), qh);
+        const float2 div = p_add(dn_n, d1_t);
+        const float2 tNN = p_mul(mu, p_fma(p_s(2.0f), dn_n, p_mul(p_s(-2.0f / 3.0f), div)));
+        const float2 tNT = p_mul(mu, p_add(d1_n, dn_t));
+        const float2 ufn = p_mul(p_s(0.5f), p_add(na, nb));
+        const float2 uft = p_mul(p_s(0.5f), p_add(ta, tb));
+        Fn = p_sub(Fn, tNN);
+        Ft = p_sub(Ft, tNT);
+        FE = p_sub(FE, p_fma(ufn, tNN, p_fma(uft, tNT, p_mul(lam, dn_T))));
+    }
+    Fx[0] = F0.x; Fx[1] = Fn.x; Fx[2] = Ft.x; Fx[3] = FE.x;
+    Fy[0] = F0.y; Fy[1] = Ft.y; Fy[2] = Fn.y; Fy[3] = FE.y;
+}
+
+// All faces of a 2D FP32 tile in one pass: thread (cx, cy) evaluates the
+// x-face on the left of its cell and the y-face below it; the BY faces on
+// the right edge and the BX faces on the top edge follow as further pairs
+// on the first warps.  acc receives each cell's flux differences.
+template <typename B>
+__device__ __forceinline__ void pair_faces_2d(const FluxK<float> &k, const float *__restrict__ sW,
+                                              float *__restrict__ sF, float (&acc)[1][4]) {
+    constexpr int BX = B::BX, BY = B::BY, PX = B::PX, PN = B::PN;
+    constexpr int FXW = BX + 1, NXF = FXW * BY, NYF = BX * (BY + 1);
+    float *FX = sF, *FY = sF + 4 * NXF;     // [4][BY][BX+1], [4][BY+1][BX]
+    const int tid = threadIdx.x;
+    const int cx = tid % BX, cy = tid / BX;
+    {
+        float Fx[4], Fy[4];
+        face_pair2d<PX, PN>(k, sW, (cx + 1) + PX * (cy + 2), (cx + 2) + PX * (cy + 1), Fx, Fy);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            FX[c * NXF + cy * FXW + cx] = Fx[c];
+            FY[c * NYF + cy * BX + cx] = Fy[c];
+        }
+    }
+    constexpr int NE = BX > BY ? BX : BY;
+    if (tid < NE) {
+        const int ex = tid < BY ? tid : 0, ey = tid < BX ? tid : 0;
+        float Fx[4], Fy[4];
+        face_pair2d<PX, PN>(k, sW, (BX + 1) + PX * (ex + 2), (ey + 2) + PX * (BY + 1), Fx, Fy);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if (tid < BY) FX[c * NXF + ex * FXW + BX] = Fx[c];
+            if (tid < BX) FY[c * NYF + BY * BX + ey] = Fy[c];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        acc[0][c] = (FX[c * NXF + cy * FXW + cx] - FX[c * NXF + cy * FXW + cx + 1]) +
+                    (FY[c * NYF + cy * BX + cx] - FY[c * NYF + (cy + 1) * BX + cx]);
+    __syncthreads();
+}
+
 // One direction: evaluate all faces of the tile normal to axis D, then add
 // each cell's flux difference to its accumulator.
 template <typename B, typename T, int D>
@@ -316,9 +461,14 @@ __device__ __forceinline__ double stage_tile(const GridParams &g, int ox, int oy
     for (int i = 0; i < B::CPT; ++i)
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[i][c] = T(0);
-    direction_pass<B, T, 0>(k, sW, sF, acc);
-    direction_pass<B, T, 1>(k, sW, sF, acc);
-    if constexpr (DIM == 3) direction_pass<B, T, 2>(k, sW, sF, acc);
+    if constexpr (B::PAIRS) {
+        static_assert(B::NCELL == NT, "pair tiles hold one cell per thread");
+        pair_faces_2d<B>(k, sW, sF, acc);
+    } else {
+        direction_pass<B, T, 0>(k, sW, sF, acc);
+        direction_pass<B, T, 1>(k, sW, sF, acc);
+        if constexpr (DIM == 3) direction_pass<B, T, 2>(k, sW, sF, acc);
+    }
 
     // ---- outputs
     const T inv_h = k.inv_h;
@@ -394,9 +544,13 @@ stage_kernel(const GridParams g, const T *__restrict__ Uin, const T *__restrict_
 // The same stages over a batch of 2D grids: one persistent launch walks a
 // list of (case, tile) work items; every case keeps its own parameters,
 // state, step size and error word.  MODE 2 writes one maximum per item.
-// FP32: six CTAs per SM (40 registers), as the single-grid 2D kernel gets.
+// FP32: five CTAs per SM (48 registers, a few bytes of spill): measured
+// faster on the 64-case batch than four (64 registers) or three
+#ifndef IBM_BATCH_MIN_BLOCKS
+#define IBM_BATCH_MIN_BLOCKS 5
+#endif
 template <typename T, int S, int MODE>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 6 : 1)
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? IBM_BATCH_MIN_BLOCKS : 1)
 batch_stage_kernel(const BatchCase *__restrict__ cases, const int2 *__restrict__ items,
                    int n_items, double *__restrict__ item_max, double dt_fixed) {
     using B = typename Shape2<T, S>::type;

@@ -382,6 +382,9 @@ __device__ __forceinline__ double warp_max_d(double v) {
 #ifndef IBM_ZM_MIN_BLOCKS
 #define IBM_ZM_MIN_BLOCKS 3
 #endif
+#ifndef IBM_ZM_PREFETCH
+#define IBM_ZM_PREFETCH 1
+#endif
 
 // MODE 0: out = L(Uin).  MODE 1: out = U1 = Uin + dt L(Uin).
 // MODE 2: out = U* = Un/2 + (Uin + dt L(Uin))/2 with Uin = U1, plus the
@@ -474,6 +477,16 @@ zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, cons
         __syncthreads();
         if (TMA && tid == 0 && !s_tma_dead && z + 1 < z1 && z + 3 < nz)
             tma_issue(&tmap, st_addr, mbar, ox - 4, oy - 2, z + 3);
+#if IBM_ZM_PREFETCH
+        // stage 2 reads U^n at its output cells, which nothing has touched:
+        // start those lines toward L2 two planes ahead
+        if (MODE == 2 && z + 2 < z1 && ox + lx < g.n[0] && oy + ly < g.n[1]) {
+            const long long jp = (ox + lx) + (long long)g.n[0] * ((oy + ly) + (long long)g.n[1] * (z + 2));
+#pragma unroll
+            for (int m = 0; m < NC; ++m)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(Un + m * N + jp));
+        }
+#endif
         const int sm1 = slot_of(z - 1), s0 = slot_of(z), s1 = slot_of(z + 1), s2 = slot_of(z + 2);
         (void)sm1;
         const int up = s1 - s0, dn = sm1 - s0;
