@@ -24,7 +24,7 @@ def declared_functions():
     return sorted(set(re.findall(r"\b(ibm_\w+)\s*\(", src)))
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_core_calls():
     names = declared_functions()
     for n in ("ibm_create_grid", "ibm_set_markers", "ibm_step", "ibm_forces_and_nusselt",
               "ibm_backward"):
