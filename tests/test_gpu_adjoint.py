@@ -61,6 +61,20 @@ def test_rhs_vjp_matches_oracle(dim, fp, tol, bc):
     assert err < tol, err
 
 
+@pytest.mark.parametrize("dim,fp,tol", [(2, 8, 1e-11), (3, 8, 1e-11), (2, 4, 2e-4)])
+def test_rhs_vjp_inviscid_matches_oracle(dim, fp, tol):
+    n = (13, 11) if dim == 2 else (9, 7, 6)
+    g = C.small_grid(dim, n, h=0.1, fp_bytes=fp, Re=0.0, Mach=0.6, bc=MIXED)
+    U = C.random_state(g, seed=29, amp=0.05)
+    V = np.random.default_rng(6).standard_normal(U.shape)
+    dt_ = np.float32 if fp == 4 else np.float64
+    grid = ibm.Grid(g)
+    grid.record(1, 1)
+    out = grid.rhs_vjp(torch.from_numpy(U.astype(dt_)), torch.from_numpy(V.astype(dt_))).cpu().numpy()
+    ref = adj().rhs_vjp(g, U.astype(dt_).astype(np.float64), V.astype(dt_).astype(np.float64))
+    assert np.linalg.norm(out - ref) / np.linalg.norm(ref) < tol
+
+
 def cylinder(fp, n=(40, 32), h=0.1):
     g = C.small_grid(2, n, h=h, fp_bytes=fp, Re=100.0, Mach=0.3)
     X = C.circle_markers(int(np.ceil(np.pi / h)), 0.5, (0.05, -0.03))
@@ -216,6 +230,18 @@ def test_adjoint_errors():
     grid.step(2)
     gX, gT = grid.backward(1.0, 0.0)
     assert np.all(np.isfinite(gX)) and np.all(np.isfinite(gT))
+    # Nu is undefined on an inviscid grid: weighting it is an argument error
+    gi = C.small_grid(2, (40, 32), h=0.1, fp_bytes=8, Re=0.0, Mach=0.3)
+    inv = ibm.Grid(gi, max_markers=len(X))
+    inv.set_markers(X, Tw)
+    inv.set_state(C.initial_state(gi, seed))
+    inv.record(2, 1)
+    inv.step(1)
+    with pytest.raises(ibm.IbmError) as e:
+        inv.backward(0.0, 1.0)
+    assert e.value.status == 1
+    gX, gT = inv.backward(1.0, 0.0)          # drag alone is fine
+    assert np.all(np.isfinite(gX))
     mov = ibm.Grid(g, max_markers=len(X))
     mov.set_markers(X, Tw, motion=C.Motion(0.05, 1.0, 1))
     mov.set_state(C.initial_state(g, seed))

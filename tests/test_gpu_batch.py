@@ -109,6 +109,23 @@ def test_batch_bitwise_equals_per_case_loop(fp, shape, warps, graph):
     assert_bitwise(b, loop)
 
 
+def test_batch_energy_reading_total_equals_loop():
+    cs = small_batch(4, n=3, seed=17)
+    b = ibm.Batch([c.grid for c in cs], [len(c.X) for c in cs], energy_reading=1)
+    loop = []
+    for cg, c in zip(b.cases, cs):
+        cg.set_markers(c.X, c.Tw)
+        cg.set_state(cast(C.initial_state(c.grid, c.seed), c.grid))
+        gr = ibm.Grid(c.grid, max_markers=len(c.X), energy_reading=1)
+        gr.set_markers(c.X, c.Tw)
+        gr.set_state(cast(C.initial_state(c.grid, c.seed), c.grid))
+        loop.append(gr)
+    b.step(3)
+    for gr in loop:
+        gr.step(3)
+    assert_bitwise(b, loop)
+
+
 def test_batch_fixed_dt_and_changes_between_steps():
     cs = small_batch(4, n=4, seed=9)
     b = make_batch(cs)
