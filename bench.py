@@ -60,7 +60,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target seconds of oracle work for the cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--workload", default="sphere", choices=["sphere", "batched", "adjoint"])
+    p.add_argument("--workload", default="sphere",
+                   choices=["sphere", "batched", "adjoint", "cylinders"])
     p.add_argument("--every", type=int, default=50, help="adjoint checkpoint interval")
     return p.parse_args()
 
@@ -651,11 +652,70 @@ def run_adjoint(args, rank, world, local):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# small 2D cylinders: time per step, direct launches vs CUDA graphs
+# ---------------------------------------------------------------------------
+
+CYL_METRIC = "us per IBM step of the small 2D cylinder cases (L2-resident), direct vs CUDA graphs"
+
+
+def run_cylinders(args, rank, world, local):
+    import torch
+    from paper_2301_09349_gb300 import build, ibm
+    build.build()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return 0
+    stream = torch.cuda.Stream()
+    out = {}
+    for c in (C.heated_cylinder(), C.oscillating_cylinder()):
+        g = c.grid
+        res = {}
+        for k in (0, 10):
+            grid = ibm.Grid(g, max_markers=len(c.X), stream=stream)
+            grid.set_markers(c.X, c.Tw, motion=c.motion)
+            grid.set_state(C.initial_state(g, c.seed).astype(
+                np.float32 if g.fp_bytes == 4 else np.float64))
+            grid.use_graphs(k)
+            grid.step(max(args.warmup, 10))
+            grid.sync()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            grid.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            grid.sync()
+            res["graphs" if k else "direct"] = 1e3 * e0.elapsed_time(e1) / args.steps
+            grid.close()
+        out[c.name] = {"cells": g.ncells, "fp": "f%d" % (8 * g.fp_bytes),
+                       "moving_markers": c.motion is not None,
+                       "us_per_step_direct": res["direct"], "us_per_step_graphs": res["graphs"],
+                       "launch_overhead_us_per_step": res["direct"] - res["graphs"]}
+    osc = out[C.oscillating_cylinder().name]
+    line = {
+        "metric": CYL_METRIC, "value": osc["cells"] * 1e6 / osc["us_per_step_graphs"],
+        "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": osc["us_per_step_graphs"] / 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "2D heated cylinder 128x64 FP64 (static) and 2D oscillating "
+                               "cylinder 1024x512 FP32 (moving markers, bins and quadrature "
+                               "rebuilt every step); value = the latter with graphs",
+                   "l2": "L2-resident by design (states of 0.26 and 8.4 MB)"},
+        "cases": out,
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.workload == "adjoint":
         return run_adjoint(args, rank, world, local)
+    if args.workload == "cylinders":
+        return run_cylinders(args, rank, world, local)
     if args.workload == "batched":
         if args.impl == "reference":
             return run_reference_batched(args, rank, world)

@@ -144,6 +144,13 @@ ibm_status ibm_set_wall_temperature(ibm_grid *g, const double *Tw);
  * set).  Asynchronous; no host synchronization. */
 ibm_status ibm_step(ibm_grid *g, int nsteps, double dt_fixed);
 
+/* steps_per_graph > 0 (even): ibm_step replays whole chunks of that many
+ * steps from CUDA graphs captured on first use (one per starting buffer and
+ * dt_fixed; recaptured after ibm_set_markers), the remainder launched
+ * directly.  Cuts the per-launch host cost of small grids.  Graphs are not
+ * used while profiling or recording.  0 (default) = direct launches. */
+ibm_status ibm_step_graphs(ibm_grid *g, int steps_per_graph);
+
 /* Force on the body and heat rate into the fluid from the last step's
  * marker forcing (Sec. 3.1, Eq. Bulk): force = -h^d sum_k eps~_k F_k,
  * heat = h^d sum_k eps~_k Q_k; Cd = 2 force_x / (rho U^2 Lref),

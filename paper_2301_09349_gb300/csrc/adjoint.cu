@@ -24,10 +24,11 @@
 //                         lam^n = lam*/2 + mu + dt J_L(U)^T mu.
 // J_L^T v is evaluated face by face: the reverse of the face flux (MUSCL /
 // van Leer states, Rusanov flux, central viscous stress and heat flux with
-// Sutherland's law) is scattered into FP64 accumulators of the primitive
+// Sutherland's law) is scattered into accumulators of the primitive
 // adjoints of its stencil cells (ghost cells mapped to their sources, with
 // the slip flips; free-stream ghosts are constants), then chained to the
-// conserved variables cell by cell.  The forward states of a step are
+// conserved variables cell by cell (the sums in the grid's type: FP32 grids
+// run the whole reverse sweep in FP32).  The forward states of a step are
 // recomputed from checkpoints taken every `every` steps.
 #include <math.h>
 #include <string.h>
@@ -334,7 +335,7 @@ constexpr int FT = 128;   // flux-reverse CTA: ~150 live registers per face
 template <int DIM, int D, typename T>
 __global__ void __launch_bounds__(FT, 3)
 adj_flux_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ V,
-                double *__restrict__ lamW) {
+                T *__restrict__ lamW) {
     using R = T;
     constexpr int NC = DIM + 2;
     constexpr int NT2 = ntan(DIM);
@@ -413,7 +414,7 @@ adj_flux_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict
             for (int q = 0; q < NC; ++q) {
                 R v = wb[i][q];
                 if (q >= 1 && q <= DIM && ((flip[i] >> (q - 1)) & 1)) v = -v;
-                if (v != R(0)) atomicAdd(lamW + q * N + src[i], (double)v);
+                if (v != R(0)) atomicAdd(lamW + q * N + src[i], v);
             }
         }
 #pragma unroll
@@ -425,7 +426,7 @@ adj_flux_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict
                 for (int m = 0; m < DIM; ++m) {
                     R v = utb[ti][i][m];
                     if ((flipt[ti][i] >> m) & 1) v = -v;
-                    if (v != R(0)) atomicAdd(lamW + (1 + m) * N + srct[ti][i], (double)v);
+                    if (v != R(0)) atomicAdd(lamW + (1 + m) * N + srct[ti][i], v);
                 }
             }
     }
@@ -434,11 +435,10 @@ adj_flux_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict
 // out = (dW/dU)^T lamW at every cell (then lamW is cleared):
 // rho-bar = W_rho - sum_m W_um u_m / rho + W_p (gamma-1) |u|^2/2,
 // m-bar = W_u / rho - W_p (gamma-1) u, E-bar = W_p (gamma-1).
-// The sums were accumulated in FP64; this per-cell chain runs in the grid's
-// type (double arithmetic is slow on this GPU).
+// In the grid's type throughout (double arithmetic is slow on this GPU).
 template <int DIM, typename T>
 __global__ void __launch_bounds__(AT)
-adj_prim_kernel(const GridParams g, const T *__restrict__ U, double *__restrict__ lamW,
+adj_prim_kernel(const GridParams g, const T *__restrict__ U, T *__restrict__ lamW,
                 T *__restrict__ out) {
     using R = T;
     constexpr int NC = DIM + 2;
@@ -456,8 +456,8 @@ adj_prim_kernel(const GridParams g, const T *__restrict__ U, double *__restrict_
         R wbv[NC];
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-            wbv[q] = (R)lamW[q * N + j];
-            lamW[q * N + j] = 0.0;
+            wbv[q] = lamW[q * N + j];
+            lamW[q * N + j] = R(0);
         }
         const R pb = wbv[NC - 1] * k.gm1;
         R rb = wbv[0] + pb * R(0.5) * ke;
@@ -720,8 +720,9 @@ adj_eps_fields_kernel(const GridParams g, const MarkerBuffers m, const unsigned 
             se += w * m.eps[kk];
             sz += w * a.z[kk];
         });
-        a.lamW[j] = se;
-        a.lamW[N + j] = sz;
+        double *w = (double *)a.lamW;   // FP64 scratch here
+        w[j] = se;
+        w[N + j] = sz;
     });
 }
 
@@ -741,7 +742,8 @@ adj_eps_x_kernel(const GridParams g, const MarkerBuffers m, const AdjBuffers a) 
         double gw[DIM];
         long long j;
         lane_weight_grad<DIM>(g, m, k, lane, gw, j);
-        const double s = a.z[k] * a.lamW[j] + m.eps[k] * a.lamW[N + j];
+        const double *w = (const double *)a.lamW;
+        const double s = a.z[k] * w[j] + m.eps[k] * w[N + j];
 #pragma unroll
         for (int d = 0; d < DIM; ++d) gx[d] = gw[d] * s;
     }
@@ -761,9 +763,10 @@ int grid_for(long long work, int per_block = AT) {
 
 // out = J_L(U)^T V (lamW must be zero on entry; it is zero again on exit)
 template <int DIM, typename T>
-cudaError_t rhs_vjp_t(const GridParams &g, const void *U, const void *V, double *lamW, void *out,
+cudaError_t rhs_vjp_t(const GridParams &g, const void *U, const void *V, void *lamW_, void *out,
                       cudaStream_t s) {
     const T *u = (const T *)U, *v = (const T *)V;
+    T *lamW = (T *)lamW_;
     for (int D = 0; D < DIM; ++D) {
         const long long faces = g.N / g.n[D] * (g.n[D] + 1);
         const int nb = grid_for(faces, FT);
@@ -821,7 +824,7 @@ cudaError_t eps_adjoint_x(const GridParams &g, const MarkerBuffers &m, const Adj
 }  // namespace
 
 cudaError_t launch_rhs_vjp(const GridParams &g, int fp_bytes, const void *U, const void *V,
-                           double *lamW, void *out, cudaStream_t s) {
+                           void *lamW, void *out, cudaStream_t s) {
     if (g.dim == 3)
         return fp_bytes == 4 ? rhs_vjp_t<3, float>(g, U, V, lamW, out, s)
                              : rhs_vjp_t<3, double>(g, U, V, lamW, out, s);
@@ -891,7 +894,7 @@ size_t adj_layout(const ibm_grid_desc &d, int cap, int max_steps, int every, cha
     b.mu = take(SB);
     b.jtv = take(SB);
     b.lfq = take(SB);
-    b.lamW = (double *)take(sizeof(double) * (size_t)N * (d.dim + 2));
+    b.lamW = take(sizeof(double) * (size_t)N * (d.dim + 2));
     b.lamX = (double *)take(sizeof(double) * 3 * c1);
     b.lamTw = (double *)take(sizeof(double) * c1);
     b.lamEps = (double *)take(sizeof(double) * c1);

@@ -261,14 +261,14 @@ cudaError_t prof_collect(ibm_grid *g) {
 }
 
 // Marker pipeline on the device: bins, then quadrature (warm start if asked).
-ibm_status rebuild_markers(ibm_grid *g, int warm) {
-    CU(launch_bin(g->gp, g->mb, g->stream), "bin markers");
-    CU(launch_band_mask(g->gp, g->mb, persistent_ctas(g), g->stream), "band mask");
+ibm_status rebuild_markers(ibm_grid *g, int warm, cudaStream_t s) {
+    CU(launch_bin(g->gp, g->mb, s), "bin markers");
+    CU(launch_band_mask(g->gp, g->mb, persistent_ctas(g), s), "band mask");
     if (g->mb.ns > 0)
-        CU(launch_quadrature(g->gp, g->mb, g->qb, g->cg_tol, g->cg_maxit, warm, g->stream),
-           "quadrature");
+        CU(launch_quadrature(g->gp, g->mb, g->qb, g->cg_tol, g->cg_maxit, warm, s), "quadrature");
     return IBM_OK;
 }
+ibm_status rebuild_markers(ibm_grid *g, int warm) { return rebuild_markers(g, warm, g->stream); }
 
 }  // namespace
 
@@ -511,6 +511,7 @@ ibm_status ibm_set_markers(ibm_grid *g, int n, const double *X0, const double *U
     g->kept = keep;
     g->Tw_h = Twh;
     ++g->marker_gen;
+    g->drop_graphs();
     g->rec_steps = 0;
     g->moving = motion != nullptr;
     if (motion) g->motion = *motion;
@@ -537,6 +538,77 @@ ibm_status ibm_set_wall_temperature(ibm_grid *g, const double *Tw) {
     return IBM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// nsteps IBM steps launched on stream s (the handle's stream, or the private
+// stream a graph is captured on)
+ibm_status run_steps(ibm_grid *g, int nsteps, double dt_fixed, cudaStream_t s) {
+    const int fpb = g->desc.fp_bytes;
+    const int ctas = persistent_ctas(g);
+    long rec;
+    const int nb = (int)fluid_stage_blocks(g->gp, fpb);
+    for (int step = 0; step < nsteps; ++step) {
+        void *Un = g->U[g->cur];
+        void *Us = g->U[1 - g->cur];
+        void *U1 = g->L;
+        if (g->recording && g->rec_steps % g->adj.every == 0)
+            CU(cudaMemcpyAsync((char *)g->adj.ckpt +
+                                   (size_t)(g->rec_steps / g->adj.every) * align_up(state_bytes(g->desc), 256),
+                               Un, state_bytes(g->desc), cudaMemcpyDeviceToDevice, s),
+               "checkpoint");
+        CU(prof_begin(g, IBM_PROF_STAGE1, 1, &rec), "profile");
+        CU(launch_stage1(g->gp, fpb, Un, U1, g->fb, dt_fixed, s), "stage 1");
+        CU(prof_end(g, rec), "profile");
+        if (g->moving && g->mb.ns > 0) {
+            CU(prof_begin(g, IBM_PROF_MARKERS, 8, &rec), "profile");
+            CU(launch_motion(g->gp, g->mb, g->motion.amp, g->motion.freq, g->motion.axis, g->fb.dt,
+                             dt_fixed, s),
+               "motion");
+            ibm_status st = rebuild_markers(g, 1, s);
+            if (st != IBM_OK) return st;
+            CU(prof_end(g, rec), "profile");
+        }
+        if (g->desc.forcing_per_stage && g->mb.ns > 0) {
+            // variant: the first stage is forced too; its sources are summed now
+            CU(prof_begin(g, IBM_PROF_INTERP, 2, &rec), "profile");
+            CU(launch_interp_force(g->gp, fpb, U1, g->mb, ctas, s), "interp/force (stage 1)");
+            CU(launch_partial_sums(g->gp, g->mb, s), "stage-1 sums");
+            CU(prof_end(g, rec), "profile");
+            CU(prof_begin(g, IBM_PROF_SPREAD, 1, &rec), "profile");
+            CU(launch_spread_apply(g->gp, fpb, U1, g->mb, ctas, s), "spread/apply (stage 1)");
+            CU(prof_end(g, rec), "profile");
+        }
+        CU(prof_begin(g, IBM_PROF_STAGE2, 1, &rec), "profile");
+        CU(launch_stage2(g->gp, fpb, Un, U1, Us, g->fb, dt_fixed, s), "stage 2");
+        CU(prof_end(g, rec), "profile");
+        if (g->mb.ns > 0) {
+            CU(prof_begin(g, IBM_PROF_INTERP, 1, &rec), "profile");
+            CU(launch_interp_force(g->gp, fpb, Us, g->mb, ctas, s), "interp/force");
+            CU(prof_end(g, rec), "profile");
+            CU(prof_begin(g, IBM_PROF_SPREAD, 1, &rec), "profile");
+            CU(launch_spread_apply(g->gp, fpb, Us, g->mb, ctas, s), "spread/apply");
+            CU(prof_end(g, rec), "profile");
+        }
+        CU(prof_begin(g, IBM_PROF_FINISH, 1, &rec), "profile");
+        CU(launch_finish(g->gp, g->mb, g->fb, nb, g->mb.ns > 0 ? ctas : 0, dt_fixed, s),
+           "finish");
+        CU(prof_end(g, rec), "profile");
+        if (g->recording) {
+            CU(cudaMemcpyAsync(g->adj.dt_hist + g->rec_steps, g->mb.sums + 4, sizeof(double),
+                               cudaMemcpyDeviceToDevice, s),
+               "record dt");
+            ++g->rec_steps;
+        }
+        g->cur = 1 - g->cur;
+    }
+    return IBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 ibm_status ibm_step(ibm_grid *g, int nsteps, double dt_fixed) {
     if (!g) return IBM_ERR_ARG;
     if (nsteps < 0 || !isfinite(dt_fixed)) return fail(g, IBM_ERR_ARG, "invalid step arguments");
@@ -548,64 +620,47 @@ ibm_status ibm_step(ibm_grid *g, int nsteps, double dt_fixed) {
             return fail(g, IBM_ERR_WORKSPACE, "more steps than the adjoint workspace records (" +
                                                   std::to_string(g->adj.max_steps) + ")");
     }
-    const int fpb = g->desc.fp_bytes;
-    const int ctas = persistent_ctas(g);
-    long rec;
-    const int nb = (int)fluid_stage_blocks(g->gp, fpb);
-    for (int s = 0; s < nsteps; ++s) {
-        void *Un = g->U[g->cur];
-        void *Us = g->U[1 - g->cur];
-        void *U1 = g->L;
-        if (g->recording && g->rec_steps % g->adj.every == 0)
-            CU(cudaMemcpyAsync((char *)g->adj.ckpt +
-                                   (size_t)(g->rec_steps / g->adj.every) * align_up(state_bytes(g->desc), 256),
-                               Un, state_bytes(g->desc), cudaMemcpyDeviceToDevice, g->stream),
-               "checkpoint");
-        CU(prof_begin(g, IBM_PROF_STAGE1, 1, &rec), "profile");
-        CU(launch_stage1(g->gp, fpb, Un, U1, g->fb, dt_fixed, g->stream), "stage 1");
-        CU(prof_end(g, rec), "profile");
-        if (g->moving && g->mb.ns > 0) {
-            CU(prof_begin(g, IBM_PROF_MARKERS, 8, &rec), "profile");
-            CU(launch_motion(g->gp, g->mb, g->motion.amp, g->motion.freq, g->motion.axis, g->fb.dt,
-                             dt_fixed, g->stream),
-               "motion");
-            ibm_status st = rebuild_markers(g, 1);
-            if (st != IBM_OK) return st;
-            CU(prof_end(g, rec), "profile");
+    // graphs: whole chunks of graph_steps steps (an even number, so the
+    // buffers end where they started); not while profiling or recording
+    const int k = g->graph_steps;
+    if (k > 0 && !g->prof && !g->recording) {
+        while (nsteps >= k) {
+            const int p = g->cur;
+            if (!g->gexec[p] || g->gexec_dt[p] != dt_fixed) {
+                if (g->gexec[p]) cudaGraphExecDestroy(g->gexec[p]);
+                g->gexec[p] = nullptr;
+                if (!g->cap) CU(cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking), "stream");
+                CU(cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeRelaxed), "begin capture");
+                const ibm_status st = run_steps(g, k, dt_fixed, g->cap);
+                cudaGraph_t graph = nullptr;
+                const cudaError_t e = cudaStreamEndCapture(g->cap, &graph);
+                g->cur = p;
+                if (st != IBM_OK) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return st;
+                }
+                if (e != cudaSuccess) return cuda_fail(g, e, "end capture");
+                const cudaError_t e2 = cudaGraphInstantiate(&g->gexec[p], graph, 0);
+                cudaGraphDestroy(graph);
+                if (e2 != cudaSuccess) {
+                    g->gexec[p] = nullptr;
+                    return cuda_fail(g, e2, "instantiate step graph");
+                }
+                g->gexec_dt[p] = dt_fixed;
+            }
+            CU(cudaGraphLaunch(g->gexec[p], g->stream), "graph launch");
+            nsteps -= k;
         }
-        if (g->desc.forcing_per_stage && g->mb.ns > 0) {
-            // variant: the first stage is forced too; its sources are summed now
-            CU(prof_begin(g, IBM_PROF_INTERP, 2, &rec), "profile");
-            CU(launch_interp_force(g->gp, fpb, U1, g->mb, ctas, g->stream), "interp/force (stage 1)");
-            CU(launch_partial_sums(g->gp, g->mb, g->stream), "stage-1 sums");
-            CU(prof_end(g, rec), "profile");
-            CU(prof_begin(g, IBM_PROF_SPREAD, 1, &rec), "profile");
-            CU(launch_spread_apply(g->gp, fpb, U1, g->mb, ctas, g->stream), "spread/apply (stage 1)");
-            CU(prof_end(g, rec), "profile");
-        }
-        CU(prof_begin(g, IBM_PROF_STAGE2, 1, &rec), "profile");
-        CU(launch_stage2(g->gp, fpb, Un, U1, Us, g->fb, dt_fixed, g->stream), "stage 2");
-        CU(prof_end(g, rec), "profile");
-        if (g->mb.ns > 0) {
-            CU(prof_begin(g, IBM_PROF_INTERP, 1, &rec), "profile");
-            CU(launch_interp_force(g->gp, fpb, Us, g->mb, ctas, g->stream), "interp/force");
-            CU(prof_end(g, rec), "profile");
-            CU(prof_begin(g, IBM_PROF_SPREAD, 1, &rec), "profile");
-            CU(launch_spread_apply(g->gp, fpb, Us, g->mb, ctas, g->stream), "spread/apply");
-            CU(prof_end(g, rec), "profile");
-        }
-        CU(prof_begin(g, IBM_PROF_FINISH, 1, &rec), "profile");
-        CU(launch_finish(g->gp, g->mb, g->fb, nb, g->mb.ns > 0 ? ctas : 0, dt_fixed, g->stream),
-           "finish");
-        CU(prof_end(g, rec), "profile");
-        if (g->recording) {
-            CU(cudaMemcpyAsync(g->adj.dt_hist + g->rec_steps, g->mb.sums + 4, sizeof(double),
-                               cudaMemcpyDeviceToDevice, g->stream),
-               "record dt");
-            ++g->rec_steps;
-        }
-        g->cur = 1 - g->cur;
     }
+    return run_steps(g, nsteps, dt_fixed, g->stream);
+}
+
+ibm_status ibm_step_graphs(ibm_grid *g, int steps_per_graph) {
+    if (!g) return IBM_ERR_ARG;
+    if (steps_per_graph < 0 || (steps_per_graph & 1))
+        return fail(g, IBM_ERR_ARG, "steps_per_graph must be 0 or a positive even number");
+    if (steps_per_graph != g->graph_steps) g->drop_graphs();
+    g->graph_steps = steps_per_graph;
     return IBM_OK;
 }
 

@@ -58,7 +58,22 @@ struct ibm_grid {
     double prof_ms[IBM_PROF_GROUPS] = {0};
     long long prof_n[IBM_PROF_GROUPS] = {0};
 
+    // ibm_step_graphs: steps replayed from captured CUDA graphs of graph_steps
+    // steps each, one graph per starting buffer (cur)
+    int graph_steps = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    double gexec_dt[2] = {0.0, 0.0};
+
+    void drop_graphs() {
+        for (int p = 0; p < 2; ++p) {
+            if (gexec[p]) cudaGraphExecDestroy(gexec[p]);
+            gexec[p] = nullptr;
+        }
+    }
     ~ibm_grid() {
+        drop_graphs();
+        if (cap) cudaStreamDestroy(cap);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     }
 };

@@ -72,6 +72,7 @@ SIGNATURES = [
                                        ctypes.c_int, _ip]),
     ("ibm_set_wall_temperature", ctypes.c_int, [_vp, _dp]),
     ("ibm_step", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double]),
+    ("ibm_step_graphs", ctypes.c_int, [_vp, ctypes.c_int]),
     ("ibm_forces_and_nusselt", ctypes.c_int, [_vp, _dp, _dp, _dp, _dp, _dp]),
     ("ibm_backward", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _dp, _dp]),
     ("ibm_sync", ctypes.c_int, [_vp]),
@@ -229,6 +230,10 @@ def ibm_set_wall_temperature(h, Tw):
 
 def ibm_step(h, nsteps: int, dt_fixed: float = 0.0):
     _check(lib().ibm_step(h, int(nsteps), ctypes.c_double(dt_fixed)), h)
+
+
+def ibm_step_graphs(h, steps_per_graph: int):
+    _check(lib().ibm_step_graphs(h, int(steps_per_graph)), h)
 
 
 def ibm_forces_and_nusselt(h) -> dict:
@@ -515,6 +520,10 @@ class Grid:
 
     def step(self, nsteps: int = 1, dt_fixed: float = 0.0):
         ibm_step(self.h, nsteps, dt_fixed)
+
+    def use_graphs(self, steps_per_graph: int):
+        """replay chunks of steps_per_graph (even) steps from CUDA graphs"""
+        ibm_step_graphs(self.h, steps_per_graph)
 
     def sync(self):
         ibm_sync(self.h)

@@ -144,3 +144,33 @@ def test_forcing_per_stage_is_refused_by_batch_and_adjoint():
     with pytest.raises(ibm.IbmError) as e:
         grid.record(4, 2)
     assert e.value.status == 8
+
+
+@pytest.mark.parametrize("moving", [False, True])
+def test_step_graphs_are_bitwise_direct_launches(moving):
+    c = C.oscillating_cylinder(scale_div=4) if moving else C.heated_cylinder()
+    g = c.grid
+    U0 = C.initial_state(g, c.seed).astype(np.float32 if g.fp_bytes == 4 else np.float64)
+    grids = []
+    for k in (0, 4):
+        gr = ibm.Grid(g, max_markers=len(c.X))
+        gr.set_markers(c.X, c.Tw, motion=c.motion)
+        gr.set_state(U0)
+        gr.use_graphs(k)
+        grids.append(gr)
+    for n in (9, 4, 3):          # chunks of 4 plus direct remainders, both parities
+        for gr in grids:
+            gr.step(n)
+        a, b = (gr.get_state().cpu().numpy() for gr in grids)
+        assert np.array_equal(a, b)
+        assert grids[0].time() == grids[1].time()
+        assert grids[0].forces()["Cd"] == grids[1].forces()["Cd"]
+    # new markers: the graphs are recaptured
+    X2 = c.X + np.array([0.02, -0.01])
+    for gr in grids:
+        gr.set_markers(X2, c.Tw, motion=c.motion)
+        gr.step(8, dt_fixed=1e-3)
+    a, b = (gr.get_state().cpu().numpy() for gr in grids)
+    assert np.array_equal(a, b)
+    with pytest.raises(ibm.IbmError):
+        grids[1].use_graphs(3)
