@@ -703,7 +703,6 @@ def run_cylinders(args, rank, world, local):
                                "rebuilt every step); value = the latter with graphs",
                    "l2": "L2-resident by design (states of 0.26 and 8.4 MB)"},
         "cases": out,
-        "gpu_launches": None,
     }
     print(json.dumps(line), flush=True)
     return 0
