@@ -679,6 +679,13 @@ def run_cylinders(args, rank, world, local):
             grid.use_graphs(k)
             grid.step(max(args.warmup, 10))
             grid.sync()
+            if k == 0:       # the kernel split of direct launches
+                ibm.ibm_profile(grid.h, True)
+                grid.step(args.steps)
+                prof = ibm.ibm_profile_read(grid.h)
+                ibm.ibm_profile(grid.h, False)
+                res["split_us_per_step"] = {n: 1e3 * ms / args.steps
+                                            for n, (ms, nl) in prof.items() if nl}
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -691,6 +698,7 @@ def run_cylinders(args, rank, world, local):
         out[c.name] = {"cells": g.ncells, "fp": "f%d" % (8 * g.fp_bytes),
                        "moving_markers": c.motion is not None,
                        "us_per_step_direct": res["direct"], "us_per_step_graphs": res["graphs"],
+                       "split_us_per_step": res["split_us_per_step"],
                        "launch_overhead_us_per_step": res["direct"] - res["graphs"]}
     osc = out[C.oscillating_cylinder().name]
     line = {

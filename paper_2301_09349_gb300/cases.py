@@ -204,14 +204,26 @@ def heated_sphere(n: int = 256, mach: float = 0.3, Tw: float = 1.5,
                 1000, seed)
 
 
+def markers_at_arc_spacing(h: float, D: float = 1.0) -> int:
+    """Markers on a circle of diameter D one cell apart along the arc:
+    round(pi D / h) (101 at h = D/32).  A moving body keeps the marker set
+    it starts with; at this spacing the set stays close to one marker per
+    cell as it moves, where a denser set thinned to one per cell at t = 0
+    ends up with up to 35 cells holding two markers, a near-singular A~ and
+    a run that goes non-finite (measured on the transverse case)."""
+    return int(round(math.pi * D / h))
+
+
 def oscillating_cylinder(scale_div: int = 1, seed: int = 3) -> Case:
     """2D cylinder in transverse motion y(t) = 0.2 sin(2 pi 0.2 t): 1024x512 over
-    [-8,24]x[-8,8], 400 markers, Ma 0.2, Re 100, T_w 1.2, FP32 (Sec. 5 stand-in).
-    `scale_div` divides the resolution for reduced-size tests."""
+    [-8,24]x[-8,8], markers one cell apart on the circle (101), Ma 0.2,
+    Re 100, T_w 1.2, FP32 (Sec. 5 stand-in).  `scale_div` divides the
+    resolution for reduced-size tests."""
     n = (1024 // scale_div, 512 // scale_div, 1)
-    g = GridDesc(dim=2, n=n, lo=(-8.0, -8.0, 0.0), h=(1.0 / 32.0) * scale_div, fp_bytes=4,
+    h = (1.0 / 32.0) * scale_div
+    g = GridDesc(dim=2, n=n, lo=(-8.0, -8.0, 0.0), h=h, fp_bytes=4,
                  Re=100.0, Mach=0.2, bc=_bc_for(2, 0.2), tile=(16, 16, 1))
-    X = circle_markers(400)
+    X = circle_markers(markers_at_arc_spacing(h))
     return Case(f"oscillating_cylinder_{n[0]}x{n[1]}", g, X, np.full(len(X), 1.2), None,
                 Motion(amp=0.2, freq=0.2, axis=1), 5000, seed)
 
@@ -233,7 +245,7 @@ def streamwise_oscillating_cylinder(scale_div: int = 1, f0: float = ST0_RE100,
     h = (1.0 / 32.0) * scale_div
     g = GridDesc(dim=2, n=n, lo=(-8.0, -8.0, 0.0), h=h, fp_bytes=4, Re=100.0, Mach=0.3,
                  bc=_bc_for(2, 0.3), tile=(16, 16, 1))
-    X = circle_markers(int(math.ceil(math.pi / h)))
+    X = circle_markers(markers_at_arc_spacing(h))
     return Case(f"streamwise_oscillating_cylinder_{n[0]}x{n[1]}", g, X, np.full(len(X), 1.0),
                 None, Motion(amp=0.14, freq=2.0 * f0, axis=0), 5000, seed)
 

@@ -6,19 +6,28 @@
 //
 // Because Phi is a tensor product, A~_kl = prod_d sum_i phi(r_k,d(i))
 // phi(r_l,d(i)) over the three support columns of k on each axis.  Rows are
-// assembled in ELL form (column-major, one thread per marker, neighbours
-// found through the marker bins in a fixed order), then a single CTA runs
-// Jacobi-preconditioned CG in FP64 with fixed-order block reductions, so the
-// result is bitwise reproducible.  Every loop is bounded by maxit.
+// assembled in ELL form (column-major, one warp per marker, neighbours
+// found through the marker bins in a fixed order).  Up to 160 markers a
+// single CTA factors the dense matrix (Cholesky, FP64); above, a single CTA
+// runs Jacobi-preconditioned CG in FP64 with fixed-order block reductions.
+// Either way the result is bitwise reproducible; every loop is bounded.
 #include "internal.h"
 
 namespace ibmk {
 namespace {
 
+// Row k of A~: one warp per marker, one lane per neighbour cell of its owner
+// cell (the 5^d cells whose markers can overlap its support), visited in
+// (z, y, x) order and bin order within a cell; a warp scan of the per-cell
+// counts places every entry where a serial walk would, so the rows are the
+// same whatever the warp size.
 template <int DIM>
-__global__ void assemble_kernel(const GridParams g, const MarkerBuffers m, const QuadBuffers q,
-                                const unsigned *__restrict__ keys, const int *__restrict__ perm) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128)
+assemble_kernel(const GridParams g, const MarkerBuffers m, const QuadBuffers q,
+                const unsigned *__restrict__ keys, const int *__restrict__ perm) {
+    constexpr int NCELLS = DIM == 3 ? 125 : 25;
+    const int lane = threadIdx.x & 31;
+    const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (k >= m.ns) return;
     int ck[3] = {0, 0, 0};
     double wk[3][3];
@@ -27,47 +36,66 @@ __global__ void assemble_kernel(const GridParams g, const MarkerBuffers m, const
         const double fk = m.frac_d[(long long)k * 3 + d];
         for (int i = 0; i < 3; ++i) wk[d][i] = phi_d(((double)(i - 1) + 0.5) - fk);
     }
-    int cnt = 0;
+    int base = 0;
     bool overflow = false;
-    const int zr = DIM == 3 ? 2 : 0;
-    for (int oz = -zr; oz <= zr; ++oz)
-        for (int oy = -2; oy <= 2; ++oy)
-            for (int ox = -2; ox <= 2; ++ox) {
-                const int x = ck[0] + ox, y = ck[1] + oy, z = (DIM == 3 ? ck[2] : 0) + oz;
-                if (x < 0 || y < 0 || z < 0 || x >= g.n[0] || y >= g.n[1]) continue;
-                if (DIM == 3 && z >= g.n[2]) continue;
+    for (int r0 = 0; r0 < NCELLS; r0 += 32) {
+        const int c = r0 + lane;
+        int lo = 0, end = 0;
+        if (c < NCELLS) {
+            const int ox = c % 5 - 2, oy = (c / 5) % 5 - 2, oz = DIM == 3 ? c / 25 - 2 : 0;
+            const int x = ck[0] + ox, y = ck[1] + oy, z = (DIM == 3 ? ck[2] : 0) + oz;
+            const bool in = x >= 0 && y >= 0 && z >= 0 && x < g.n[0] && y < g.n[1] &&
+                            (DIM == 2 || z < g.n[2]);
+            if (in) {
                 const unsigned key = cell_key(g, x, y, z);
                 const int tc = (int)(key / (unsigned)g.cells_per_tile);
-                int lo = m.tile_off[tc], hi = m.tile_off[tc + 1];
-                const int end = hi;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (keys[mid] < key) lo = mid + 1;
-                    else hi = mid;
+                int a = m.tile_off[tc], b = m.tile_off[tc + 1];
+                const int tend = b;
+                while (a < b) {
+                    const int mid = (a + b) >> 1;
+                    if (keys[mid] < key) a = mid + 1;
+                    else b = mid;
                 }
-                for (int p = lo; p < end && keys[p] == key; ++p) {
-                    const int l = perm[p];
-                    double a = 1.0;
-                    for (int d = 0; d < DIM; ++d) {
-                        const int cl = m.cell[(long long)l * 3 + d];
-                        const double fl = m.frac_d[(long long)l * 3 + d];
-                        double s = 0.0;
-                        for (int i = 0; i < 3; ++i)
-                            s += wk[d][i] * phi_d(((double)(ck[d] - 1 + i - cl) + 0.5) - fl);
-                        a *= s;
-                    }
-                    if (l == k) q.diag[k] = a;
-                    if (cnt < q.width) {
-                        q.col[(long long)cnt * q.cap + k] = l;
-                        q.val[(long long)cnt * q.cap + k] = a;
-                        ++cnt;
-                    } else {
-                        overflow = true;
-                    }
-                }
+                lo = a;
+                end = a;
+                while (end < tend && keys[end] == key) ++end;
             }
-    q.cnt[k] = cnt;
-    if (overflow) record_error(m.err, ERR_CAPACITY);
+        }
+        const int cnt = end - lo;
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        int w = base + incl - cnt;
+        for (int p = lo; p < end; ++p, ++w) {
+            const int l = perm[p];
+            double a = 1.0;
+            for (int d = 0; d < DIM; ++d) {
+                const int cl = m.cell[(long long)l * 3 + d];
+                const double fl = m.frac_d[(long long)l * 3 + d];
+                double sum = 0.0;
+                for (int i = 0; i < 3; ++i)
+                    sum += wk[d][i] * phi_d(((double)(ck[d] - 1 + i - cl) + 0.5) - fl);
+                a *= sum;
+            }
+            if (l == k) q.diag[k] = a;
+            if (w < q.width) {
+                q.col[(long long)w * q.cap + k] = l;
+                q.val[(long long)w * q.cap + k] = a;
+            } else {
+                overflow = true;
+            }
+        }
+        base += tot;
+    }
+    overflow = __any_sync(0xffffffffu, overflow);
+    if (lane == 0) {
+        q.cnt[k] = base < q.width ? base : q.width;
+        if (overflow) record_error(m.err, ERR_CAPACITY);
+    }
 }
 
 template <int NTH>
@@ -181,33 +209,136 @@ pcg_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rh
     }
 }
 
+// Small systems: A~ is assembled dense in shared memory from the ELL rows and
+// factored A~ = L L^T by a right-looking Cholesky (FP64, fixed order, one
+// CTA), then the two triangular solves.  ~ns^3/6 multiply-adds against a
+// few hundred latency-bound CG iterations; the residual max|rhs - A~ x| is
+// checked against tol like the CG's.  A non-positive pivot (A~ not positive
+// definite) records ERR_NOCONV.
+constexpr int CHOL_T = 512;
+#ifndef IBM_CHOL_MAX
+#define IBM_CHOL_MAX 160
+#endif
+constexpr int CHOL_MAX = IBM_CHOL_MAX;   // (ns^2 + ns) doubles of shared memory
+
+__global__ void __launch_bounds__(CHOL_T)
+chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rhs, double tol,
+            int *err) {
+    extern __shared__ __align__(16) double sA[];   // [ns][ns] row-major, then b[ns]
+    double *b = sA + (size_t)ns * ns;
+    __shared__ double s_red[CHOL_T / 32];
+    __shared__ int s_bad;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < ns * ns; i += CHOL_T) sA[i] = 0.0;
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    for (int k = tid; k < ns; k += CHOL_T) {
+        const int c = q.cnt[k];
+        for (int i = 0; i < c; ++i)
+            sA[(size_t)k * ns + q.col[(long long)i * q.cap + k]] = q.val[(long long)i * q.cap + k];
+        b[k] = rhs ? rhs[k] : 1.0;
+    }
+    __syncthreads();
+    // factor: column j of L, then the trailing lower triangle
+    for (int j = 0; j < ns; ++j) {
+        if (tid == 0) {
+            const double d = sA[(size_t)j * ns + j];
+            if (!(d > 0.0)) s_bad = 1;
+            sA[(size_t)j * ns + j] = d > 0.0 ? sqrt(d) : 1.0;
+        }
+        __syncthreads();
+        const double inv = 1.0 / sA[(size_t)j * ns + j];
+        for (int i = j + 1 + tid; i < ns; i += CHOL_T) sA[(size_t)i * ns + j] *= inv;
+        __syncthreads();
+        // trailing lower triangle: one warp per row, lanes along the row
+        for (int i = j + 1 + (tid >> 5); i < ns; i += CHOL_T / 32) {
+            const double lij = sA[(size_t)i * ns + j];
+            for (int kk = j + 1 + (tid & 31); kk <= i; kk += 32)
+                sA[(size_t)i * ns + kk] -= lij * sA[(size_t)kk * ns + j];
+        }
+        __syncthreads();
+    }
+    // L y = b (forward), L^T x = y (backward), one unknown per step
+    for (int j = 0; j < ns; ++j) {
+        if (tid == 0) b[j] /= sA[(size_t)j * ns + j];
+        __syncthreads();
+        const double yj = b[j];
+        for (int i = j + 1 + tid; i < ns; i += CHOL_T) b[i] -= sA[(size_t)i * ns + j] * yj;
+        __syncthreads();
+    }
+    for (int j = ns - 1; j >= 0; --j) {
+        if (tid == 0) b[j] /= sA[(size_t)j * ns + j];
+        __syncthreads();
+        const double xj = b[j];
+        for (int i = tid; i < j; i += CHOL_T) b[i] -= sA[(size_t)j * ns + i] * xj;
+        __syncthreads();
+    }
+    for (int k = tid; k < ns; k += CHOL_T) x[k] = b[k];
+    __syncthreads();
+    // true residual with the ELL matrix
+    double lm = 0.0;
+    for (int k = tid; k < ns; k += CHOL_T) {
+        const int c = q.cnt[k];
+        double sum = 0.0;
+        for (int i = 0; i < c; ++i)
+            sum += q.val[(long long)i * q.cap + k] * x[q.col[(long long)i * q.cap + k]];
+        lm = fmax(lm, fabs((rhs ? rhs[k] : 1.0) - sum));
+    }
+    const double rmax = block_max<CHOL_T>(lm, s_red);
+    if (tid == 0) {
+        *q.iters = 0;
+        *q.resid = rmax;
+        if (s_bad || !(rmax <= tol)) record_error(err, ERR_NOCONV);
+    }
+}
+
 }  // namespace
 
 int quad_row_width(int dim) { return dim == 3 ? 125 * 4 : 25 * 4; }
+
+// A~ x = rhs (rhs == nullptr: all ones): dense Cholesky up to CHOL_MAX
+// markers, Jacobi-PCG (warm start if asked) above
+static cudaError_t launch_quadrature_solve_w(int ns, const QuadBuffers &qb, const double *rhs,
+                                            double *x, double tol, int maxit, int warm, int *err,
+                                            cudaStream_t s) {
+    if (ns <= 0) return cudaSuccess;
+    if (ns <= CHOL_MAX) {
+        const size_t smem = sizeof(double) * ((size_t)ns * ns + ns);
+        static bool configured = false;
+        if (!configured) {
+            cudaError_t e = cudaFuncSetAttribute(
+                chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                (int)(sizeof(double) * ((size_t)CHOL_MAX * CHOL_MAX + CHOL_MAX)));
+            if (e != cudaSuccess) return e;
+            configured = true;
+        }
+        chol_kernel<<<1, CHOL_T, smem, s>>>(ns, qb, x, rhs, tol, err);
+    } else if (ns <= 2048) {
+        pcg_kernel<256><<<1, 256, 0, s>>>(ns, qb, x, rhs, tol, maxit, warm, err);
+    } else {
+        pcg_kernel<1024><<<1, 1024, 0, s>>>(ns, qb, x, rhs, tol, maxit, warm, err);
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_quadrature(const GridParams &g, const MarkerBuffers &m, const QuadBuffers &qb,
                               double tol, int maxit, int warm, cudaStream_t s) {
     if (m.ns <= 0) return cudaSuccess;
     const unsigned *keys = m.keys[m.sorted];
     const int *perm = m.perm[m.sorted];
-    const int nb = (m.ns + 127) / 128;
+    const int nb = (m.ns * 32 + 127) / 128;   // one warp per marker
     if (g.dim == 3) assemble_kernel<3><<<nb, 128, 0, s>>>(g, m, qb, keys, perm);
     else assemble_kernel<2><<<nb, 128, 0, s>>>(g, m, qb, keys, perm);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (m.ns <= 2048) pcg_kernel<256><<<1, 256, 0, s>>>(m.ns, qb, m.eps, nullptr, tol, maxit, warm, m.err);
-    else pcg_kernel<1024><<<1, 1024, 0, s>>>(m.ns, qb, m.eps, nullptr, tol, maxit, warm, m.err);
-    return cudaGetLastError();
+    return launch_quadrature_solve_w(m.ns, qb, nullptr, m.eps, tol, maxit, warm, m.err, s);
 }
 
 // A~ x = rhs with the matrix assembled by the last launch_quadrature (the
 // adjoint of the weights); x starts from zero.
 cudaError_t launch_quadrature_solve(int ns, const QuadBuffers &qb, const double *rhs, double *x,
                                     double tol, int maxit, int *err, cudaStream_t s) {
-    if (ns <= 0) return cudaSuccess;
-    if (ns <= 2048) pcg_kernel<256><<<1, 256, 0, s>>>(ns, qb, x, rhs, tol, maxit, 0, err);
-    else pcg_kernel<1024><<<1, 1024, 0, s>>>(ns, qb, x, rhs, tol, maxit, 0, err);
-    return cudaGetLastError();
+    return launch_quadrature_solve_w(ns, qb, rhs, x, tol, maxit, 0, err, s);
 }
 
 }  // namespace ibmk
