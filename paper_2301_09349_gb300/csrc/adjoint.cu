@@ -329,60 +329,91 @@ __device__ __forceinline__ void face_vjp(const AdjK<R> &k, const R (&w)[4][DIM +
     }
 }
 
-// lamW (primitive adjoints) += J_L(U)^T V restricted to the faces normal to D
 constexpr int FT = 128;   // flux-reverse CTA: ~150 live registers per face
 
+// ---- tiled form: one CTA per tile of cells -------------------------------
+// The CTA stages the primitives of its tile plus a two-cell halo (ghosts
+// through the boundary maps) in shared memory, reverses every face it owns
+// - the faces whose upper cell b lies in the tile, and on the last tile of an
+// axis also the domain face b = n - accumulating the stencil adjoints in
+// shared memory, then adds the tile-plus-halo accumulators to the source
+// cells in global memory (slip flips applied, free-stream ghosts dropped).
+template <int DIM, typename T> struct AdjTile;
+template <> struct AdjTile<3, float> { static constexpr int BX = 8, BY = 8, BZ = 8; };
+template <> struct AdjTile<3, double> { static constexpr int BX = 8, BY = 8, BZ = 4; };
+template <> struct AdjTile<2, float> { static constexpr int BX = 16, BY = 16, BZ = 1; };
+template <> struct AdjTile<2, double> { static constexpr int BX = 16, BY = 16, BZ = 1; };
+
+template <int DIM, typename T>
+struct AdjBox {
+    static constexpr int BX = AdjTile<DIM, T>::BX, BY = AdjTile<DIM, T>::BY,
+                         BZ = AdjTile<DIM, T>::BZ;
+    static constexpr int PX = BX + 4, PY = BY + 4, PZ = DIM == 3 ? BZ + 4 : 1;
+    static constexpr int PN = PX * PY * PZ;
+    static constexpr size_t SMEM = 2 * sizeof(T) * (size_t)(DIM + 2) * PN;
+};
+
 template <int DIM, int D, typename T>
-__global__ void __launch_bounds__(FT, 3)
-adj_flux_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ V,
-                T *__restrict__ lamW) {
+__device__ __forceinline__ void tile_faces(const GridParams &g, const AdjK<T> &k,
+                                           const T *__restrict__ V, const T *__restrict__ Wsm,
+                                           T *__restrict__ Acc, int ox, int oy, int oz) {
+    using B = AdjBox<DIM, T>;
     using R = T;
     constexpr int NC = DIM + 2;
     constexpr int NT2 = ntan(DIM);
-    const AdjK<R> k(g);
-    int ext[3] = {g.n[0], g.n[1], DIM == 3 ? g.n[2] : 1};
-    ext[D] += 1;
-    const long long nf = (long long)ext[0] * ext[1] * ext[2];
+    constexpr int PN = B::PN;
+    const int o[3] = {ox, oy, oz};
+    const int bsz[3] = {B::BX, B::BY, B::BZ};
+    const int str[3] = {1, B::PX, B::PX * B::PY};
+    int cnt[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int n = e < DIM ? g.n[e] : 1;
+        const int b = e < DIM ? bsz[e] : 1;
+        cnt[e] = min(b, n - o[e]);
+    }
+    if (o[D] + bsz[D] >= g.n[D]) cnt[D] += 1;   // the last tile owns the domain face b = n
+    const int nf = cnt[0] * cnt[1] * cnt[2];
     const long long N = g.N;
-    for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf;
-         f += (long long)gridDim.x * blockDim.x) {
-        int c[3];
-        c[0] = (int)(f % ext[0]);
-        const long long r = f / ext[0];
-        c[1] = (int)(r % ext[1]);
-        c[2] = (int)(r / ext[1]);
-        // b = c, a = c - e_D
-        const bool b_in = c[D] < g.n[D], a_in = c[D] >= 1;
+    for (int f = threadIdx.x; f < nf; f += FT) {
+        int l[3];
+        l[0] = f % cnt[0];
+        l[1] = (f / cnt[0]) % cnt[1];
+        l[2] = f / (cnt[0] * cnt[1]);
+        const int gb = o[D] + l[D];
+        const bool b_in = gb < g.n[D], a_in = gb >= 1;
+        long long jb = 0, ja = 0;
+        {
+            int c[3] = {o[0] + l[0], o[1] + l[1], o[2] + l[2]};
+            jb = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+            c[D] -= 1;
+            ja = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+        }
         R Fb[NC];
         bool any = false;
-        {
-            int ca[3] = {c[0], c[1], c[2]};
-            ca[D] -= 1;
-            const long long jb = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
-            const long long ja = ca[0] + (long long)g.n[0] * (ca[1] + (long long)g.n[1] * ca[2]);
 #pragma unroll
-            for (int q = 0; q < NC; ++q) {
-                const R vb = b_in ? (R)V[q * N + jb] : R(0);
-                const R va = a_in ? (R)V[q * N + ja] : R(0);
-                Fb[q] = (vb - va) * k.inv_h;
-                any |= Fb[q] != R(0);
-            }
+        for (int q = 0; q < NC; ++q) {
+            const R vb = b_in ? V[q * N + jb] : R(0);
+            const R va = a_in ? V[q * N + ja] : R(0);
+            Fb[q] = (vb - va) * k.inv_h;
+            any |= Fb[q] != R(0);
         }
         if (!any) continue;
+        const int qb = (l[0] + 2) + B::PX * ((l[1] + 2) + B::PY * (DIM == 3 ? l[2] + 2 : 0));
+        const int sD = str[D];
+        int qs[4];
         R w[4][NC], wb[4][NC];
-        long long src[4];
-        int flip[4], fs[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            int p[3] = {c[0], c[1], c[2]};
-            p[D] += i - 2;
-            load_prim<DIM, T, R>(g, k, U, p[0], p[1], p[2], w[i], src[i], flip[i], fs[i]);
+            qs[i] = qb + (i - 2) * sD;
 #pragma unroll
-            for (int q = 0; q < NC; ++q) wb[i][q] = R(0);
+            for (int c = 0; c < NC; ++c) {
+                w[i][c] = Wsm[c * PN + qs[i]];
+                wb[i][c] = R(0);
+            }
         }
         R ut[NT2][4][DIM], utb[NT2][4][DIM];
-        long long srct[NT2][4];
-        int flipt[NT2][4], fst[NT2][4];
+        int qt[NT2][4];
         {
             int ti = 0;
 #pragma unroll
@@ -390,15 +421,10 @@ adj_flux_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict
                 if (e == D) continue;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    int p[3] = {c[0], c[1], c[2]};
-                    if (i < 2) p[D] -= 1;        // a - t, a + t, then b - t, b + t
-                    p[e] += (i & 1) ? 1 : -1;
-                    R wt[NC];
-                    load_prim<DIM, T, R>(g, k, U, p[0], p[1], p[2], wt, srct[ti][i], flipt[ti][i],
-                                         fst[ti][i]);
+                    qt[ti][i] = (i < 2 ? qb - sD : qb) + ((i & 1) ? str[e] : -str[e]);
 #pragma unroll
                     for (int m = 0; m < DIM; ++m) {
-                        ut[ti][i][m] = wt[1 + m];
+                        ut[ti][i][m] = Wsm[(1 + m) * PN + qt[ti][i]];
                         utb[ti][i][m] = R(0);
                     }
                 }
@@ -406,29 +432,69 @@ adj_flux_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict
             }
         }
         face_vjp<DIM, D, R>(k, w, ut, Fb, wb, utb);
-        // scatter to the source cells (free-stream ghosts are constants)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (fs[i]) continue;
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int q = 0; q < NC; ++q) {
-                R v = wb[i][q];
-                if (q >= 1 && q <= DIM && ((flip[i] >> (q - 1)) & 1)) v = -v;
-                if (v != R(0)) atomicAdd(lamW + q * N + src[i], v);
-            }
-        }
+            for (int c = 0; c < NC; ++c)
+                if (wb[i][c] != R(0)) atomicAdd(Acc + c * PN + qs[i], wb[i][c]);
 #pragma unroll
         for (int ti = 0; ti < (DIM > 1 ? DIM - 1 : 0); ++ti)
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (fst[ti][i]) continue;
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int m = 0; m < DIM; ++m) {
-                    R v = utb[ti][i][m];
-                    if ((flipt[ti][i] >> m) & 1) v = -v;
-                    if (v != R(0)) atomicAdd(lamW + (1 + m) * N + srct[ti][i], v);
-                }
-            }
+                for (int m = 0; m < DIM; ++m)
+                    if (utb[ti][i][m] != R(0)) atomicAdd(Acc + (1 + m) * PN + qt[ti][i], utb[ti][i][m]);
+    }
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(FT, 3)
+adj_flux_tile_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ V,
+                     T *__restrict__ lamW) {
+    using B = AdjBox<DIM, T>;
+    using R = T;
+    constexpr int NC = DIM + 2;
+    constexpr int PN = B::PN;
+    extern __shared__ __align__(16) unsigned char smem_adj[];
+    R *Wsm = reinterpret_cast<R *>(smem_adj);   // [NC][PN] primitives
+    R *Acc = Wsm + NC * PN;                      // [NC][PN] adjoint sums
+    const AdjK<R> k(g);
+    const int ox = blockIdx.x * B::BX, oy = blockIdx.y * B::BY;
+    const int oz = DIM == 3 ? blockIdx.z * B::BZ : 0;
+    for (int q = threadIdx.x; q < PN; q += FT) {
+        const int lx = q % B::PX, ly = (q / B::PX) % B::PY, lz = q / (B::PX * B::PY);
+        R w[NC];
+        long long src;
+        int flip, fs;
+        load_prim<DIM, T, R>(g, k, U, ox + lx - 2, oy + ly - 2, DIM == 3 ? oz + lz - 2 : 0, w, src,
+                             flip, fs);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            Wsm[c * PN + q] = w[c];
+            Acc[c * PN + q] = R(0);
+        }
+    }
+    __syncthreads();
+    tile_faces<DIM, 0, T>(g, k, V, Wsm, Acc, ox, oy, oz);
+    tile_faces<DIM, 1, T>(g, k, V, Wsm, Acc, ox, oy, oz);
+    if constexpr (DIM == 3) tile_faces<DIM, (DIM == 3 ? 2 : 0), T>(g, k, V, Wsm, Acc, ox, oy, oz);
+    __syncthreads();
+    const long long N = g.N;
+    for (int q = threadIdx.x; q < PN; q += FT) {
+        const int lx = q % B::PX, ly = (q / B::PX) % B::PY, lz = q / (B::PX * B::PY);
+        int flip = 0, fs = 0;
+        const int sx = map_axis(ox + lx - 2, g.n[0], g.bc[0], g.bc[1], 0, flip, fs);
+        const int sy = map_axis(oy + ly - 2, g.n[1], g.bc[2], g.bc[3], 1, flip, fs);
+        const int sz = DIM == 3 ? map_axis(oz + lz - 2, g.n[2], g.bc[4], g.bc[5], 2, flip, fs) : 0;
+        if (fs) continue;
+        const long long src = sx + (long long)g.n[0] * (sy + (long long)g.n[1] * sz);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            R v = Acc[c * PN + q];
+            if (v == R(0)) continue;
+            if (c >= 1 && c <= DIM && ((flip >> (c - 1)) & 1)) v = -v;
+            atomicAdd(lamW + c * N + src, v);
+        }
     }
 }
 
@@ -767,15 +833,20 @@ cudaError_t rhs_vjp_t(const GridParams &g, const void *U, const void *V, void *l
                       cudaStream_t s) {
     const T *u = (const T *)U, *v = (const T *)V;
     T *lamW = (T *)lamW_;
-    for (int D = 0; D < DIM; ++D) {
-        const long long faces = g.N / g.n[D] * (g.n[D] + 1);
-        const int nb = grid_for(faces, FT);
-        if (D == 0) adj_flux_kernel<DIM, 0, T><<<nb, FT, 0, s>>>(g, u, v, lamW);
-        else if (D == 1) adj_flux_kernel<DIM, 1, T><<<nb, FT, 0, s>>>(g, u, v, lamW);
-        else adj_flux_kernel<DIM, (DIM == 3 ? 2 : 0), T><<<nb, FT, 0, s>>>(g, u, v, lamW);
-        cudaError_t e = cudaGetLastError();
+    using B = AdjBox<DIM, T>;
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(adj_flux_tile_kernel<DIM, T>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)B::SMEM);
         if (e != cudaSuccess) return e;
+        configured = true;
     }
+    const dim3 grid((g.n[0] + B::BX - 1) / B::BX, (g.n[1] + B::BY - 1) / B::BY,
+                    DIM == 3 ? (g.n[2] + B::BZ - 1) / B::BZ : 1);
+    adj_flux_tile_kernel<DIM, T><<<grid, FT, B::SMEM, s>>>(g, u, v, lamW);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     adj_prim_kernel<DIM, T><<<grid_for(g.N), AT, 0, s>>>(g, u, lamW, (T *)out);
     return cudaGetLastError();
 }
