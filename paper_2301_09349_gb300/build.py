@@ -20,6 +20,10 @@ UNITS = ["flux.cu", "flux_zm.cu", "markers.cu", "quadrature.cu", "api.cu", "noal
          "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE]
+# The FP32 fluid-stage units flush subnormals to zero: no value of the flow
+# comes near 1e-38, and the approximate reciprocals and square roots then need
+# no subnormal handling (4-5 % of the stage time on the 3D and 2D kernels).
+UNIT_FLAGS = {"flux.cu": ["-ftz=true"], "flux_zm.cu": ["-ftz=true"]}
 # extra nvcc flags (e.g. -DIBM_ZM_MIN_BLOCKS=2) for build variants
 EXTRA = os.environ.get("IBM_NVCC_FLAGS", "").split()
 
@@ -54,7 +58,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(unit):
         obj = os.path.join(objdir, unit.replace(".cu", ".o"))
-        cmd = [cc] + ARCH + FLAGS + EXTRA + ["-c", os.path.join(SRC, unit), "-o", obj]
+        cmd = [cc] + ARCH + FLAGS + UNIT_FLAGS.get(unit, []) + EXTRA + ["-c", os.path.join(SRC, unit),
+                                                                        "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s" % (unit, r.stderr))

@@ -214,9 +214,11 @@ __device__ __forceinline__ float2 p_abs(float2 a) { return make_float2(fabsf(a.x
 __device__ __forceinline__ float2 p_max(float2 a, float2 b) {
     return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y));
 }
-__device__ __forceinline__ float2 p_vl(float2 a, float2 b) {
+// half the van Leer slope, ab / (a + b) where ab > 0: the face states are
+// w +- psi/2, and the factor 2 of psi = 2ab/(a+b) and the 1/2 cancel exactly
+__device__ __forceinline__ float2 p_vlh(float2 a, float2 b) {
     const float2 ab = p_mul(a, b);
-    const float2 q = p_mul(p_add(ab, ab), p_rcp(p_add(a, b)));
+    const float2 q = p_mul(ab, p_rcp(p_add(a, b)));
     return make_float2(ab.x > 0.0f ? q.x : 0.0f, ab.y > 0.0f ? q.y : 0.0f);
 }
 
@@ -238,8 +240,8 @@ __device__ __forceinline__ void face_pair2d(const FluxK<float> &k, const float *
         const float2 x2 = make_float2(X[ax + 1], Y[ay + PX]);
         const float2 x3 = make_float2(X[ax + 2], Y[ay + 2 * PX]);
         const float2 d0 = p_sub(x1, x0), d1 = p_sub(x2, x1), d2 = p_sub(x3, x2);
-        wl[m] = p_fma(p_s(0.5f), p_vl(d0, d1), x1);
-        wr[m] = p_fma(p_s(-0.5f), p_vl(d1, d2), x2);
+        wl[m] = p_add(x1, p_vlh(d0, d1));
+        wr[m] = p_sub(x2, p_vlh(d1, d2));
     }
     const float2 keL = p_fma(wl[1], wl[1], p_mul(wl[2], wl[2]));
     const float2 keR = p_fma(wr[1], wr[1], p_mul(wr[2], wr[2]));

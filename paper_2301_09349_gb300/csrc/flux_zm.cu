@@ -87,9 +87,11 @@ __device__ __forceinline__ float2 abs2(float2 a) { return make_float2(fabsf(a.x)
 __device__ __forceinline__ float2 max2(float2 a, float2 b) {
     return make_float2(fmaxf(a.x, b.x), fmaxf(a.y, b.y));
 }
-__device__ __forceinline__ float2 vl2(float2 a, float2 b) {
+// half the van Leer slope, ab / (a + b) where ab > 0: the face states are
+// w +- psi/2, and the factor 2 of psi = 2ab/(a+b) and the 1/2 cancel exactly
+__device__ __forceinline__ float2 vlh2(float2 a, float2 b) {
     const float2 ab = a * b;
-    const float2 q = (ab + ab) * rcp2(a + b);
+    const float2 q = ab * rcp2(a + b);
     return make_float2(ab.x > 0.0f ? q.x : 0.0f, ab.y > 0.0f ? q.y : 0.0f);
 }
 
@@ -111,8 +113,8 @@ __device__ __forceinline__ void face_xy(const FC &c, const float *__restrict__ R
         const float2 x2 = make_float2(X[ax + 1], Y[ay + PX]);
         const float2 x3 = make_float2(X[ax + 2], Y[ay + 2 * PX]);
         const float2 d0 = x1 - x0, d1 = x2 - x1, d2 = x3 - x2;
-        wl[m] = fma2(sp(0.5f), vl2(d0, d1), x1);
-        wr[m] = fma2(sp(-0.5f), vl2(d1, d2), x2);
+        wl[m] = x1 + vlh2(d0, d1);
+        wr[m] = x2 - vlh2(d1, d2);
     }
     const float2 keL = fma2(wl[1], wl[1], fma2(wl[2], wl[2], wl[3] * wl[3]));
     const float2 keR = fma2(wr[1], wr[1], fma2(wr[2], wr[2], wr[3] * wr[3]));
@@ -231,7 +233,7 @@ __device__ __forceinline__ void face_zz(const FC &c, const float *__restrict__ R
     F[4] = F[4] - fma2(ufw, tzz, fma2(ufu, tzx, fma2(ufv, tzy, lam * dn_T)));
 }
 
-// limited z-slopes of two columns (A -> .x, B -> .y) at the middle plane
+// half the limited z-slopes of two columns (A -> .x, B -> .y) at the middle plane
 __device__ __forceinline__ void column_slope2(const float *__restrict__ R, int loA, int midA,
                                               int hiA, int loB, int midB, int hiB,
                                               float2 (&sig)[NC]) {
@@ -240,7 +242,7 @@ __device__ __forceinline__ void column_slope2(const float *__restrict__ R, int l
         const float *w = R + m * PP;
         const float2 lo = make_float2(w[loA], w[loB]), mid = make_float2(w[midA], w[midB]),
                      hi = make_float2(w[hiA], w[hiB]);
-        sig[m] = vl2(mid - lo, hi - mid);
+        sig[m] = vlh2(mid - lo, hi - mid);
     }
 }
 
@@ -439,7 +441,7 @@ zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, cons
     // warps 0-3 own the z-faces of two cell rows each (2w -> .x, 2w+1 -> .y)
     const bool zwarp = ly < TY / 2;
     const int cA = (lx + 2) + PX * (2 * ly + 2), cB = cA + PX;
-    float2 sig0[NC];   // limited z-slopes of the current plane's cells, carried up
+    float2 sig0[NC];   // half limited z-slopes of the current plane's cells, carried up
     if (zwarp) {       // z-face below the first plane (z0 - 1/2)
         const int sam = slot_of(z0 - 2), sa = slot_of(z0 - 1), sb = slot_of(z0), sbp = slot_of(z0 + 1);
         float2 sgA[NC], wl[NC], wr[NC], F[NC];
@@ -447,8 +449,8 @@ zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, cons
         column_slope2(ring, sa + cA, sb + cA, sbp + cA, sa + cB, sb + cB, sbp + cB, sig0);
 #pragma unroll
         for (int m = 0; m < NC; ++m) {
-            wl[m] = fma2(sp(0.5f), sgA[m], make_float2(ring[sa + m * PP + cA], ring[sa + m * PP + cB]));
-            wr[m] = fma2(sp(-0.5f), sig0[m], make_float2(ring[sb + m * PP + cA], ring[sb + m * PP + cB]));
+            wl[m] = make_float2(ring[sa + m * PP + cA], ring[sa + m * PP + cB]) + sgA[m];
+            wr[m] = make_float2(ring[sb + m * PP + cA], ring[sb + m * PP + cB]) - sig0[m];
         }
         face_zz(c, ring, sa + cA, sb + cA, sa + cB, sb + cB, wl, wr, F);
         float *Fz = FZb + ((z0 - 1) & 1) * NC * TY * TX;
@@ -509,8 +511,8 @@ zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, cons
             column_slope2(ring, s0 + cA, s1 + cA, s2 + cA, s0 + cB, s1 + cB, s2 + cB, sig1);
 #pragma unroll
             for (int m = 0; m < NC; ++m) {
-                wl[m] = fma2(sp(0.5f), sig0[m], make_float2(ring[s0 + m * PP + cA], ring[s0 + m * PP + cB]));
-                wr[m] = fma2(sp(-0.5f), sig1[m], make_float2(ring[s1 + m * PP + cA], ring[s1 + m * PP + cB]));
+                wl[m] = make_float2(ring[s0 + m * PP + cA], ring[s0 + m * PP + cB]) + sig0[m];
+                wr[m] = make_float2(ring[s1 + m * PP + cA], ring[s1 + m * PP + cB]) - sig1[m];
                 sig0[m] = sig1[m];
             }
             face_zz(c, ring, s0 + cA, s1 + cA, s0 + cB, s1 + cB, wl, wr, F);
