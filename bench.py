@@ -506,20 +506,20 @@ def run_batched(args, rank, world, local):
         gr.close()
 
     # end to end through the C ABI with host buffers: per step the wall
-    # temperatures of every case go up from page-locked memory, the batch
-    # steps, and the forces of all cases come back in one read
-    Tw_pin = []
+    # temperatures of every case go up from page-locked memory in one copy,
+    # the batch steps, and the forces of all cases come back in one read
+    tws = []
     for cg, c in zip(b.cases, cs):
         _, _, idx = cg.markers()
-        t = torch.empty(len(idx), dtype=torch.float64, pin_memory=True).numpy()
-        t[:] = c.Tw[idx]
-        Tw_pin.append(t)
+        tws.append(c.Tw[idx])
+    tw_all = np.concatenate(tws)
+    Tw_pin = torch.empty(len(tw_all), dtype=torch.float64, pin_memory=True).numpy()
+    Tw_pin[:] = tw_all
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        for cg, t in zip(b.cases, Tw_pin):
-            ibm.ibm_set_wall_temperature(cg.h, t)
+        ibm.ibm_batch_set_wall_temperature(b.h, Tw_pin)
         ibm.ibm_batch_step(b.h, 1)
         res = ibm.ibm_batch_forces(b.h, len(cs))
     e2e_s = time.perf_counter() - t0
@@ -575,8 +575,8 @@ def run_batched(args, rank, world, local):
             "gpu_launches": 5 * steps * world,
             "e2e": {"value": cells_all * steps / (e2e_ms_max * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * int(sum(kept)),
-                    "d2h_bytes_per_step": 48 * len(cs),
-                    "path": "ibm_set_wall_temperature per case (pinned host) + ibm_batch_step + "
+                    "d2h_bytes_per_step": 64 * len(cs),
+                    "path": "ibm_batch_set_wall_temperature (pinned host) + ibm_batch_step + "
                             "ibm_batch_forces per step"},
             "clocks": clk,
             "result": {"Cd_case0": float(res[0, 3]), "Nu_case0": float(res[0, 5])},

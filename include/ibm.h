@@ -345,6 +345,16 @@ ibm_status ibm_batch_step(ibm_batch *b, int nsteps, double dt_fixed);
  * NULL) is the first failing case and the status is that case's. */
 ibm_status ibm_batch_sync(ibm_batch *b, int *bad_case);
 
+/* Wall temperatures of every case in one upload: Tw holds the kept markers of
+ * case 0, then case 1, ... (host, ibm_batch_case(b, c)'s n_kept values per
+ * case, in each case's kept order), the batch counterpart of
+ * ibm_set_wall_temperature (T_w of Eq. corr3.8's target rho_L c_v T_w).
+ * Every value must be finite and positive (IBM_ERR_ARG otherwise, nothing
+ * changed).  Tw is read before the call returns if it is pageable and by the
+ * stream's copy otherwise, so page-locked buffers must stay unchanged until
+ * the next synchronizing call. */
+ibm_status ibm_batch_set_wall_temperature(ibm_batch *b, const double *Tw);
+
 /* Forces of all cases from one gathered device read: out[c*8 + i] for
  * i = 0..7 holds Fx, Fy, Q, Cd, Cl, Nu, dt, t of case c (as
  * ibm_forces_and_nusselt and ibm_get_time).  Synchronizes. */

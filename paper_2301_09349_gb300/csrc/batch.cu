@@ -16,6 +16,7 @@
 // replayed.  Each case's arithmetic is the single-grid kernels' own device
 // code, so a batch step is bitwise a per-case ibm_step.
 #include <math.h>
+#include <cmath>
 #include <string.h>
 
 #include <algorithm>
@@ -45,7 +46,11 @@ struct ibm_batch {
     double *band_max = nullptr;
     int2 *mk_items = nullptr;
     double *save = nullptr;     // autotune: the last marker forcing of every case
-    double *gather = nullptr;   // ncases * 6 force sums, dt and t
+    double *gather = nullptr;   // ncases * 8: force sums, dt, t and the error word
+    // wall temperatures: ncases slots, then the values of all kept markers
+    BatchTwSlot *tw_slots = nullptr;
+    double *tw_vals = nullptr;
+    std::vector<BatchTwSlot> tw_slots_h;   // what tw_slots holds on the device
     size_t stage_cap = 0, band_cap = 0, mk_cap = 0;
 
     // what the tables were built from
@@ -126,7 +131,7 @@ int marker_tiles(const ibm_grid_desc &d) {
 struct BatchLayout {
     std::vector<size_t> case_off, case_bytes;
     size_t tbl = 0, stage_items = 0, item_max = 0, band_items = 0, band_max = 0, mk_items = 0,
-           save = 0, gather = 0, total = 0;
+           save = 0, gather = 0, tw = 0, total = 0;
     size_t stage_cap = 0, band_cap = 0, mk_cap = 0;
 };
 
@@ -184,7 +189,8 @@ BatchLayout batch_layout(int ncases, const ibm_grid_desc *descs, const int *max_
     L.band_max = take(sizeof(double) * L.band_cap);
     L.mk_items = take(sizeof(int2) * L.mk_cap);
     L.save = take(sizeof(double) * 4 * L.mk_cap);
-    L.gather = take(sizeof(double) * 6 * (size_t)ncases);
+    L.gather = take(sizeof(double) * 8 * (size_t)ncases);
+    L.tw = take(sizeof(BatchTwSlot) * (size_t)ncases + sizeof(double) * L.mk_cap);
     L.total = align_up(off, 256);
     return L;
 }
@@ -444,6 +450,8 @@ ibm_status ibm_create_batch(int ncases, const ibm_grid_desc *descs, const int *m
     b->mk_items = (int2 *)(base + L.mk_items);
     b->save = (double *)(base + L.save);
     b->gather = (double *)(base + L.gather);
+    b->tw_slots = (BatchTwSlot *)(base + L.tw);
+    b->tw_vals = (double *)(b->tw_slots + ncases);
     b->stage_cap = L.stage_cap;
     b->band_cap = L.band_cap;
     b->mk_cap = L.mk_cap;
@@ -569,6 +577,44 @@ ibm_status ibm_batch_sync(ibm_batch *b, int *bad_case) {
     return IBM_OK;
 }
 
+ibm_status ibm_batch_set_wall_temperature(ibm_batch *b, const double *Tw) {
+    if (!b) return IBM_ERR_ARG;
+    const int nc = b->ncases;
+    std::vector<BatchTwSlot> slots((size_t)nc);
+    long long total = 0;
+    for (int c = 0; c < nc; ++c) {
+        ibm_grid *g = b->grids[c];
+        slots[c] = BatchTwSlot{g->mb.Tw, total, (long long)g->mb.ns};
+        total += g->mb.ns;
+    }
+    if (total == 0) return IBM_OK;
+    if (!Tw) return fail(b, IBM_ERR_ARG, "null wall temperatures");
+    for (long long k = 0; k < total; ++k)
+        if (!std::isfinite(Tw[k]) || Tw[k] <= 0.0)
+            return fail(b, IBM_ERR_ARG,
+                        "wall temperature " + std::to_string(k) + " must be finite and positive");
+    for (int c = 0; c < nc; ++c) {
+        ibm_grid *g = b->grids[c];
+        g->Tw_h.assign(Tw + slots[c].off, Tw + slots[c].off + slots[c].n);
+    }
+    // the slot table changes only with the kept-marker counts
+    bool same = b->tw_slots_h.size() == slots.size();
+    for (size_t c = 0; same && c < slots.size(); ++c)
+        same = b->tw_slots_h[c].dst == slots[c].dst && b->tw_slots_h[c].off == slots[c].off &&
+               b->tw_slots_h[c].n == slots[c].n;
+    if (!same) {
+        BCU(cudaMemcpyAsync(b->tw_slots, slots.data(), sizeof(BatchTwSlot) * nc,
+                            cudaMemcpyHostToDevice, b->stream),
+            "upload wall-temperature slots");
+        BCU(cudaStreamSynchronize(b->stream), "stream synchronize");
+        b->tw_slots_h = slots;
+    }
+    BCU(cudaMemcpyAsync(b->tw_vals, Tw, sizeof(double) * total, cudaMemcpyHostToDevice, b->stream),
+        "upload wall temperatures");
+    BCU(launch_batch_tw(b->tw_slots, nc, b->tw_vals, b->stream), "scatter wall temperatures");
+    return IBM_OK;
+}
+
 ibm_status ibm_batch_forces(ibm_batch *b, double *out) {
     if (!b) return IBM_ERR_ARG;
     if (!out) return fail(b, IBM_ERR_ARG, "null output");
@@ -576,16 +622,19 @@ ibm_status ibm_batch_forces(ibm_batch *b, double *out) {
     ibm_status st = current_parity(b, &p);
     if (st != IBM_OK) return st;
     const int nc = b->ncases;
-    std::vector<double> sums((size_t)nc * 6);
+    std::vector<double> sums((size_t)nc * 8);
     BCU(launch_batch_gather(b->tbl[p], nc, b->gather, b->stream), "gather sums");
-    BCU(cudaMemcpyAsync(sums.data(), b->gather, sizeof(double) * 6 * nc, cudaMemcpyDeviceToHost,
+    BCU(cudaMemcpyAsync(sums.data(), b->gather, sizeof(double) * 8 * nc, cudaMemcpyDeviceToHost,
                         b->stream),
         "read sums");
-    st = ibm_batch_sync(b, nullptr);
-    if (st != IBM_OK) return st;
+    BCU(cudaStreamSynchronize(b->stream), "stream synchronize");
+    // the error words came with the sums; a failing case reports as
+    // ibm_batch_sync would
+    for (int c = 0; c < nc; ++c)
+        if (sums[(size_t)c * 8 + 6] != 0.0) return ibm_batch_sync(b, nullptr);
     for (int c = 0; c < nc; ++c) {
         double f[3], q, cd, cl, nu;
-        const double *sc = &sums[(size_t)c * 6];
+        const double *sc = &sums[(size_t)c * 8];
         forces_from_sums(b->grids[c], sc, f, &q, &cd, &cl, &nu);
         double *o = out + (size_t)c * 8;
         o[0] = f[0];

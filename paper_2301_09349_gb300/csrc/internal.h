@@ -203,8 +203,15 @@ cudaError_t launch_batch_spread(int fp_bytes, size_t smem, const BatchCase *case
                                 cudaStream_t s);
 size_t batch_spread_smem(const GridParams &g, int fp_bytes);
 // per-case sums, time update and next step size (one CTA per case)
-// sums[0..4] and t of every case into out[c * 6 + 0..5]
+// sums[0..4], t and the error word of every case into out[c * 8 + 0..6]
 cudaError_t launch_batch_gather(const BatchCase *cases, int ncases, double *out, cudaStream_t s);
+// wall temperatures of a batch: slot c copies vals[off, off + n) to dst
+struct BatchTwSlot {
+    double *dst;
+    long long off, n;
+};
+cudaError_t launch_batch_tw(const BatchTwSlot *slots, int ncases, const double *vals,
+                            cudaStream_t s);
 cudaError_t launch_batch_finish(const BatchCase *cases, int ncases, const double *item_max,
                                 const double *band_max, double dt_fixed, cudaStream_t s);
 

@@ -816,8 +816,16 @@ __global__ void batch_gather_kernel(const BatchCase *__restrict__ cases, int nca
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= ncases) return;
     const MarkerBuffers &m = cases[c].m;
-    for (int i = 0; i < 5; ++i) out[c * 6 + i] = m.sums[i];
-    out[c * 6 + 5] = *m.t;
+    for (int i = 0; i < 5; ++i) out[c * 8 + i] = m.sums[i];
+    out[c * 8 + 5] = *m.t;
+    out[c * 8 + 6] = (double)*cases[c].err;
+    out[c * 8 + 7] = 0.0;
+}
+
+__global__ void batch_tw_kernel(const BatchTwSlot *__restrict__ slots,
+                                const double *__restrict__ vals) {
+    const BatchTwSlot sl = slots[blockIdx.x];
+    for (long long k = threadIdx.x; k < sl.n; k += blockDim.x) sl.dst[k] = vals[sl.off + k];
 }
 
 // ---------------------------------------------------------------------------
@@ -1070,6 +1078,13 @@ cudaError_t launch_batch_finish(const BatchCase *cases, int ncases, const double
 cudaError_t launch_batch_gather(const BatchCase *cases, int ncases, double *out, cudaStream_t s) {
     if (ncases <= 0) return cudaSuccess;
     batch_gather_kernel<<<(ncases + 127) / 128, 128, 0, s>>>(cases, ncases, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_tw(const BatchTwSlot *slots, int ncases, const double *vals,
+                            cudaStream_t s) {
+    if (ncases <= 0) return cudaSuccess;
+    batch_tw_kernel<<<ncases, 128, 0, s>>>(slots, vals);
     return cudaGetLastError();
 }
 

@@ -99,6 +99,7 @@ SIGNATURES = [
     ("ibm_batch_case", _vp, [_vp, ctypes.c_int]),
     ("ibm_batch_step", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double]),
     ("ibm_batch_sync", ctypes.c_int, [_vp, _ip]),
+    ("ibm_batch_set_wall_temperature", ctypes.c_int, [_vp, _dp]),
     ("ibm_batch_forces", ctypes.c_int, [_vp, _dp]),
     ("ibm_batch_get_tuning", ctypes.c_int, [_vp, ctypes.POINTER(BatchTuningC)]),
     ("ibm_batch_set_tuning", ctypes.c_int, [_vp, ctypes.POINTER(BatchTuningC)]),
@@ -392,6 +393,12 @@ def ibm_batch_sync(h):
     _bcheck(lib().ibm_batch_sync(h, ctypes.byref(bad)), h)
 
 
+def ibm_batch_set_wall_temperature(h, Tw):
+    """Tw: the kept markers' wall temperatures of all cases, case after case"""
+    Tw = _f64(Tw)
+    _bcheck(lib().ibm_batch_set_wall_temperature(h, _ptr(Tw)), h)
+
+
 def ibm_batch_forces(h, ncases: int) -> np.ndarray:
     """(ncases, 8) array: Fx, Fy, heat rate, Cd, Cl, Nu, dt, t per case."""
     out = np.zeros((ncases, 8))
@@ -652,6 +659,10 @@ class Batch:
 
     def sync(self):
         ibm_batch_sync(self.h)
+
+    def set_wall_temperature(self, Tw):
+        """wall temperatures of every case's kept markers, concatenated in case order"""
+        ibm_batch_set_wall_temperature(self.h, Tw)
 
     def forces(self) -> np.ndarray:
         return ibm_batch_forces(self.h, len(self.cases))

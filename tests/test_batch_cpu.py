@@ -90,6 +90,7 @@ def test_null_batch_is_an_argument_error(lib):
     assert lib.ibm_batch_sync(None, None) == 1
     assert lib.ibm_batch_destroy(None) == 1
     assert lib.ibm_batch_forces(None, None) == 1
+    assert lib.ibm_batch_set_wall_temperature(None, None) == 1
     assert lib.ibm_batch_autotune(None, 1, None, None) == 1
     assert lib.ibm_batch_set_tuning(None, None) == 1
     assert lib.ibm_batch_get_tuning(None, None) == 1

@@ -148,10 +148,13 @@ def test_backward_fp32_3d_matches_oracle():
 
 
 def test_backward_matches_gpu_finite_differences():
-    """Central differences of the GPU's own J (FP64, the recorded step sizes
-    held fixed).  T_w does not enter the weights, so its differences are
-    clean at 1e-6; a marker shift also moves eps~, whose CG solution carries
-    ~1e-9 relative noise, so X is differenced at 1e-4."""
+    """Central differences (h = 1e-6) of the GPU's own J in FP64 with the
+    recorded step sizes held fixed, on 32 seeded (marker, axis) draws whose
+    shift keeps the marker in its owner cell (so the bins do not change) and
+    16 wall temperatures.  The 32 markers are few enough for the direct
+    (Cholesky) quadrature solve, so eps~ moves smoothly with X and the
+    differences are clean: gate 1e-4 relative, with an absolute floor of 1e-6
+    of the largest entry for entries near zero."""
     g, X, Tw, seed = cylinder(8)
     a, b = 1.0, 0.3
     _, gX, gT, Xk, Twk, U0, dts = gpu_gradient(g, X, Tw, seed, 3, 2, a, b)
@@ -163,25 +166,33 @@ def test_backward_matches_gpu_finite_differences():
         for dt in dts:
             gr.step(1, dt_fixed=dt)
         f = gr.forces()
+        gr.close()
         return a * f["Cd"] + b * f["Nu"]
 
+    lo = np.array(g.lo[:2])
     rng = np.random.default_rng(7)
-    for _ in range(6):
+    d = 1e-6
+    done = 0
+    while done < 32:
         k, ax = int(rng.integers(len(Xk))), int(rng.integers(2))
-        d = 1e-4
+        cell = np.floor((Xk[k, ax] - lo[ax]) / g.h)
+        if (np.floor((Xk[k, ax] + d - lo[ax]) / g.h) != cell or
+                np.floor((Xk[k, ax] - d - lo[ax]) / g.h) != cell):
+            continue
         Xp, Xm = Xk.copy(), Xk.copy()
         Xp[k, ax] += d
         Xm[k, ax] -= d
         fd = (J_of(Xp, Twk) - J_of(Xm, Twk)) / (2 * d)
-        assert abs(gX[k, ax] - fd) <= 2e-3 * np.abs(gX).max(), (k, ax, gX[k, ax], fd)
-    for _ in range(4):
+        assert abs(gX[k, ax] - fd) <= 1e-4 * abs(fd) + 1e-6 * np.abs(gX).max(), \
+            (k, ax, gX[k, ax], fd)
+        done += 1
+    for _ in range(16):
         k = int(rng.integers(len(Xk)))
-        d = 1e-6
         Tp, Tm = Twk.copy(), Twk.copy()
         Tp[k] += d
         Tm[k] -= d
         fd = (J_of(Xk, Tp) - J_of(Xk, Tm)) / (2 * d)
-        assert abs(gT[k] - fd) <= 1e-5 * np.abs(gT).max(), (k, gT[k], fd)
+        assert abs(gT[k] - fd) <= 1e-4 * abs(fd) + 1e-6 * np.abs(gT).max(), (k, gT[k], fd)
 
 
 def test_autograd_function_returns_the_adjoint_gradient():

@@ -258,3 +258,49 @@ def test_batch_errors():
     with pytest.raises(ibm.IbmError) as e:
         b.sync()
     assert e.value.status == 3 and "case 1" in e.value.message
+
+
+def test_batch_wall_temperature_setter_equals_per_case_setter():
+    """ibm_batch_set_wall_temperature (one upload for all cases) leaves every
+    case as ibm_set_wall_temperature on each case would, bit for bit; a bad
+    value anywhere is rejected and changes nothing."""
+    cs = small_batch(4, n=4, seed=11)
+    b = make_batch(cs)
+    loop = make_loop(cs)
+    b.step(2)
+    for gr in loop:
+        gr.step(2)
+    rng = np.random.default_rng(5)
+    new = [rng.uniform(0.6, 1.9, cg.n_kept) for cg in b.cases]
+    b.set_wall_temperature(np.concatenate(new))
+    for gr, t in zip(loop, new):
+        gr.set_wall_temperature(t)
+    b.step(3)
+    for gr in loop:
+        gr.step(3)
+    assert_bitwise(b, loop)
+    bad = np.concatenate(new)
+    bad[-1] = -1.0
+    with pytest.raises(ibm.IbmError) as e:
+        b.set_wall_temperature(bad)
+    assert e.value.status == 1 and "finite and positive" in e.value.message
+    b.step(1)
+    for gr in loop:
+        gr.step(1)
+    assert_bitwise(b, loop)
+
+
+def test_batch_forces_report_the_failing_case():
+    """the error words travel with the gathered force sums: ibm_batch_forces
+    reports a failing case as ibm_batch_sync does"""
+    g2 = C.small_grid(2, (32, 32), h=0.1, fp_bytes=4)
+    U = C.random_state(g2, seed=3)
+    b = ibm.Batch([g2, g2, g2], [0, 0, 0])
+    U2 = U.copy()
+    U2[0, 7, 9] = -1.0
+    for i, Ui in enumerate([U, U, U2]):
+        b.cases[i].set_state(Ui)
+    b.step(1)
+    with pytest.raises(ibm.IbmError) as e:
+        b.forces()
+    assert e.value.status == 3 and "case 2" in e.value.message
