@@ -120,4 +120,19 @@ __device__ __forceinline__ unsigned cell_key(const GridParams &g, int cx, int cy
 
 __device__ __forceinline__ void record_error(int *err, int bits) { atomicOr(err, bits); }
 
+// a - b on both lanes of an FP32 pair in one packed instruction, rounded to
+// nearest, subnormal results flushed (the FP32 stage units are built with
+// flushing on).  Adding the negated pair instead costs two scalar negations.
+__device__ __forceinline__ float2 fsub2_ftz(float2 a, float2 b) {
+    float2 r;
+    asm("{ .reg .b64 pa, pb, pd;\n\t"
+        "mov.b64 pa, {%2, %3};\n\t"
+        "mov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.ftz.f32x2 pd, pa, pb;\n\t"
+        "mov.b64 {%0, %1}, pd; }"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+
 }  // namespace ibmk

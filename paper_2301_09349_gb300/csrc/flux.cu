@@ -200,9 +200,7 @@ __device__ __forceinline__ void face_flux(const FluxK<T> &k, const T *__restrict
 // Both faces run the same arithmetic with their velocities ordered (normal,
 // tangential); every pair operation is one packed FP32x2 instruction.
 __device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 p_sub(float2 a, float2 b) {
-    return __fadd2_rn(a, make_float2(-b.x, -b.y));
-}
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return fsub2_ftz(a, b); }
 __device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 p_s(float s) { return make_float2(s, s); }

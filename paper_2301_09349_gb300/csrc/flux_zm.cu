@@ -73,9 +73,7 @@ FC make_fc(const GridParams &g) { return float_consts(g); }
 // the y-face (v, u, w).  Each pair operation is one packed FP32x2
 // instruction on sm_100-class GPUs.
 __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
-    return __fadd2_rn(a, make_float2(-b.x, -b.y));
-}
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return fsub2_ftz(a, b); }
 __device__ __forceinline__ float2 operator*(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 sp(float s) { return make_float2(s, s); }
