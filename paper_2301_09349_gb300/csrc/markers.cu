@@ -272,8 +272,12 @@ __device__ __forceinline__ void store_forcing(const GridParams &g, const MarkerB
     m.H[k] = rk * g.cv * m.Tw[k] - (double)acc[DIM + 1];
 }
 
+// threads of the staged interpolation (one CTA per occupied tile; 3D tiles
+// hold more markers, served by more warps)
+template <int DIM> constexpr int IF_T = DIM == 3 ? 512 : 256;
+
 template <int DIM, typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(IF_T<DIM>)
 interp_force_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuffers m,
                     const int *__restrict__ perm) {
     using R = T;
@@ -387,7 +391,10 @@ batch_interp_kernel(const BatchCase *__restrict__ cases, const int2 *__restrict_
 // spreading as a cell-centric gather
 // ---------------------------------------------------------------------------
 
-constexpr int SP_T = 256;
+// threads of a spreading CTA (one band tile at a time): a 3D body has a few
+// dozen 8^3 band tiles, whose candidate staging and gathers finish sooner with
+// 512 threads; the many small 2D tiles of a batch run best at 256
+template <int DIM> constexpr int SP_T = DIM == 3 ? 512 : 256;
 constexpr int SP_MAXC = 1024;   // staged candidates per band tile
 
 template <typename R>
@@ -488,7 +495,7 @@ __device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__
     // 2. stage, in order, the markers whose owner cell lies in the tile
     //    grown by one cell (their supports reach the tile)
     int kept = 0;
-    for (int base = 0; base < total; base += SP_T) {
+    for (int base = 0; base < total; base += SP_T<DIM>) {
         const int i = base + tid;
         int keep = 0, p = 0, lc = 0;
         if (i < total) {
@@ -526,9 +533,9 @@ __device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__
     const bool overflow = kept > SP_MAXC;
     // 3. runs of candidates per owner cell (contiguous in bin order)
     if (!overflow) {
-        for (int q = tid; q < bn; q += SP_T) s_head[q] = -1;
+        for (int q = tid; q < bn; q += SP_T<DIM>) s_head[q] = -1;
         __syncthreads();
-        for (int i = tid; i < kept; i += SP_T) {
+        for (int i = tid; i < kept; i += SP_T<DIM>) {
             const int c = s_cell[i];
             if (i == 0 || s_cell[i - 1] != c) {
                 int j = i + 1;
@@ -540,7 +547,7 @@ __device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__
     }
     __syncthreads();
     // 4. gather per cell in the fixed order, then the forced update
-    for (int q = tid; q < cpt; q += SP_T) {
+    for (int q = tid; q < cpt; q += SP_T<DIM>) {
         const int l[3] = {q % g.tile[0], (q / g.tile[0]) % g.tile[1],
                           DIM == 3 ? q / (g.tile[0] * g.tile[1]) : 0};
         const int c[3] = {o[0] + l[0], o[1] + l[1], o[2] + l[2]};
@@ -591,13 +598,13 @@ __device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__
 }
 
 template <int DIM, typename T>
-__global__ void __launch_bounds__(SP_T)
+__global__ void __launch_bounds__(SP_T<DIM>)
 spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m,
                     const unsigned *__restrict__ keys, const int *__restrict__ perm) {
     constexpr int NT3 = DIM == 3 ? 27 : 9;
     extern __shared__ __align__(16) unsigned char smem_sp[];
     __shared__ int s_cnt[NT3 + 1], s_start[NT3], s_warp[33];
-    __shared__ double s_max[SP_T / 32];
+    __shared__ double s_max[SP_T<DIM> / 32];
     const SpreadSmem<T> sm = spread_smem<T>(smem_sp, g, s_cnt, s_start, s_warp);
     const int tid = threadIdx.x;
     const int n_band = m.counts[1];
@@ -612,7 +619,7 @@ spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m
     __syncthreads();
     if (tid == 0) {
         double mx = s_max[0];
-        for (int w = 1; w < SP_T / 32; ++w) mx = fmax(mx, s_max[w]);
+        for (int w = 1; w < SP_T<DIM> / 32; ++w) mx = fmax(mx, s_max[w]);
         m.bandmax[blockIdx.x] = mx;
         if (bad) record_error(m.err, ERR_NONFINITE);
     }
@@ -622,13 +629,13 @@ spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m
 // Batched form: items are (case, position in the case's band list); one
 // step-size maximum per item.
 template <int DIM, typename T>
-__global__ void __launch_bounds__(SP_T)
+__global__ void __launch_bounds__(SP_T<DIM>)
 batch_spread_kernel(const BatchCase *__restrict__ cases, const int2 *__restrict__ items,
                     int n_items, double *__restrict__ band_max) {
     constexpr int NT3 = DIM == 3 ? 27 : 9;
     extern __shared__ __align__(16) unsigned char smem_sp[];
     __shared__ int s_cnt[NT3 + 1], s_start[NT3], s_warp[33];
-    __shared__ double s_max[SP_T / 32];
+    __shared__ double s_max[SP_T<DIM> / 32];
     const int tid = threadIdx.x;
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const int2 w = items[it];
@@ -647,7 +654,7 @@ batch_spread_kernel(const BatchCase *__restrict__ cases, const int2 *__restrict_
         __syncthreads();
         if (tid == 0) {
             double mx = s_max[0];
-            for (int w2 = 1; w2 < SP_T / 32; ++w2) mx = fmax(mx, s_max[w2]);
+            for (int w2 = 1; w2 < SP_T<DIM> / 32; ++w2) mx = fmax(mx, s_max[w2]);
             band_max[it] = mx;
             if (bad) record_error(bc.err, ERR_NONFINITE);
         }
@@ -976,7 +983,7 @@ static cudaError_t interp_force_t(const GridParams &g, const void *U, const Mark
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    interp_force_kernel<DIM, T><<<grid_ctas, 256, smem, s>>>(g, (const T *)U, m, m.perm[m.sorted]);
+    interp_force_kernel<DIM, T><<<grid_ctas, IF_T<DIM>, smem, s>>>(g, (const T *)U, m, m.perm[m.sorted]);
     return cudaGetLastError();
 }
 
@@ -1001,7 +1008,7 @@ static cudaError_t spread_apply_t(const GridParams &g, void *U, const MarkerBuff
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    spread_apply_kernel<DIM, T><<<grid_ctas, SP_T, smem, s>>>(g, (T *)U, m, m.keys[m.sorted],
+    spread_apply_kernel<DIM, T><<<grid_ctas, SP_T<DIM>, smem, s>>>(g, (T *)U, m, m.keys[m.sorted],
                                                                 m.perm[m.sorted]);
     return cudaGetLastError();
 }
@@ -1048,7 +1055,7 @@ static cudaError_t batch_spread_t(size_t smem, const BatchCase *cases, const int
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    batch_spread_kernel<2, T><<<ctas, SP_T, smem, s>>>(cases, items, n_items, band_max);
+    batch_spread_kernel<2, T><<<ctas, SP_T<2>, smem, s>>>(cases, items, n_items, band_max);
     return cudaGetLastError();
 }
 

@@ -317,9 +317,10 @@ def test_deterministic_bitwise():
     assert outs[0][1] == outs[1][1]
 
 
-@pytest.mark.parametrize("mach,Tw", [(0.3, 1.5)])
+@pytest.mark.parametrize("mach,Tw", [(0.3, 1.5), (0.3, 0.5), (2.0, 0.5), (2.0, 1.5)])
 def test_full_size_sphere_one_step(oracle, mach, Tw):
-    """The benchmark workload (256^3, 20000 markers -> dedup) for one step,
+    """The 256^3 sphere in each of its four flow conditions (Mach 0.3 or 2.0,
+    hot or cold wall; the first is the benchmark workload) for one step,
     compared element by element with the oracle."""
     c = C.heated_sphere(n=256, mach=mach, Tw=Tw)
     _compare_run(oracle, c, 1, 1e-5, tol_force=1e-3)
