@@ -8,7 +8,8 @@
 // phi(r_l,d(i)) over the three support columns of k on each axis.  Rows are
 // assembled in ELL form (column-major, one warp per marker, neighbours
 // found through the marker bins in a fixed order).  Up to 160 markers a
-// single CTA factors the dense matrix (Cholesky, FP64); above, a single CTA
+// single CTA factors the dense matrix (Cholesky in FP32, refined to the FP64
+// solution); above, a single CTA
 // runs Jacobi-preconditioned CG in FP64 with fixed-order block reductions.
 // Either way the result is bitwise reproducible; every loop is bounded.
 #include "internal.h"
@@ -209,84 +210,192 @@ pcg_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rh
     }
 }
 
-// Small systems: A~ is assembled dense in shared memory from the ELL rows and
-// factored A~ = L L^T by a right-looking Cholesky (FP64, fixed order, one
-// CTA), then the two triangular solves.  ~ns^3/6 multiply-adds against a
-// few hundred latency-bound CG iterations; the residual max|rhs - A~ x| is
-// checked against tol like the CG's.  A non-positive pivot (A~ not positive
-// definite) records ERR_NOCONV.
+// Small systems: A~ is copied dense, in FP32, into shared memory from the
+// ELL rows.  FP64 runs at a small fraction of the FP32 rate on this GPU, so
+// the O(ns^3) work is done in FP32: a right-looking Cholesky A~ = L L^T and
+// the explicit inverse X = L^-1, each one pass over the columns with one
+// barrier per column.  The FP64 solution then comes from iterative
+// refinement, x += X^T X (rhs - A~ x), with the residual taken in FP64 from
+// the ELL rows (only their nonzeros); it contracts by about cond(A~) times
+// the FP32 rounding per pass and stops when the FP64 residual stops falling
+// (its rounding floor) or reaches zero.  Fixed order throughout, so the
+// result is bitwise reproducible.  max|rhs - A~ x| is checked against tol
+// like the CG's; a non-positive pivot records ERR_NOCONV.
 constexpr int CHOL_T = 512;
+constexpr int CHOL_W = CHOL_T / 32;
 #ifndef IBM_CHOL_MAX
 #define IBM_CHOL_MAX 160
 #endif
-constexpr int CHOL_MAX = IBM_CHOL_MAX;   // (ns^2 + ns) doubles of shared memory
+constexpr int CHOL_MAX = IBM_CHOL_MAX;
+constexpr int CHOL_CC = (CHOL_MAX + 31) / 32;               // 32-wide chunks of a row
+static_assert(CHOL_CC <= 5, "the row updates dispatch on at most 5 chunks");
+constexpr int CHOL_REFINE_MAX = 40;
+
+// x [ns] in FP64, then the FP32 factors [ns][ns | 1], 1/L_jj, r and t
+size_t chol_smem(int ns) {
+    return sizeof(double) * (size_t)ns + sizeof(float) * ((size_t)ns * (ns | 1) + 3 * (size_t)ns);
+}
+
+// row i of the inverse's step j: F[c][i] = (F[c][i] - li X_jc) sc for c <= j
+// over NCH 32-wide chunks, all loads before the stores
+template <int NCH>
+__device__ __forceinline__ void inv_row(float *__restrict__ F, int ld, int i, int j, float li,
+                                        float sc, const float (&xj)[CHOL_CC], int lane) {
+    float v[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        const int cc = 32 * c + lane;
+        if (cc <= j) v[c] = F[cc * ld + i];
+    }
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        const int cc = 32 * c + lane;
+        if (cc <= j) F[cc * ld + i] = (v[c] - li * xj[c]) * sc;
+    }
+}
 
 __global__ void __launch_bounds__(CHOL_T)
 chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rhs, double tol,
-            int *err) {
-    extern __shared__ __align__(16) double sA[];   // [ns][ns] row-major, then b[ns]
-    double *b = sA + (size_t)ns * ns;
+            int warm, int *err) {
+    // rows have an odd stride, so a warp walking a column (consecutive rows)
+    // or threads walking their own rows hit distinct banks
+    const int ld = ns | 1;
+    extern __shared__ __align__(16) double sD[];
+    double *sx = sD;                                 // [ns] solution
+    float *F = reinterpret_cast<float *>(sx + ns);   // [ns][ld]: L on and below the diagonal,
+                                                     // X = L^-1 transposed above it
+    float *dinv = F + (size_t)ns * ld;               // [ns] 1 / L_jj, the diagonal of X
+    float *r32 = dinv + ns;                          // [ns] residual in FP32
+    float *st = r32 + ns;                            // [ns] X r
     __shared__ double s_red[CHOL_T / 32];
     __shared__ int s_bad;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < ns * ns; i += CHOL_T) sA[i] = 0.0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < ns * ld; i += CHOL_T) F[i] = 0.0f;
     if (tid == 0) s_bad = 0;
     __syncthreads();
+    // lower triangle of A~ (the upper triangle stays zero)
     for (int k = tid; k < ns; k += CHOL_T) {
         const int c = q.cnt[k];
-        for (int i = 0; i < c; ++i)
-            sA[(size_t)k * ns + q.col[(long long)i * q.cap + k]] = q.val[(long long)i * q.cap + k];
-        b[k] = rhs ? rhs[k] : 1.0;
+        for (int i = 0; i < c; ++i) {
+            const int l = q.col[(long long)i * q.cap + k];
+            if (l <= k) F[(size_t)k * ld + l] = (float)q.val[(long long)i * q.cap + k];
+        }
+        sx[k] = warm ? x[k] : 0.0;
     }
     __syncthreads();
-    // factor: column j of L, then the trailing lower triangle
+    // factor with unscaled columns: step j subtracts a_ij a_kj / a_jj from the
+    // trailing lower triangle and leaves column j as it is, so each column
+    // costs one barrier; the columns are scaled by 1/sqrt(a_jj) at the end.
+    // One warp per row, lanes along the row; a row's operands are all loaded
+    // before its stores.
     for (int j = 0; j < ns; ++j) {
-        if (tid == 0) {
-            const double d = sA[(size_t)j * ns + j];
-            if (!(d > 0.0)) s_bad = 1;
-            sA[(size_t)j * ns + j] = d > 0.0 ? sqrt(d) : 1.0;
+        const float d = F[j * ld + j];
+        const float invd = d > 0.0f ? 1.0f / d : 0.0f;
+        if (tid == 0 && !(d > 0.0f)) s_bad = 1;
+        for (int i = j + 1 + warp; i < ns; i += CHOL_W) {
+            float *row = F + i * ld;
+            const float ci = row[j] * invd;
+            float a[CHOL_CC], b[CHOL_CC];
+#pragma unroll
+            for (int c = 0; c < CHOL_CC; ++c) {
+                const int kk = j + 1 + 32 * c + lane;
+                if (kk <= i) {
+                    a[c] = row[kk];
+                    b[c] = F[kk * ld + j];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < CHOL_CC; ++c) {
+                const int kk = j + 1 + 32 * c + lane;
+                if (kk <= i) row[kk] = a[c] - ci * b[c];
+            }
         }
         __syncthreads();
-        const double inv = 1.0 / sA[(size_t)j * ns + j];
-        for (int i = j + 1 + tid; i < ns; i += CHOL_T) sA[(size_t)i * ns + j] *= inv;
-        __syncthreads();
-        // trailing lower triangle: one warp per row, lanes along the row
-        for (int i = j + 1 + (tid >> 5); i < ns; i += CHOL_T / 32) {
-            const double lij = sA[(size_t)i * ns + j];
-            for (int kk = j + 1 + (tid & 31); kk <= i; kk += 32)
-                sA[(size_t)i * ns + kk] -= lij * sA[(size_t)kk * ns + j];
-        }
-        __syncthreads();
     }
-    // L y = b (forward), L^T x = y (backward), one unknown per step
-    for (int j = 0; j < ns; ++j) {
-        if (tid == 0) b[j] /= sA[(size_t)j * ns + j];
-        __syncthreads();
-        const double yj = b[j];
-        for (int i = j + 1 + tid; i < ns; i += CHOL_T) b[i] -= sA[(size_t)i * ns + j] * yj;
-        __syncthreads();
+    for (int j = tid; j < ns; j += CHOL_T) {
+        const float d = F[(size_t)j * ld + j];
+        dinv[j] = d > 0.0f ? 1.0f / sqrtf(d) : 1.0f;
     }
-    for (int j = ns - 1; j >= 0; --j) {
-        if (tid == 0) b[j] /= sA[(size_t)j * ns + j];
-        __syncthreads();
-        const double xj = b[j];
-        for (int i = tid; i < j; i += CHOL_T) b[i] -= sA[(size_t)j * ns + i] * xj;
-        __syncthreads();
-    }
-    for (int k = tid; k < ns; k += CHOL_T) x[k] = b[k];
     __syncthreads();
-    // true residual with the ELL matrix
-    double lm = 0.0;
-    for (int k = tid; k < ns; k += CHOL_T) {
-        const int c = q.cnt[k];
-        double sum = 0.0;
-        for (int i = 0; i < c; ++i)
-            sum += q.val[(long long)i * q.cap + k] * x[q.col[(long long)i * q.cap + k]];
-        lm = fmax(lm, fabs((rhs ? rhs[k] : 1.0) - sum));
+    for (int i = tid; i < ns * ld; i += CHOL_T) {
+        const int r = i / ld, c = i - r * ld;
+        if (c < r) F[i] *= dinv[c];
     }
-    const double rmax = block_max<CHOL_T>(lm, s_red);
+    __syncthreads();
+    // X = L^-1, right-looking: once row j of X is final, rows i > j take
+    // -L_ij X_jc (c <= j); row j+1 is then complete and is scaled by
+    // 1/L_{j+1,j+1}.  X_ic (c < i) lives at F[c][i]; X_jj = dinv[j].  One
+    // warp per row, lanes along c; row j of X is read once per step.
+    for (int j = 0; j + 1 < ns; ++j) {
+        float xj[CHOL_CC];
+#pragma unroll
+        for (int c = 0; c < CHOL_CC; ++c) {
+            const int cc = 32 * c + lane;
+            xj[c] = cc < j ? F[(size_t)cc * ld + j] : (cc == j ? dinv[j] : 0.0f);
+        }
+        const int nch = j >> 5;   // live chunks - 1, the same for every row of the step
+        for (int i = j + 1 + warp; i < ns; i += CHOL_W) {
+            const float li = F[i * ld + j];
+            const float sc = i == j + 1 ? dinv[i] : 1.0f;
+            switch (nch) {
+                case 0: inv_row<1>(F, ld, i, j, li, sc, xj, lane); break;
+                case 1: inv_row<2>(F, ld, i, j, li, sc, xj, lane); break;
+                case 2: inv_row<3>(F, ld, i, j, li, sc, xj, lane); break;
+                case 3: inv_row<4>(F, ld, i, j, li, sc, xj, lane); break;
+                default: inv_row<5>(F, ld, i, j, li, sc, xj, lane); break;
+            }
+        }
+        __syncthreads();
+    }
+    // refinement: r = rhs - A~ x in FP64 from the ELL rows (one thread per
+    // row), x += X^T X r in FP32
+    double rmax = 0.0, rprev = 0.0;
+    int it = 0;
+    for (;; ++it) {
+        double lm = 0.0;
+        for (int k = tid; k < ns; k += CHOL_T) {
+            const int c = q.cnt[k];
+            double sum = 0.0;
+            for (int i = 0; i < c; ++i)
+                sum += q.val[(long long)i * q.cap + k] * sx[q.col[(long long)i * q.cap + k]];
+            const double r = (rhs ? rhs[k] : 1.0) - sum;
+            r32[k] = (float)r;
+            lm = fmax(lm, fabs(r));
+        }
+        rmax = block_max<CHOL_T>(lm, s_red);   // synchronizes
+        if (!(rmax > 0.0) || (it > 0 && !(rmax < 0.5 * rprev)) || it == CHOL_REFINE_MAX) break;
+        rprev = rmax;
+        for (int i = tid; i < ns; i += CHOL_T) {
+            float s0 = dinv[i] * r32[i], s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+            int c = 0;
+            for (; c + 4 <= i; c += 4) {
+                s0 += F[(size_t)c * ld + i] * r32[c];
+                s1 += F[(size_t)(c + 1) * ld + i] * r32[c + 1];
+                s2 += F[(size_t)(c + 2) * ld + i] * r32[c + 2];
+                s3 += F[(size_t)(c + 3) * ld + i] * r32[c + 3];
+            }
+            for (; c < i; ++c) s0 += F[(size_t)c * ld + i] * r32[c];
+            st[i] = (s0 + s1) + (s2 + s3);
+        }
+        __syncthreads();
+        for (int c = tid; c < ns; c += CHOL_T) {
+            const float *row = F + (size_t)c * ld;
+            float s0 = dinv[c] * st[c], s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+            int i = c + 1;
+            for (; i + 4 <= ns; i += 4) {
+                s0 += row[i] * st[i];
+                s1 += row[i + 1] * st[i + 1];
+                s2 += row[i + 2] * st[i + 2];
+                s3 += row[i + 3] * st[i + 3];
+            }
+            for (; i < ns; ++i) s0 += row[i] * st[i];
+            sx[c] += (double)((s0 + s1) + (s2 + s3));
+        }
+        __syncthreads();
+    }
+    for (int k = tid; k < ns; k += CHOL_T) x[k] = sx[k];
     if (tid == 0) {
-        *q.iters = 0;
+        *q.iters = it;
         *q.resid = rmax;
         if (s_bad || !(rmax <= tol)) record_error(err, ERR_NOCONV);
     }
@@ -296,23 +405,22 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
 
 int quad_row_width(int dim) { return dim == 3 ? 125 * 4 : 25 * 4; }
 
-// A~ x = rhs (rhs == nullptr: all ones): dense Cholesky up to CHOL_MAX
-// markers, Jacobi-PCG (warm start if asked) above
+// A~ x = rhs (rhs == nullptr: all ones): dense Cholesky with refinement up
+// to CHOL_MAX markers, Jacobi-PCG above (either warm-started if asked)
 static cudaError_t launch_quadrature_solve_w(int ns, const QuadBuffers &qb, const double *rhs,
                                             double *x, double tol, int maxit, int warm, int *err,
                                             cudaStream_t s) {
     if (ns <= 0) return cudaSuccess;
     if (ns <= CHOL_MAX) {
-        const size_t smem = sizeof(double) * ((size_t)ns * ns + ns);
         static bool configured = false;
         if (!configured) {
-            cudaError_t e = cudaFuncSetAttribute(
-                chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                (int)(sizeof(double) * ((size_t)CHOL_MAX * CHOL_MAX + CHOL_MAX)));
+            cudaError_t e = cudaFuncSetAttribute(chol_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)chol_smem(CHOL_MAX));
             if (e != cudaSuccess) return e;
             configured = true;
         }
-        chol_kernel<<<1, CHOL_T, smem, s>>>(ns, qb, x, rhs, tol, err);
+        chol_kernel<<<1, CHOL_T, chol_smem(ns), s>>>(ns, qb, x, rhs, tol, warm, err);
     } else if (ns <= 2048) {
         pcg_kernel<256><<<1, 256, 0, s>>>(ns, qb, x, rhs, tol, maxit, warm, err);
     } else {
