@@ -17,6 +17,8 @@
 // accumulates the flux differences in registers.
 #include <float.h>
 
+#include <type_traits>
+
 #include "internal.h"
 
 // the pair tiles leave some of BoxT's stride constants unused
@@ -59,6 +61,16 @@ template <> struct DefaultBox<3, double> { using type = BoxT<3, double, 8, 8, 4>
 template <> struct DefaultBox<2, float> { using type = BoxT<2, float, 16, 16, 1>; };
 template <> struct DefaultBox<2, double> { using type = BoxT<2, double, 16, 16, 1>; };
 template <int DIM, typename T> using Box = typename DefaultBox<DIM, T>::type;
+
+// Small 2D FP64 grids: FP64 arithmetic runs at a small fraction of the FP32
+// rate on this GPU, so the stage time of a grid with few 16 x 16 tiles is set
+// by how many SMs take part; 8 x 8 tiles spread it over four times as many.
+using SmallBox2D = BoxT<2, double, 8, 8, 1>;
+inline bool small_2d_fp64(const GridParams &g) {
+    return g.dim == 2 && (long long)((g.n[0] + 15) / 16) * ((g.n[1] + 15) / 16) < 256;
+}
+template <int DIM, typename T, bool SMALL>
+using StageBox = typename std::conditional<SMALL, SmallBox2D, Box<DIM, T>>::type;
 
 // 2D tile shapes of the batched kernel (all 256 cells): the autotuner's
 // choices.  Every face is evaluated by the same arithmetic whatever the
@@ -524,12 +536,12 @@ __device__ __forceinline__ double stage_tile(const GridParams &g, int ox, int oy
     return 0.0;
 }
 
-template <int DIM, typename T, int MODE>
+template <int DIM, typename T, int MODE, bool SMALL>
 __global__ void __launch_bounds__(NT)
 stage_kernel(const GridParams g, const T *__restrict__ Uin, const T *__restrict__ Un,
              T *__restrict__ out, double *__restrict__ blockmax, const double *__restrict__ dt_ptr,
              int *__restrict__ err, const unsigned *__restrict__ band_bits, double dt_fixed) {
-    using B = Box<DIM, T>;
+    using B = StageBox<DIM, T, SMALL>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double s_red[NT / 32];
     const int ox = blockIdx.x * B::BX, oy = blockIdx.y * B::BY;
@@ -628,29 +640,37 @@ dt_init_kernel(const GridParams g, const T *__restrict__ U, double *__restrict__
     }
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, bool SMALL = false>
 dim3 stage_grid(const GridParams &g) {
-    using B = Box<DIM, T>;
+    using B = StageBox<DIM, T, SMALL>;
     return dim3((g.n[0] + B::BX - 1) / B::BX, (g.n[1] + B::BY - 1) / B::BY,
                 DIM == 3 ? (g.n[2] + B::BZ - 1) / B::BZ : 1);
 }
 
-template <int DIM, typename T, int MODE>
-cudaError_t launch_one(const GridParams &g, const void *Uin, const void *Un, void *out,
+template <int DIM, typename T, int MODE, bool SMALL>
+cudaError_t launch_box(const GridParams &g, const void *Uin, const void *Un, void *out,
                        const FluidBuffers &fb, double dt_fixed, cudaStream_t s) {
-    using B = Box<DIM, T>;
+    using B = StageBox<DIM, T, SMALL>;
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(stage_kernel<DIM, T, MODE>,
+        cudaError_t e = cudaFuncSetAttribute(stage_kernel<DIM, T, MODE, SMALL>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)B::SMEM);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    stage_kernel<DIM, T, MODE><<<stage_grid<DIM, T>(g), NT, B::SMEM, s>>>(
+    stage_kernel<DIM, T, MODE, SMALL><<<stage_grid<DIM, T, SMALL>(g), NT, B::SMEM, s>>>(
         g, (const T *)Uin, (const T *)Un, (T *)out, fb.blockmax, fb.dt, fb.err, fb.band_bits,
         dt_fixed);
     return cudaGetLastError();
+}
+
+template <int DIM, typename T, int MODE>
+cudaError_t launch_one(const GridParams &g, const void *Uin, const void *Un, void *out,
+                       const FluidBuffers &fb, double dt_fixed, cudaStream_t s) {
+    if (DIM == 2 && sizeof(T) == 8 && small_2d_fp64(g))
+        return launch_box<DIM, T, MODE, DIM == 2 && sizeof(T) == 8>(g, Uin, Un, out, fb, dt_fixed, s);
+    return launch_box<DIM, T, MODE, false>(g, Uin, Un, out, fb, dt_fixed, s);
 }
 
 template <int MODE>
@@ -726,7 +746,8 @@ size_t fluid_stage_blocks(const GridParams &g, int fp_bytes) {
     dim3 d;
     if (g.dim == 3 && fp_bytes == 4) return zmarch_blocks(g);
     if (g.dim == 3) d = stage_grid<3, double>(g);
-    else d = fp_bytes == 4 ? stage_grid<2, float>(g) : stage_grid<2, double>(g);
+    else if (fp_bytes == 4) d = stage_grid<2, float>(g);
+    else d = small_2d_fp64(g) ? stage_grid<2, double, true>(g) : stage_grid<2, double>(g);
     return (size_t)d.x * d.y * d.z;
 }
 

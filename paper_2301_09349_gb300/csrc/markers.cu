@@ -721,7 +721,7 @@ band_refine_kernel(const GridParams g, const MarkerBuffers m) {
 // forces/heat sums (fixed-order reduction) and the time update
 // ---------------------------------------------------------------------------
 
-constexpr int FIN_T = 1024;
+constexpr int FIN_T = 256;
 
 // One CTA of FIN_T threads: the force/heat sums of one grid, its time
 // update and its next step size from the stage-2 maxima (blockmax[0..nb))
@@ -751,15 +751,22 @@ __device__ __forceinline__ void finish_grid(const GridParams &g, int ns, const M
     if (lane == 0)
         for (int i = 0; i < 5; ++i) s[i][w] = a[i];
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (w != 0) return;
+    // warp 0 combines the warp partials as a fixed tree
+#pragma unroll
+    for (int i = 0; i < 5; ++i) a[i] = lane < FIN_T / 32 ? s[i][lane] : 0.0;
+#pragma unroll
+    for (int o = FIN_T / 64; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
+        a[4] = fmax(a[4], __shfl_xor_sync(0xffffffffu, a[4], o));
+    }
+    if (lane == 0) {
         for (int i = 0; i < 4; ++i) {
-            double t = 0.0;
-            for (int j = 0; j < FIN_T / 32; ++j) t += s[i][j];
             // forcing per stage: the first stage's sources count with weight 1/2
-            m.sums[i] = g.forcing_per_stage ? t + 0.5 * m.sums[8 + i] : t;
+            m.sums[i] = g.forcing_per_stage ? a[i] + 0.5 * m.sums[8 + i] : a[i];
         }
-        double mx = s[4][0];
-        for (int j = 1; j < FIN_T / 32; ++j) mx = fmax(mx, s[4][j]);
+        const double mx = a[4];
         const double dt_used = dt_fixed > 0.0 ? dt_fixed : *dt_ptr;
         m.sums[4] = dt_used;
         *m.t += dt_used;
@@ -791,12 +798,15 @@ partial_sums_kernel(const GridParams g, const MarkerBuffers m) {
     if (lane == 0)
         for (int i = 0; i < 4; ++i) s[i][w] = a[i];
     __syncthreads();
-    if (threadIdx.x == 0)
-        for (int i = 0; i < 4; ++i) {
-            double t = 0.0;
-            for (int j = 0; j < FIN_T / 32; ++j) t += s[i][j];
-            m.sums[8 + i] = t;
-        }
+    if (w != 0) return;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = lane < FIN_T / 32 ? s[i][lane] : 0.0;
+#pragma unroll
+    for (int o = FIN_T / 64; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
+    if (lane == 0)
+        for (int i = 0; i < 4; ++i) m.sums[8 + i] = a[i];
 }
 
 __global__ void __launch_bounds__(FIN_T)
