@@ -512,18 +512,20 @@ adj_prim_kernel(const GridParams g, const T *__restrict__ U, T *__restrict__ lam
     const AdjK<R> k(g);
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N;
          j += (long long)gridDim.x * blockDim.x) {
-        const R rho = U[j], inv = R(1) / rho;
+        // all of a cell's loads are issued before its stores
+        R uc[DIM + 1], wbv[NC];
+#pragma unroll
+        for (int q = 0; q <= DIM; ++q) uc[q] = __ldg(U + q * N + j);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) wbv[q] = lamW[q * N + j];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) lamW[q * N + j] = R(0);
+        const R rho = uc[0], inv = R(1) / rho;
         R v[DIM], ke = R(0);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            v[d] = U[(1 + d) * N + j] * inv;
+            v[d] = uc[1 + d] * inv;
             ke += v[d] * v[d];
-        }
-        R wbv[NC];
-#pragma unroll
-        for (int q = 0; q < NC; ++q) {
-            wbv[q] = lamW[q * N + j];
-            lamW[q * N + j] = R(0);
         }
         const R pb = wbv[NC - 1] * k.gm1;
         R rb = wbv[0] + pb * R(0.5) * ke;
@@ -550,24 +552,48 @@ __global__ void adj_combine_kernel(long long M, int mode, double dt_d, T *__rest
     }
 }
 
-// visit every band cell of the grid: fn(c, j)
+// One warp per band cell (cells of the band tiles in order, warps strided
+// over the grid); fn(c, j, lane) runs on every lane of the warp.
 template <int DIM, typename F>
-__device__ __forceinline__ void for_band_cells(const GridParams &g, const MarkerBuffers &m, F &&fn) {
-    const int n_band = m.counts[1];
-    for (int it = blockIdx.x; it < n_band; it += gridDim.x) {
-        const int t = m.band_list[it];
+__device__ __forceinline__ void for_band_cells_warp(const GridParams &g, const MarkerBuffers &m,
+                                                    F &&fn) {
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const long long nw = (long long)gridDim.x * wpb;
+    const long long total = (long long)m.counts[1] * g.cells_per_tile;
+    for (long long it = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); it < total; it += nw) {
+        const int t = m.band_list[it / g.cells_per_tile];
+        const int q = (int)(it % g.cells_per_tile);
         const int tx = t % g.ntile[0], ty = (t / g.ntile[0]) % g.ntile[1],
                   tz = t / (g.ntile[0] * g.ntile[1]);
-        for (int q = threadIdx.x; q < g.cells_per_tile; q += blockDim.x) {
-            const int c[3] = {tx * g.tile[0] + q % g.tile[0],
-                              ty * g.tile[1] + (q / g.tile[0]) % g.tile[1],
-                              DIM == 3 ? tz * g.tile[2] + q / (g.tile[0] * g.tile[1]) : 0};
-            if (c[0] >= g.n[0] || c[1] >= g.n[1] || (DIM == 3 && c[2] >= g.n[2])) continue;
-            const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
-            if (!((m.band_bits[j >> 5] >> (j & 31)) & 1u)) continue;
-            fn(c, j);
-        }
+        const int c[3] = {tx * g.tile[0] + q % g.tile[0],
+                          ty * g.tile[1] + (q / g.tile[0]) % g.tile[1],
+                          DIM == 3 ? tz * g.tile[2] + q / (g.tile[0] * g.tile[1]) : 0};
+        if (c[0] >= g.n[0] || c[1] >= g.n[1] || (DIM == 3 && c[2] >= g.n[2])) continue;
+        const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+        if (!((m.band_bits[j >> 5] >> (j & 31)) & 1u)) continue;
+        fn(c, j, lane);
     }
+}
+
+// Lane n < 3^DIM visits the markers owned by neighbour n of c (the order of
+// gather_markers: z, y, x offsets ascending); the warp then sums the lanes'
+// partials with warp_sum_d, a fixed tree.
+template <int DIM, typename F>
+__device__ __forceinline__ void gather_markers_lane(const GridParams &g, const MarkerBuffers &m,
+                                                    const unsigned *__restrict__ keys,
+                                                    const int *__restrict__ perm, const int c[3],
+                                                    int lane, F &&visit) {
+    constexpr int NT3 = DIM == 3 ? 27 : 9;
+    if (lane >= NT3) return;
+    gather_cell<DIM, double>(g, m, keys, perm, c, lane % 3 - 1, (lane / 3) % 3 - 1,
+                             DIM == 3 ? lane / 9 - 1 : 0, visit);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
 // 1. reverse of the forced update at the band cells: lam (adjoint of
@@ -578,16 +604,20 @@ adj_apply_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__re
                  const int *__restrict__ perm, const T *__restrict__ Us, T *__restrict__ lam,
                  T *__restrict__ lfq) {
     const long long N = g.N;
-    for_band_cells<DIM>(g, m, [&](const int *c, long long j) {
+    for_band_cells_warp<DIM>(g, m, [&](const int *c, long long j, int lane) {
         double f[DIM], q = 0.0;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) f[d] = 0.0;
-        gather_markers<DIM, double>(g, m, keys, perm, c, [&](int kk, double w) {
+        gather_markers_lane<DIM>(g, m, keys, perm, c, lane, [&](int kk, double w) {
             const double e = m.eps[kk];
 #pragma unroll
             for (int d = 0; d < DIM; ++d) f[d] += m.G[(long long)kk * DIM + d] * e * w;
             q += m.H[kk] * e * w;
         });
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) f[d] = warp_sum_d(f[d]);
+        q = warp_sum_d(q);
+        if (lane != 0) return;
         const double rho = (double)Us[j];
         const double lE = (double)lam[(DIM + 1) * N + j];
         double m0sq = 0.0, m1sq = 0.0;
@@ -650,12 +680,6 @@ __device__ __forceinline__ double lane_weight_grad(const GridParams &g, const Ma
     }
     j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
     return w;
-}
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 // 2.-3. one warp per marker: spreading and forcing reversed, the X parts of
@@ -750,17 +774,22 @@ adj_interp_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__r
                   const int *__restrict__ perm, const AdjBuffers a, const T *__restrict__ Us,
                   T *__restrict__ lam) {
     const long long N = g.N;
-    for_band_cells<DIM>(g, m, [&](const int *c, long long j) {
+    for_band_cells_warp<DIM>(g, m, [&](const int *c, long long j, int lane) {
         double sr = 0.0, sm[DIM], se = 0.0;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) sm[d] = 0.0;
-        gather_markers<DIM, double>(g, m, keys, perm, c, [&](int kk, double w) {
+        gather_markers_lane<DIM>(g, m, keys, perm, c, lane, [&](int kk, double w) {
             const double *mr = a.mr + (long long)kk * 5;
             sr += w * mr[0];
 #pragma unroll
             for (int d = 0; d < DIM; ++d) sm[d] += w * mr[1 + d];
             se += w * mr[4];
         });
+        sr = warp_sum_d(sr);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) sm[d] = warp_sum_d(sm[d]);
+        se = warp_sum_d(se);
+        if (lane != 0) return;
         const double rho = (double)Us[j];
         double msq = 0.0;
 #pragma unroll
@@ -780,12 +809,15 @@ __global__ void __launch_bounds__(AT)
 adj_eps_fields_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__restrict__ keys,
                       const int *__restrict__ perm, const AdjBuffers a) {
     const long long N = g.N;
-    for_band_cells<DIM>(g, m, [&](const int *c, long long j) {
+    for_band_cells_warp<DIM>(g, m, [&](const int *c, long long j, int lane) {
         double se = 0.0, sz = 0.0;
-        gather_markers<DIM, double>(g, m, keys, perm, c, [&](int kk, double w) {
+        gather_markers_lane<DIM>(g, m, keys, perm, c, lane, [&](int kk, double w) {
             se += w * m.eps[kk];
             sz += w * a.z[kk];
         });
+        se = warp_sum_d(se);
+        sz = warp_sum_d(sz);
+        if (lane != 0) return;
         double *w = (double *)a.lamW;   // FP64 scratch here
         w[j] = se;
         w[N + j] = sz;

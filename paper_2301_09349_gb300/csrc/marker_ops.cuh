@@ -62,6 +62,38 @@ __device__ __forceinline__ R lane_weight(const R *fr, const int *ck, int l, int 
     return w;
 }
 
+// Visit, in sorted bin order (ascending marker index), the markers owned by
+// the neighbour (c + (ox, oy, oz)) of cell c.  Global-memory form.
+template <int DIM, typename R, typename F>
+__device__ __forceinline__ bool gather_cell(const GridParams &g, const MarkerBuffers &m,
+                                            const unsigned *__restrict__ keys,
+                                            const int *__restrict__ perm, const int c[3], int ox,
+                                            int oy, int oz, F &&visit) {
+    const int x = c[0] + ox, y = c[1] + oy, z = c[2] + oz;
+    if (x < 0 || y < 0 || x >= g.n[0] || y >= g.n[1]) return false;
+    if (DIM == 3 && (z < 0 || z >= g.n[2])) return false;
+    const unsigned key = cell_key(g, x, y, z);
+    const int tc = (int)(key / (unsigned)g.cells_per_tile);
+    int lo = m.tile_off[tc], hi = m.tile_off[tc + 1];
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (keys[mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    const int end = m.tile_off[tc + 1];
+    const int oo[3] = {-ox, -oy, -oz};   // cell c seen from owner cell (x, y, z)
+    bool any = false;
+    for (int p = lo; p < end && keys[p] == key; ++p) {
+        const int k = perm[p];
+        R w = R(1);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) w *= phi_r<R>(cell_offset<R>(oo[d], marker_frac<R>(m, k, d)));
+        visit(k, w);
+        any = true;
+    }
+    return any;
+}
+
 // Visit, in a fixed order, every marker whose support contains cell c:
 // neighbour owner cells (z, y, x offsets ascending), then sorted bin order
 // (ascending marker index within a cell).  Global-memory form.
@@ -74,29 +106,8 @@ __device__ __forceinline__ bool gather_markers(const GridParams &g, const Marker
     const int zr = DIM == 3 ? 1 : 0;
     for (int oz = -zr; oz <= zr; ++oz)
         for (int oy = -1; oy <= 1; ++oy)
-            for (int ox = -1; ox <= 1; ++ox) {
-                const int x = c[0] + ox, y = c[1] + oy, z = c[2] + oz;
-                if (x < 0 || y < 0 || x >= g.n[0] || y >= g.n[1]) continue;
-                if (DIM == 3 && (z < 0 || z >= g.n[2])) continue;
-                const unsigned key = cell_key(g, x, y, z);
-                const int tc = (int)(key / (unsigned)g.cells_per_tile);
-                int lo = m.tile_off[tc], hi = m.tile_off[tc + 1];
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    if (keys[mid] < key) lo = mid + 1;
-                    else hi = mid;
-                }
-                const int end = m.tile_off[tc + 1];
-                const int oo[3] = {-ox, -oy, -oz};   // cell c seen from owner cell (x, y, z)
-                for (int p = lo; p < end && keys[p] == key; ++p) {
-                    const int k = perm[p];
-                    R w = R(1);
-#pragma unroll
-                    for (int d = 0; d < DIM; ++d) w *= phi_r<R>(cell_offset<R>(oo[d], marker_frac<R>(m, k, d)));
-                    visit(k, w);
-                    any = true;
-                }
-            }
+            for (int ox = -1; ox <= 1; ++ox)
+                any |= gather_cell<DIM, R>(g, m, keys, perm, c, ox, oy, oz, visit);
     return any;
 }
 
