@@ -393,3 +393,30 @@ def test_errors_are_reported():
     with pytest.raises(ibm.IbmError) as e:
         grid.sync()
     assert e.value.status == 3
+
+
+@pytest.mark.parametrize("dim,n", [(2, 1), (2, 37), (2, 97), (2, 160), (2, 161), (3, 160), (3, 161)])
+def test_quadrature_around_the_dense_solver_limit(oracle, dim, n):
+    """Weights from the dense FP32 factorization refined in FP64 (up to 160
+    markers) and from the PCG (above) against the oracle's CG: markers one
+    cell apart along a line with sub-cell jitter, so neighbouring supports
+    overlap as on a body surface."""
+    rng = np.random.default_rng(100 + n)
+    nx = n + 8
+    if dim == 2:
+        g = C.small_grid(2, (nx, 16), h=0.1, fp_bytes=4)
+    else:
+        g = C.small_grid(3, (nx, 8, 8), h=0.1, fp_bytes=4)
+    lo = np.array(g.lo[:dim])
+    cells = np.zeros((n, dim))
+    cells[:, 0] = 4 + np.arange(n)
+    cells[:, 1:] = 4
+    X = lo + (cells + 0.5 + rng.uniform(-0.3, 0.3, (n, dim))) * g.h
+    grid = ibm.Grid(g, max_markers=n)
+    nk = grid.set_markers(X, np.ones(n), dedup=False)
+    assert nk == n
+    _, eps, idx = grid.markers()
+    rc, eo, it, res = oracle.quadrature(g, X[idx])
+    assert rc == 0
+    assert np.max(np.abs(eps - eo) / np.abs(eo)) < 1e-9
+    grid.close()
