@@ -329,7 +329,16 @@ __device__ __forceinline__ void face_vjp(const AdjK<R> &k, const R (&w)[4][DIM +
     }
 }
 
-constexpr int FT = 128;   // flux-reverse CTA: ~150 live registers per face
+// flux-reverse CTA: 256 threads, three per SM (80 registers, a few bytes of
+// spill; 69 KB of shared memory each); measured faster than 128 x 3 (115
+// registers) and 256 x 2 on the 128^3 adjoint
+#ifndef IBM_ADJ_FT
+#define IBM_ADJ_FT 256
+#endif
+#ifndef IBM_ADJ_FT_MIN
+#define IBM_ADJ_FT_MIN 3
+#endif
+constexpr int FT = IBM_ADJ_FT;
 
 // ---- tiled form: one CTA per tile of cells -------------------------------
 // The CTA stages the primitives of its tile plus a two-cell halo (ghosts
@@ -448,7 +457,7 @@ __device__ __forceinline__ void tile_faces(const GridParams &g, const AdjK<T> &k
 }
 
 template <int DIM, typename T>
-__global__ void __launch_bounds__(FT, 3)
+__global__ void __launch_bounds__(FT, IBM_ADJ_FT_MIN)
 adj_flux_tile_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ V,
                      T *__restrict__ lamW) {
     using B = AdjBox<DIM, T>;
