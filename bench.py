@@ -701,6 +701,30 @@ def run_cylinders(args, rank, world, local):
                        "split_us_per_step": res["split_us_per_step"],
                        "launch_overhead_us_per_step": res["direct"] - res["graphs"]}
     osc = out[C.oscillating_cylinder().name]
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        # the oracle on the host cores, whole grids: the heated cylinder for
+        # its 200 configured steps, the oscillating cylinder for 50 steps
+        from oracle import oracle as O
+        O.build()
+        threads = os.cpu_count() or 1
+        O.set_threads(threads)
+        for c, nsteps in ((C.heated_cylinder(), 200), (C.oscillating_cylinder(), 50)):
+            U = C.initial_state(c.grid, c.seed).astype(
+                np.float32 if c.grid.fp_bytes == 4 else np.float64).astype(np.float64)
+            run = O.Run(c.grid, c.X, c.Tw, motion=c.motion)
+            t0 = time.perf_counter()
+            for _ in range(nsteps):
+                U = run.step(U)
+            el = time.perf_counter() - t0
+            out[c.name]["oracle"] = {"cell_updates_per_s": c.grid.ncells * nsteps / el,
+                                     "us_per_step": 1e6 * el / nsteps, "steps": nsteps,
+                                     "cores": threads}
+        o = out[C.oscillating_cylinder().name]["oracle"]
+        cpu = {"value": o["cell_updates_per_s"], "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": "whole 1024x512 oscillating-cylinder grid, 50 steps (markers moved, "
+                         "quadrature re-solved every step); the heated cylinder's 200 steps "
+                         "are in cases"}
     line = {
         "metric": CYL_METRIC, "value": osc["cells"] * 1e6 / osc["us_per_step_graphs"],
         "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -712,6 +736,8 @@ def run_cylinders(args, rank, world, local):
                    "l2": "L2-resident by design (states of 0.26 and 8.4 MB)"},
         "cases": out,
     }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
     return 0
 
