@@ -137,11 +137,13 @@ __device__ __forceinline__ void spmv(int ns, const QuadBuffers &q, const double 
     }
 }
 
+// Jacobi-PCG on A~ x = rhs (all ones when rhs is null) by one CTA of NTH
+// threads, from x (warm) or from zero; restarts from the true residual.
+// Returns whether max|rhs - A~ x| <= tol; *iters and *resid report the run.
 template <int NTH>
-__global__ void __launch_bounds__(NTH)
-pcg_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rhs, double tol,
-           int maxit, int warm, int *err) {
-    __shared__ double s_red[32];
+__device__ bool pcg_solve(int ns, const QuadBuffers &q, double *x, const double *__restrict__ rhs,
+                          double tol, int maxit, int warm, double *s_red, int *iters,
+                          double *resid) {
     double *r = q.r, *z = q.z, *p = q.p, *qv = q.q;
     if (!warm)
         for (int k = threadIdx.x; k < ns; k += NTH) x[k] = 0.0;
@@ -203,6 +205,19 @@ pcg_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rh
         rmax = block_max<NTH>(lm, s_red);
         converged = rmax <= tol;
     }
+    *iters = it;
+    *resid = rmax;
+    return converged;
+}
+
+template <int NTH>
+__global__ void __launch_bounds__(NTH)
+pcg_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rhs, double tol,
+           int maxit, int warm, int *err) {
+    __shared__ double s_red[32];
+    int it = 0;
+    double rmax = 0.0;
+    const bool converged = pcg_solve<NTH>(ns, q, x, rhs, tol, maxit, warm, s_red, &it, &rmax);
     if (threadIdx.x == 0) {
         *q.iters = it;
         *q.resid = rmax;
@@ -219,8 +234,10 @@ pcg_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rh
 // the ELL rows (only their nonzeros); it contracts by about cond(A~) times
 // the FP32 rounding per pass and stops when the FP64 residual stops falling
 // (its rounding floor) or reaches zero.  Fixed order throughout, so the
-// result is bitwise reproducible.  max|rhs - A~ x| is checked against tol
-// like the CG's; a non-positive pivot records ERR_NOCONV.
+// result is bitwise reproducible.  If the refinement stops above tol or a
+// pivot is not positive (a system too ill-conditioned for the FP32 factor),
+// the same CTA runs the FP64 Jacobi-PCG instead; ERR_NOCONV only if that
+// fails too.
 constexpr int CHOL_T = 512;
 constexpr int CHOL_W = CHOL_T / 32;
 #ifndef IBM_CHOL_MAX
@@ -256,7 +273,7 @@ __device__ __forceinline__ void inv_row(float *__restrict__ F, int ld, int i, in
 
 __global__ void __launch_bounds__(CHOL_T)
 chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rhs, double tol,
-            int warm, int *err) {
+            int maxit, int warm, int *err) {
     // rows have an odd stride, so a warp walking a column (consecutive rows)
     // or threads walking their own rows hit distinct banks
     const int ld = ns | 1;
@@ -394,10 +411,19 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
         __syncthreads();
     }
     for (int k = tid; k < ns; k += CHOL_T) x[k] = sx[k];
+    bool ok = !s_bad && rmax <= tol;
+    if (!ok) {
+        // too ill-conditioned for the FP32 factor (e.g. two markers in one
+        // cell, placed without dedup): the FP64 Jacobi-PCG takes over, from
+        // the refined x when it is finite
+        __shared__ double s_red32[32];
+        const bool warm_x = !s_bad && rmax < 1.0;
+        ok = pcg_solve<CHOL_T>(ns, q, x, rhs, tol, maxit, warm_x, s_red32, &it, &rmax);
+    }
     if (tid == 0) {
         *q.iters = it;
         *q.resid = rmax;
-        if (s_bad || !(rmax <= tol)) record_error(err, ERR_NOCONV);
+        if (!ok) record_error(err, ERR_NOCONV);
     }
 }
 
@@ -420,7 +446,7 @@ static cudaError_t launch_quadrature_solve_w(int ns, const QuadBuffers &qb, cons
             if (e != cudaSuccess) return e;
             configured = true;
         }
-        chol_kernel<<<1, CHOL_T, chol_smem(ns), s>>>(ns, qb, x, rhs, tol, warm, err);
+        chol_kernel<<<1, CHOL_T, chol_smem(ns), s>>>(ns, qb, x, rhs, tol, maxit, warm, err);
     } else if (ns <= 2048) {
         pcg_kernel<256><<<1, 256, 0, s>>>(ns, qb, x, rhs, tol, maxit, warm, err);
     } else {

@@ -420,3 +420,25 @@ def test_quadrature_around_the_dense_solver_limit(oracle, dim, n):
     assert rc == 0
     assert np.max(np.abs(eps - eo) / np.abs(eo)) < 1e-9
     grid.close()
+
+
+@pytest.mark.parametrize("sep", [0.5, 0.1])
+def test_quadrature_two_markers_in_one_cell(oracle, sep):
+    """Markers placed without dedup, two of them `sep` cells apart inside one
+    cell: A~ has a condition number of 1e8-1e9, too much for the FP32
+    factor of the dense solver, whose kernel then hands over to the FP64
+    Jacobi-PCG.  The weights must satisfy A~ eps~ = 1 to the solver bound,
+    checked with the oracle's dense A~ (the weights themselves are not well
+    determined at this conditioning)."""
+    g = C.small_grid(2, (64, 32), h=0.1, fp_bytes=8)
+    lo = np.array(g.lo[:2])
+    base = lo + (np.stack([8 + np.arange(20), np.full(20, 10)], 1) + 0.5) * g.h
+    X = np.vstack([base, base[5] + np.array([sep * g.h, 0.0])])
+    grid = ibm.Grid(g, max_markers=len(X))
+    nk = grid.set_markers(X, np.ones(len(X)), dedup=False)
+    assert nk == len(X)
+    grid.sync()
+    _, eps, idx = grid.markers()
+    A = oracle.assemble_A_dense(g, X[idx])
+    assert np.max(np.abs(1.0 - A @ eps)) < 1e-9
+    grid.close()
