@@ -587,9 +587,11 @@ zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, cons
 }  // namespace
 
 int zmarch_chunk(const GridParams &g) {
-    // planes per CTA: enough CTAs to fill the GPU several times over
+    // planes per CTA: enough CTAs to fill the GPU several times over.  At
+    // 256^3, chunks of 19-24 planes measured 2.6 % faster per step than 32
+    // (8 was 5 % slower, 43 3 %)
     const long long cols = (long long)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY);
-    int zc = 32;
+    int zc = 24;
     while (zc > 8 && cols * ((g.n[2] + zc - 1) / zc) < 8 * 152) zc /= 2;
     return zc;
 }
