@@ -174,8 +174,10 @@ ibm_status ibm_forces_and_nusselt(ibm_grid *g, double force[3], double *heat_rat
  * taken every `every` steps. */
 
 /* Bytes of the adjoint workspace for max_steps recorded steps with a
- * checkpoint every `every` steps: ceil(max_steps/every) + every + 6 states,
- * (dim+2) x N doubles and a few doubles per marker (0 if invalid). */
+ * checkpoint every `every` steps: ceil(max_steps/every) + 3 every + 6
+ * states (a replayed segment keeps each step's state, U1 and U*),
+ * (dim+2) x N doubles and a few doubles per marker and segment step (0 if
+ * invalid). */
 size_t ibm_adjoint_workspace_bytes(const ibm_grid_desc *desc, int max_markers, int max_steps,
                                    int every);
 

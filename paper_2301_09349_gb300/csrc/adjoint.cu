@@ -1000,6 +1000,9 @@ size_t adj_layout(const ibm_grid_desc &d, int cap, int max_steps, int every, cha
     b.ckpt = take(SB * n_ckpt);
     b.dt_hist = (double *)take(sizeof(double) * max_steps);
     b.seg = take(SB * every);
+    b.seg1 = take(SB * every);
+    b.segs = take(SB * every);
+    b.segf = (double *)take(sizeof(double) * 5 * c1 * every);
     b.A = take(SB);
     b.B = take(SB);
     b.lam = take(SB);
@@ -1036,13 +1039,30 @@ int marker_ctas(const ibm_grid *g) {
 
 // one forward step from Un into Unext with a given dt (no finish: the
 // handle's time, sums and step size are left alone)
-ibm_status replay_step(ibm_grid *g, const void *Un, void *Unext, double dt) {
+// The marker buffers with the forcing (rho_L, G, H) of segment step i
+// redirected into the segment store.
+MarkerBuffers seg_markers(const ibm_grid *g, int i) {
+    MarkerBuffers m = g->mb;
+    const size_t c1 = g->adj.cap > 0 ? (size_t)g->adj.cap : 1;
+    double *f = g->adj.segf + (size_t)i * 5 * c1;
+    m.rhoL = f;
+    m.G = f + c1;
+    m.H = f + 4 * c1;
+    return m;
+}
+
+// One recorded step again (its recorded dt), keeping what its reverse needs:
+// U1 into U1s, U* before the forcing into Uss, the marker forcing into m.
+ibm_status replay_step(ibm_grid *g, const void *Un, void *Unext, double dt, void *U1s,
+                       void *Uss, const MarkerBuffers &m) {
     const int fpb = g->desc.fp_bytes;
-    ACU(launch_stage1(g->gp, fpb, Un, g->adj.A, g->fb, dt, g->stream), "replay stage 1");
-    ACU(launch_stage2(g->gp, fpb, Un, g->adj.A, Unext, g->fb, dt, g->stream), "replay stage 2");
+    ACU(launch_stage1(g->gp, fpb, Un, U1s, g->fb, dt, g->stream), "replay stage 1");
+    ACU(launch_stage2(g->gp, fpb, Un, U1s, Unext, g->fb, dt, g->stream), "replay stage 2");
+    ACU(cudaMemcpyAsync(Uss, Unext, state_bytes_of(g->desc), cudaMemcpyDeviceToDevice, g->stream),
+        "keep U*");
     if (g->mb.ns > 0) {
-        ACU(launch_interp_force(g->gp, fpb, Unext, g->mb, marker_ctas(g), g->stream), "replay interp");
-        ACU(launch_spread_apply(g->gp, fpb, Unext, g->mb, marker_ctas(g), g->stream), "replay spread");
+        ACU(launch_interp_force(g->gp, fpb, Unext, m, marker_ctas(g), g->stream), "replay interp");
+        ACU(launch_spread_apply(g->gp, fpb, Unext, m, marker_ctas(g), g->stream), "replay spread");
     }
     return IBM_OK;
 }
@@ -1151,18 +1171,25 @@ ibm_status ibm_backward(ibm_grid *g, double dJ_dCd, double dJ_dNu, double *dJ_dX
         char *segb = (char *)a.seg;
         ACU(cudaMemcpyAsync(segb, (char *)a.ckpt + (size_t)seg * SB, sb, cudaMemcpyDeviceToDevice, s),
             "restore checkpoint");
-        for (int n = s0; n < s1 - 1; ++n) {
-            st = replay_step(g, segb + (size_t)(n - s0) * SB, segb + (size_t)(n - s0 + 1) * SB, dts[n]);
+        // replay the segment, keeping each step's U1, U* and marker forcing
+        // (the last step's successor state goes to scratch: jtv is rewritten
+        // by the reverse sweep before it is read)
+        for (int n = s0; n < s1; ++n) {
+            const size_t i = (size_t)(n - s0);
+            void *next = n + 1 < s1 ? (void *)(segb + (i + 1) * SB) : a.jtv;
+            st = replay_step(g, segb + i * SB, next, dts[n], (char *)a.seg1 + i * SB,
+                             (char *)a.segs + i * SB, seg_markers(g, (int)i));
             if (st != IBM_OK) return st;
         }
         for (int n = s1 - 1; n >= s0; --n) {
-            const void *Un = segb + (size_t)(n - s0) * SB;
-            ACU(launch_stage1(g->gp, fpb, Un, a.A, g->fb, dts[n], s), "recompute stage 1");
-            ACU(launch_stage2(g->gp, fpb, Un, a.A, a.B, g->fb, dts[n], s), "recompute stage 2");
-            ACU(launch_interp_force(g->gp, fpb, a.B, g->mb, marker_ctas(g), s), "recompute forcing");
+            const size_t i = (size_t)(n - s0);
+            const void *Un = segb + i * SB;
+            AdjBuffers an = a;
+            an.A = (char *)a.seg1 + i * SB;
+            an.B = (char *)a.segs + i * SB;
             const bool last = n == S - 1;
-            ACU(launch_reverse_step(g->gp, fpb, g->mb, a, Un, dts[n], last ? cd : 0.0,
-                                    last ? nu : 0.0, g->n_sm, s),
+            ACU(launch_reverse_step(g->gp, fpb, seg_markers(g, (int)i), an, Un, dts[n],
+                                    last ? cd : 0.0, last ? nu : 0.0, g->n_sm, s),
                 "reverse step");
         }
     }

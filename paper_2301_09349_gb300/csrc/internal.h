@@ -223,6 +223,9 @@ struct AdjBuffers {
     void *ckpt = nullptr;        // n_ckpt states: U at steps 0, every, 2 every, ...
     double *dt_hist = nullptr;   // step size of every recorded step
     void *seg = nullptr;         // every states: one replayed segment
+    void *seg1 = nullptr;        // every states: U1 of each step of the segment
+    void *segs = nullptr;        // every states: U* (before forcing) of each step
+    double *segf = nullptr;      // every x cap x 5: rho_L, G (3), H of each step
     void *A = nullptr;           // U1 of the step being reversed
     void *B = nullptr;           // U* of the step being reversed
     void *lam = nullptr;         // adjoint state
