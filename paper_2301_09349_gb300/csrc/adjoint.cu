@@ -507,26 +507,34 @@ adj_flux_tile_kernel(const GridParams g, const T *__restrict__ U, const T *__res
     }
 }
 
-// out = (dW/dU)^T lamW at every cell (then lamW is cleared):
+// w = (dW/dU)^T lamW at every cell (then lamW is cleared):
 // rho-bar = W_rho - sum_m W_um u_m / rho + W_p (gamma-1) |u|^2/2,
 // m-bar = W_u / rho - W_p (gamma-1) u, E-bar = W_p (gamma-1).
+// MODE -1 stores w in out; the reverse sweep's two SSP-RK2 updates take w
+// directly: MODE 0 mu = lam/2 + (dt/2) w, MODE 1 lam = lam/2 + mu + dt w.
 // In the grid's type throughout (double arithmetic is slow on this GPU).
-template <int DIM, typename T>
+template <int DIM, typename T, int MODE>
 __global__ void __launch_bounds__(AT)
 adj_prim_kernel(const GridParams g, const T *__restrict__ U, T *__restrict__ lamW,
-                T *__restrict__ out) {
+                T *__restrict__ out, T *__restrict__ lam, T *__restrict__ mu, double dt_d) {
     using R = T;
     constexpr int NC = DIM + 2;
     const long long N = g.N;
     const AdjK<R> k(g);
+    const R dt = (R)dt_d, half = R(0.5);
     for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < N;
          j += (long long)gridDim.x * blockDim.x) {
         // all of a cell's loads are issued before its stores
-        R uc[DIM + 1], wbv[NC];
+        R uc[DIM + 1], wbv[NC], lv[NC], mv[NC];
 #pragma unroll
         for (int q = 0; q <= DIM; ++q) uc[q] = __ldg(U + q * N + j);
 #pragma unroll
         for (int q = 0; q < NC; ++q) wbv[q] = lamW[q * N + j];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            lv[q] = MODE >= 0 ? lam[q * N + j] : R(0);
+            mv[q] = MODE == 1 ? mu[q * N + j] : R(0);
+        }
 #pragma unroll
         for (int q = 0; q < NC; ++q) lamW[q * N + j] = R(0);
         const R rho = uc[0], inv = R(1) / rho;
@@ -537,29 +545,24 @@ adj_prim_kernel(const GridParams g, const T *__restrict__ U, T *__restrict__ lam
             ke += v[d] * v[d];
         }
         const R pb = wbv[NC - 1] * k.gm1;
+        R w[NC];
         R rb = wbv[0] + pb * R(0.5) * ke;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             rb -= wbv[1 + d] * v[d] * inv;
-            out[(1 + d) * N + j] = wbv[1 + d] * inv - pb * v[d];
+            w[1 + d] = wbv[1 + d] * inv - pb * v[d];
         }
-        out[j] = rb;
-        out[(NC - 1) * N + j] = pb;
+        w[0] = rb;
+        w[NC - 1] = pb;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+            if (MODE < 0) out[q * N + j] = w[q];
+            else if (MODE == 0) mu[q * N + j] = half * lv[q] + half * dt * w[q];
+            else lam[q * N + j] = half * lv[q] + mv[q] + dt * w[q];
+        }
     }
 }
 
-// mu = lam/2 + (dt/2) jtv  (mode 0);  lam = lam/2 + mu + dt jtv  (mode 1)
-template <typename T>
-__global__ void adj_combine_kernel(long long M, int mode, double dt_d, T *__restrict__ lam,
-                                   T *__restrict__ mu, const T *__restrict__ jtv) {
-    const T dt = (T)dt_d, half = T(0.5);
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < M;
-         q += (long long)gridDim.x * blockDim.x) {
-        const T l = lam[q], j = jtv[q];
-        if (mode == 0) mu[q] = half * l + half * dt * j;
-        else lam[q] = half * l + mu[q] + dt * j;
-    }
-}
 
 // One warp per band cell (cells of the band tiles in order, warps strided
 // over the grid); fn(c, j, lane) runs on every lane of the warp.
@@ -871,7 +874,8 @@ int grid_for(long long work, int per_block = AT) {
 // out = J_L(U)^T V (lamW must be zero on entry; it is zero again on exit)
 template <int DIM, typename T>
 cudaError_t rhs_vjp_t(const GridParams &g, const void *U, const void *V, void *lamW_, void *out,
-                      cudaStream_t s) {
+                      cudaStream_t s, int mode = -1, void *lam = nullptr, void *mu = nullptr,
+                      double dt = 0.0) {
     const T *u = (const T *)U, *v = (const T *)V;
     T *lamW = (T *)lamW_;
     using B = AdjBox<DIM, T>;
@@ -888,7 +892,13 @@ cudaError_t rhs_vjp_t(const GridParams &g, const void *U, const void *V, void *l
     adj_flux_tile_kernel<DIM, T><<<grid, FT, B::SMEM, s>>>(g, u, v, lamW);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    adj_prim_kernel<DIM, T><<<grid_for(g.N), AT, 0, s>>>(g, u, lamW, (T *)out);
+    const int nb = grid_for(g.N);
+    if (mode == 0)
+        adj_prim_kernel<DIM, T, 0><<<nb, AT, 0, s>>>(g, u, lamW, nullptr, (T *)lam, (T *)mu, dt);
+    else if (mode == 1)
+        adj_prim_kernel<DIM, T, 1><<<nb, AT, 0, s>>>(g, u, lamW, nullptr, (T *)lam, (T *)mu, dt);
+    else
+        adj_prim_kernel<DIM, T, -1><<<nb, AT, 0, s>>>(g, u, lamW, (T *)out, nullptr, nullptr, 0.0);
     return cudaGetLastError();
 }
 
@@ -896,11 +906,10 @@ template <int DIM, typename T>
 cudaError_t reverse_step_t(const GridParams &g, const MarkerBuffers &m, const AdjBuffers &a,
                            const void *Un, double dt, double cd, double nu, int n_sm,
                            cudaStream_t s) {
-    const long long M = g.N * (DIM + 2);
     const unsigned *keys = m.keys[m.sorted];
     const int *perm = m.perm[m.sorted];
     const int bc = 4 * (n_sm > 0 ? n_sm : 1);
-    T *lam = (T *)a.lam, *mu = (T *)a.mu, *jtv = (T *)a.jtv;
+    T *lam = (T *)a.lam, *mu = (T *)a.mu;
     cudaError_t e = cudaSuccess;
     if (m.ns > 0) {
         adj_apply_kernel<DIM, T><<<bc, AT, 0, s>>>(g, m, keys, perm, (const T *)a.B, lam,
@@ -911,13 +920,10 @@ cudaError_t reverse_step_t(const GridParams &g, const MarkerBuffers &m, const Ad
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    e = rhs_vjp_t<DIM, T>(g, a.A, lam, a.lamW, jtv, s);
+    // mu = lam/2 + (dt/2) J_L(U1)^T lam, then lam = lam/2 + mu + dt J_L(U)^T mu
+    e = rhs_vjp_t<DIM, T>(g, a.A, lam, a.lamW, nullptr, s, 0, lam, mu, dt);
     if (e != cudaSuccess) return e;
-    adj_combine_kernel<T><<<grid_for(M), AT, 0, s>>>(M, 0, dt, lam, mu, jtv);
-    e = rhs_vjp_t<DIM, T>(g, Un, mu, a.lamW, jtv, s);
-    if (e != cudaSuccess) return e;
-    adj_combine_kernel<T><<<grid_for(M), AT, 0, s>>>(M, 1, dt, lam, mu, jtv);
-    return cudaGetLastError();
+    return rhs_vjp_t<DIM, T>(g, Un, mu, a.lamW, nullptr, s, 1, lam, mu, dt);
 }
 
 template <int DIM>
@@ -1172,8 +1178,8 @@ ibm_status ibm_backward(ibm_grid *g, double dJ_dCd, double dJ_dNu, double *dJ_dX
         ACU(cudaMemcpyAsync(segb, (char *)a.ckpt + (size_t)seg * SB, sb, cudaMemcpyDeviceToDevice, s),
             "restore checkpoint");
         // replay the segment, keeping each step's U1, U* and marker forcing
-        // (the last step's successor state goes to scratch: jtv is rewritten
-        // by the reverse sweep before it is read)
+        // (the last step's successor state is not needed: it goes to the
+        // scratch state jtv)
         for (int n = s0; n < s1; ++n) {
             const size_t i = (size_t)(n - s0);
             void *next = n + 1 < s1 ? (void *)(segb + (i + 1) * SB) : a.jtv;

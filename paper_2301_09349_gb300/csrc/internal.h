@@ -230,7 +230,7 @@ struct AdjBuffers {
     void *B = nullptr;           // U* of the step being reversed
     void *lam = nullptr;         // adjoint state
     void *mu = nullptr;          // adjoint of U1
-    void *jtv = nullptr;         // transpose-Jacobian product of L
+    void *jtv = nullptr;         // scratch state
     void *lfq = nullptr;         // (dim+1) x N: adjoints of the spread sources
     void *lamW = nullptr;        // (dim+2) x N accumulators of the primitive adjoints, in
                                  // the grid's type (sized for doubles: also FP64 scratch)
