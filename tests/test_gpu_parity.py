@@ -65,6 +65,9 @@ MIXED_BC = (C.BC_FREESTREAM, C.BC_ZEROGRAD, C.BC_SLIP, C.BC_SLIP, C.BC_ZEROGRAD,
     (3, (21, 19, 13), 4, 1e-4), (3, (21, 19, 13), 8, 1e-12),
     # x extents that are multiples of 4 take the bulk-tensor-copy path
     (3, (36, 19, 13), 4, 1e-4), (3, (68, 27, 21), 4, 1e-4),
+    # 2D FP64 grids of 256 or more 16 x 16 tiles keep 16 x 16 stage tiles
+    # (smaller ones take 8 x 8); 263 x 250 is 17 x 16 tiles with ragged edges
+    (2, (263, 250), 8, 1e-12),
 ])
 @pytest.mark.parametrize("bc", ["mixed", "periodic"])
 def test_rhs_matches_oracle(oracle, dim, n, fp, tol, bc):
