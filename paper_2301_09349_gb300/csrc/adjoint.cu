@@ -590,16 +590,20 @@ __device__ __forceinline__ void for_band_cells_warp(const GridParams &g, const M
 
 // Lane n < 3^DIM visits the markers owned by neighbour n of c (the order of
 // gather_markers: z, y, x offsets ascending); the warp then sums the lanes'
-// partials with warp_sum_d, a fixed tree.
-template <int DIM, typename F>
+// partials with warp_sum_d, a fixed tree.  The weights Phi_k(j) are taken in
+// precision R: the field precision where the pass reverses the forward
+// interpolation or spreading (the forward evaluates them in that precision,
+// and FP64 square roots run at a small fraction of the FP32 rate on this
+// GPU), double for the quadrature's FP64 fields.
+template <int DIM, typename R, typename F>
 __device__ __forceinline__ void gather_markers_lane(const GridParams &g, const MarkerBuffers &m,
                                                     const unsigned *__restrict__ keys,
                                                     const int *__restrict__ perm, const int c[3],
                                                     int lane, F &&visit) {
     constexpr int NT3 = DIM == 3 ? 27 : 9;
     if (lane >= NT3) return;
-    gather_cell<DIM, double>(g, m, keys, perm, c, lane % 3 - 1, (lane / 3) % 3 - 1,
-                             DIM == 3 ? lane / 9 - 1 : 0, visit);
+    gather_cell<DIM, R>(g, m, keys, perm, c, lane % 3 - 1, (lane / 3) % 3 - 1,
+                        DIM == 3 ? lane / 9 - 1 : 0, visit);
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -609,7 +613,11 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 // 1. reverse of the forced update at the band cells: lam (adjoint of
-//    U^{n+1}) -> lam* in place, and lam_f, lam_q into lfq.
+//    U^{n+1}) -> lam* in place, and lam_f, lam_q into lfq.  Sums and
+//    arithmetic in the field precision T, like the forward spreading (a
+//    warp-wide FP64 instruction costs the FP64 pipe ~16 cycles on this GPU
+//    whatever the active lanes); the change of |rho u|^2 is taken as
+//    sum_d f_d (2 m_d + f_d), free of cancellation.
 template <int DIM, typename T>
 __global__ void __launch_bounds__(AT)
 adj_apply_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__restrict__ keys,
@@ -617,39 +625,38 @@ adj_apply_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__re
                  T *__restrict__ lfq) {
     const long long N = g.N;
     for_band_cells_warp<DIM>(g, m, [&](const int *c, long long j, int lane) {
-        double f[DIM], q = 0.0;
+        T f[DIM], q = T(0);
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) f[d] = 0.0;
-        gather_markers_lane<DIM>(g, m, keys, perm, c, lane, [&](int kk, double w) {
-            const double e = m.eps[kk];
+        for (int d = 0; d < DIM; ++d) f[d] = T(0);
+        gather_markers_lane<DIM, T>(g, m, keys, perm, c, lane, [&](int kk, T w) {
+            const T ew = (T)m.eps[kk] * w;
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) f[d] += m.G[(long long)kk * DIM + d] * e * w;
-            q += m.H[kk] * e * w;
+            for (int d = 0; d < DIM; ++d) f[d] += (T)m.G[(long long)kk * DIM + d] * ew;
+            q += (T)m.H[kk] * ew;
         });
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) f[d] = warp_sum_d(f[d]);
-        q = warp_sum_d(q);
+        for (int d = 0; d < DIM; ++d) f[d] = warp_sum_r<T>(f[d]);
+        q = warp_sum_r<T>(q);
         if (lane != 0) return;
-        const double rho = (double)Us[j];
-        const double lE = (double)lam[(DIM + 1) * N + j];
-        double m0sq = 0.0, m1sq = 0.0;
+        const T irho = T(1) / Us[j];
+        const T lE = lam[(DIM + 1) * N + j];
+        const T lEr = lE * irho;
+        T dk = T(0);   // |m1|^2 - |m0|^2
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            const double ms = (double)Us[(1 + d) * N + j];
-            const double m1 = ms + f[d];
-            const double lm = (double)lam[(1 + d) * N + j];
-            m0sq += ms * ms;
-            m1sq += m1 * m1;
+            const T ms = Us[(1 + d) * N + j];
+            const T m1 = ms + f[d];
+            const T lm = lam[(1 + d) * N + j];
+            dk += f[d] * (ms + m1);
             if (g.energy_reading == 1) {
-                lfq[d * N + j] = (T)lm;
+                lfq[d * N + j] = lm;
             } else {
-                lfq[d * N + j] = (T)(lm + lE * m1 / rho);
-                lam[(1 + d) * N + j] = (T)(lm + lE * f[d] / rho);
+                lfq[d * N + j] = lm + lEr * m1;
+                lam[(1 + d) * N + j] = lm + lEr * f[d];
             }
         }
-        lfq[DIM * N + j] = (T)lE;
-        if (g.energy_reading != 1)
-            lam[j] = (T)((double)lam[j] + lE * 0.5 * (m0sq - m1sq) / (rho * rho));
+        lfq[DIM * N + j] = lE;
+        if (g.energy_reading != 1) lam[j] = lam[j] - T(0.5) * lEr * irho * dk;
     });
 }
 
@@ -780,6 +787,7 @@ adj_marker_kernel(const GridParams g, const MarkerBuffers m, const AdjBuffers a,
 }
 
 // 4. interpolation reversed: lam* += sum_k Phi_k(j) d(rho, rho u, rho e)/dU^T mr_k
+//    (sums and arithmetic in the field precision T, as in step 1)
 template <int DIM, typename T>
 __global__ void __launch_bounds__(AT)
 adj_interp_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__restrict__ keys,
@@ -787,31 +795,32 @@ adj_interp_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__r
                   T *__restrict__ lam) {
     const long long N = g.N;
     for_band_cells_warp<DIM>(g, m, [&](const int *c, long long j, int lane) {
-        double sr = 0.0, sm[DIM], se = 0.0;
+        T sr = T(0), sm[DIM], se = T(0);
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) sm[d] = 0.0;
-        gather_markers_lane<DIM>(g, m, keys, perm, c, lane, [&](int kk, double w) {
+        for (int d = 0; d < DIM; ++d) sm[d] = T(0);
+        gather_markers_lane<DIM, T>(g, m, keys, perm, c, lane, [&](int kk, T w) {
             const double *mr = a.mr + (long long)kk * 5;
-            sr += w * mr[0];
+            sr += w * (T)mr[0];
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) sm[d] += w * mr[1 + d];
-            se += w * mr[4];
+            for (int d = 0; d < DIM; ++d) sm[d] += w * (T)mr[1 + d];
+            se += w * (T)mr[4];
         });
-        sr = warp_sum_d(sr);
+        sr = warp_sum_r<T>(sr);
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) sm[d] = warp_sum_d(sm[d]);
-        se = warp_sum_d(se);
+        for (int d = 0; d < DIM; ++d) sm[d] = warp_sum_r<T>(sm[d]);
+        se = warp_sum_r<T>(se);
         if (lane != 0) return;
-        const double rho = (double)Us[j];
-        double msq = 0.0;
+        const T irho = T(1) / Us[j];
+        const T ser = se * irho;
+        T msq = T(0);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            const double md = (double)Us[(1 + d) * N + j];
+            const T md = Us[(1 + d) * N + j];
             msq += md * md;
-            lam[(1 + d) * N + j] = (T)((double)lam[(1 + d) * N + j] + sm[d] - se * md / rho);
+            lam[(1 + d) * N + j] = lam[(1 + d) * N + j] + sm[d] - ser * md;
         }
-        lam[j] = (T)((double)lam[j] + sr + se * 0.5 * msq / (rho * rho));
-        lam[(DIM + 1) * N + j] = (T)((double)lam[(DIM + 1) * N + j] + se);
+        lam[j] = lam[j] + sr + T(0.5) * ser * irho * msq;
+        lam[(DIM + 1) * N + j] = lam[(DIM + 1) * N + j] + se;
     });
 }
 
@@ -823,7 +832,7 @@ adj_eps_fields_kernel(const GridParams g, const MarkerBuffers m, const unsigned 
     const long long N = g.N;
     for_band_cells_warp<DIM>(g, m, [&](const int *c, long long j, int lane) {
         double se = 0.0, sz = 0.0;
-        gather_markers_lane<DIM>(g, m, keys, perm, c, lane, [&](int kk, double w) {
+        gather_markers_lane<DIM, double>(g, m, keys, perm, c, lane, [&](int kk, double w) {
             se += w * m.eps[kk];
             sz += w * a.z[kk];
         });
