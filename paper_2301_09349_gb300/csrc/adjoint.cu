@@ -660,38 +660,39 @@ adj_apply_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__re
     });
 }
 
-// derivative of the 1D kernel
-__device__ __forceinline__ double dphi_d(double r) {
-    const double a = fabs(r), s = r < 0.0 ? -1.0 : 1.0;
-    if (a <= 0.5) return -r / sqrt(1.0 - 3.0 * a * a);
-    if (a <= 1.5) {
-        const double b = 1.0 - a;
-        return s * (-3.0 - 3.0 * b / sqrt(1.0 - 3.0 * b * b)) / 6.0;
+// derivative of the 1D kernel, in precision R
+template <typename R> __device__ __forceinline__ R dphi_r(R r) {
+    const R a = r < R(0) ? -r : r, s = r < R(0) ? R(-1) : R(1);
+    if (a <= R(0.5)) return -r / sqrt(R(1) - R(3) * a * a);
+    if (a <= R(1.5)) {
+        const R b = R(1) - a;
+        return s * (R(-3) - R(3) * b / sqrt(R(1) - R(3) * b * b)) / R(6);
     }
-    return 0.0;
+    return R(0);
 }
 
-// Phi_k and dPhi_k/dX_k at the support cell `lane` of marker k (double)
-template <int DIM>
-__device__ __forceinline__ double lane_weight_grad(const GridParams &g, const MarkerBuffers &m,
-                                                   int k, int lane, double (&gw)[DIM],
-                                                   long long &j) {
+// Phi_k and dPhi_k/dX_k at the support cell `lane` of marker k, in
+// precision R (the field precision where the pass reverses the forward
+// interpolation or spreading, double for the quadrature)
+template <int DIM, typename R>
+__device__ __forceinline__ R lane_weight_grad(const GridParams &g, const MarkerBuffers &m, int k,
+                                              int lane, R (&gw)[DIM], long long &j) {
     const int o[3] = {lane % 3 - 1, (lane / 3) % 3 - 1, DIM == 3 ? lane / 9 - 1 : 0};
-    double ph[DIM], dp[DIM];
+    R ph[DIM], dp[DIM];
     int c[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         c[d] = m.cell[(long long)k * 3 + d] + o[d];
-        const double r = ((double)o[d] + 0.5) - m.frac_d[(long long)k * 3 + d];
-        ph[d] = phi_d(r);
-        dp[d] = dphi_d(r);
+        const R r = cell_offset<R>(o[d], marker_frac<R>(m, k, d));
+        ph[d] = phi_r<R>(r);
+        dp[d] = dphi_r<R>(r);
     }
-    double w = 1.0;
+    R w = R(1);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) w *= ph[d];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        double pr = -dp[d] * g.inv_h;   // dr/dX = -1/h
+        R pr = -dp[d] * (R)g.inv_h;   // dr/dX = -1/h
 #pragma unroll
         for (int e = 0; e < DIM; ++e)
             if (e != d) pr *= ph[e];
@@ -717,31 +718,36 @@ adj_marker_kernel(const GridParams g, const MarkerBuffers m, const AdjBuffers a,
     double G[DIM], H = m.H[k];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) G[d] = m.G[(long long)k * DIM + d];
-    double gw[DIM], w = 0.0, sf[DIM], sq = 0.0, gxs[DIM];
+    // the weights, their X derivatives and the lane sums in the field
+    // precision T (the forward spreading and interpolation use the same
+    // weights); the per-marker terms and the interpolation part, which
+    // cancels where the wall and fluid temperatures are close, in double
+    T gw[DIM], w = T(0), sfT[DIM], sqT = T(0), gxT[DIM];
     long long j = 0;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) sf[d] = gxs[d] = gw[d] = 0.0;
+    for (int d = 0; d < DIM; ++d) sfT[d] = gxT[d] = gw[d] = T(0);
     if (lane < NS) {
-        w = lane_weight_grad<DIM>(g, m, k, lane, gw, j);
-        double dot = 0.0;
+        w = lane_weight_grad<DIM, T>(g, m, k, lane, gw, j);
+        T dot = T(0);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            const double lf = (double)((const T *)a.lfq)[d * N + j];
-            sf[d] = w * lf;
-            dot += G[d] * lf;
+            const T lf = ((const T *)a.lfq)[d * N + j];
+            sfT[d] = w * lf;
+            dot += (T)G[d] * lf;
         }
-        const double lq = (double)((const T *)a.lfq)[DIM * N + j];
-        sq = w * lq;
-        dot += H * lq;
+        const T lq = ((const T *)a.lfq)[DIM * N + j];
+        sqT = w * lq;
+        dot += (T)H * lq;
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) gxs[d] = gw[d] * dot;
+        for (int d = 0; d < DIM; ++d) gxT[d] = gw[d] * dot;
     }
+    double sf[DIM], gxs[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        sf[d] = warp_sum_d(sf[d]);
-        gxs[d] = warp_sum_d(gxs[d]);
+        sf[d] = (double)warp_sum_r<T>(sfT[d]);
+        gxs[d] = (double)warp_sum_r<T>(gxT[d]);
     }
-    sq = warp_sum_d(sq);
+    const double sq = (double)warp_sum_r<T>(sqT);
     double lG[DIM], lH = e * sq + nu * e;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) lG[d] = e * sf[d] + (d == 0 ? cd * e : 0.0);
@@ -765,7 +771,7 @@ adj_marker_kernel(const GridParams g, const MarkerBuffers m, const AdjBuffers a,
         const double rhoe = (double)Us[(DIM + 1) * N + j] - 0.5 * msq / rho;
         const double s = lrho * rho + dotm - lH * rhoe;
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) gxi[d] = gw[d] * s;
+        for (int d = 0; d < DIM; ++d) gxi[d] = (double)gw[d] * s;
     }
 #pragma unroll
     for (int d = 0; d < DIM; ++d) gxi[d] = warp_sum_d(gxi[d]);
@@ -860,7 +866,7 @@ adj_eps_x_kernel(const GridParams g, const MarkerBuffers m, const AdjBuffers a) 
     if (lane < NS) {
         double gw[DIM];
         long long j;
-        lane_weight_grad<DIM>(g, m, k, lane, gw, j);
+        lane_weight_grad<DIM, double>(g, m, k, lane, gw, j);
         const double *w = (const double *)a.lamW;
         const double s = a.z[k] * w[j] + m.eps[k] * w[N + j];
 #pragma unroll

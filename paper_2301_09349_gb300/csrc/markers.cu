@@ -404,24 +404,25 @@ size_t spread_smem_bytes(const GridParams &g) {
 }
 
 // Forced update of one band cell (App. B, Eqs. u_centralF2 and e_centralF2;
-// f.u dropped): momentum += dt f, internal energy += dt q, rho unchanged.
+// f.u dropped): momentum += dt f, internal energy += dt q, rho unchanged, so
+// rho E gains dt q + (|m1|^2 - |m0|^2) / (2 rho), the difference taken as
+// sum_d f_d (m0_d + m1_d) (no cancellation).  In the spreading precision R
+// (the field precision).
 template <int DIM, typename T, typename R>
 __device__ __forceinline__ void apply_forcing(const GridParams &g, T *__restrict__ U, long long j,
                                               const R *f, R qh) {
     const long long N = g.N;
-    const double rho = (double)U[j];
-    double ke0 = 0.0, ke1 = 0.0;
+    const R rho = (R)U[j];
+    R dke = R(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-        const double m0 = (double)U[(1 + d) * N + j];
-        const double m1 = m0 + (double)f[d];
-        ke0 += m0 * m0;
-        ke1 += m1 * m1;
+        const R m0 = (R)U[(1 + d) * N + j];
+        const R m1 = m0 + f[d];
+        dke += f[d] * (m0 + m1);
         U[(1 + d) * N + j] = (T)m1;
     }
-    const double E = (double)U[(DIM + 1) * N + j];
-    const double En = g.energy_reading == 1 ? E + (double)qh
-                                            : (E - 0.5 * ke0 / rho + (double)qh) + 0.5 * ke1 / rho;
+    const R E = (R)U[(DIM + 1) * N + j];
+    const R En = g.energy_reading == 1 ? E + qh : E + (qh + R(0.5) * dke / rho);
     U[(DIM + 1) * N + j] = (T)En;
 }
 
