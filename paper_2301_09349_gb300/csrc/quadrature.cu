@@ -227,25 +227,29 @@ pcg_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rh
 
 // Small systems: A~ is copied dense, in FP32, into shared memory from the
 // ELL rows.  FP64 runs at a small fraction of the FP32 rate on this GPU, so
-// the O(ns^3) work is done in FP32: a right-looking Cholesky A~ = L L^T and
-// the explicit inverse X = L^-1, each one pass over the columns with one
-// barrier per column.  The FP64 solution then comes from iterative
-// refinement, x += X^T X (rhs - A~ x), with the residual taken in FP64 from
-// the ELL rows (only their nonzeros); it contracts by about cond(A~) times
-// the FP32 rounding per pass and stops when the FP64 residual stops falling
-// (its rounding floor) or reaches zero.  Fixed order throughout, so the
-// result is bitwise reproducible.  If the refinement stops above tol or a
-// pivot is not positive (a system too ill-conditioned for the FP32 factor),
-// the same CTA runs the FP64 Jacobi-PCG instead; ERR_NOCONV only if that
-// fails too.
+// the O(ns^3) work is done in FP32: a blocked right-looking Cholesky
+// A~ = L L^T over 32-column panels (one warp factors the panel's diagonal
+// block without block barriers, one thread per row solves the rows below
+// it, 4 x 4 register tiles update the trailing matrix: three barriers per
+// panel), then the inverses of the 32 x 32 diagonal blocks of L, one warp
+// each.  The FP64 solution comes from iterative refinement,
+// x += L^-T L^-1 (rhs - A~ x), with the residual taken in FP64 from the
+// ELL rows (only their nonzeros) and the two triangular solves blocked by
+// the same panels (each diagonal block applied through its inverse); it
+// contracts by about cond(A~) times the FP32 rounding per pass and stops
+// when the FP64 residual stops falling (its rounding floor) or reaches
+// zero.  Fixed order throughout, so the result is bitwise reproducible.
+// If the refinement stops above tol or a pivot is not positive (a system
+// too ill-conditioned for the FP32 factor), the same CTA runs the FP64
+// Jacobi-PCG instead; ERR_NOCONV only if that fails too.
 constexpr int CHOL_T = 512;
 constexpr int CHOL_W = CHOL_T / 32;
 #ifndef IBM_CHOL_MAX
 #define IBM_CHOL_MAX 160
 #endif
 constexpr int CHOL_MAX = IBM_CHOL_MAX;
-constexpr int CHOL_CC = (CHOL_MAX + 31) / 32;               // 32-wide chunks of a row
-static_assert(CHOL_CC <= 5, "the row updates dispatch on at most 5 chunks");
+constexpr int CHOL_PB = 32;                                  // panel width
+static_assert((CHOL_MAX + CHOL_PB - 1) / CHOL_PB <= CHOL_W, "one warp per diagonal block");
 constexpr int CHOL_REFINE_MAX = 40;
 
 // x [ns] in FP64, then the FP32 factors [ns][ns | 1], 1/L_jj, r and t
@@ -253,21 +257,129 @@ size_t chol_smem(int ns) {
     return sizeof(double) * (size_t)ns + sizeof(float) * ((size_t)ns * (ns | 1) + 3 * (size_t)ns);
 }
 
-// row i of the inverse's step j: F[c][i] = (F[c][i] - li X_jc) sc for c <= j
-// over NCH 32-wide chunks, all loads before the stores
-template <int NCH>
-__device__ __forceinline__ void inv_row(float *__restrict__ F, int ld, int i, int j, float li,
-                                        float sc, const float (&xj)[CHOL_CC], int lane) {
-    float v[NCH];
+// Cholesky of the diagonal block [c0, c0 + w) in place, by one warp: lane r
+// holds row c0 + r of the block in registers, and step k hands the pivot
+// column L_lk to the lanes by shuffles; 1 / L_kk into dinv, *bad set on a
+// pivot that is not positive
+__device__ __forceinline__ void chol_diag_block(float *__restrict__ F, int ld, int c0, int w,
+                                                float *__restrict__ dinv, int lane, int *bad) {
+    float a[CHOL_PB];
 #pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-        const int cc = 32 * c + lane;
-        if (cc <= j) v[c] = F[cc * ld + i];
+    for (int l = 0; l < CHOL_PB; ++l)
+        a[l] = (lane < w && l <= lane) ? F[(size_t)(c0 + lane) * ld + c0 + l] : 0.0f;
+#pragma unroll
+    for (int k = 0; k < CHOL_PB; ++k) {
+        if (k < w) {
+            const float d = __shfl_sync(0xffffffffu, a[k], k);
+            const bool good = d > 0.0f;
+            const float sd = good ? sqrtf(d) : 1.0f;
+            const float inv = 1.0f / sd;
+            if (lane == k) {
+                a[k] = sd;
+                dinv[c0 + k] = inv;
+                if (!good) *bad = 1;
+            } else if (lane > k) {
+                a[k] *= inv;
+            }
+            const float lk = a[k];
+#pragma unroll
+            for (int l = k + 1; l < CHOL_PB; ++l) {
+                const float llk = __shfl_sync(0xffffffffu, lk, l);
+                if (lane >= l) a[l] -= lk * llk;
+            }
+        }
     }
+    if (lane < w) {
 #pragma unroll
-    for (int c = 0; c < NCH; ++c) {
-        const int cc = 32 * c + lane;
-        if (cc <= j) F[cc * ld + i] = (v[c] - li * xj[c]) * sc;
+        for (int l = 0; l < CHOL_PB; ++l)
+            if (l <= lane) F[(size_t)(c0 + lane) * ld + c0 + l] = a[l];
+    }
+}
+
+// rows i >= c0 + w of panel [c0, c0 + w): L_i = A_i L_D^-T, one thread per row
+__device__ __forceinline__ void chol_panel_rows(float *__restrict__ F, int ld, int c0, int w,
+                                                int ns, const float *__restrict__ dinv, int tid) {
+    for (int i = c0 + w + tid; i < ns; i += CHOL_T) {
+        float *row = F + (size_t)i * ld + c0;
+        float v[CHOL_PB];
+#pragma unroll
+        for (int k = 0; k < CHOL_PB; ++k) v[k] = k < w ? row[k] : 0.0f;
+#pragma unroll
+        for (int k = 0; k < CHOL_PB; ++k) {
+            if (k < w) {
+                const float *lk = F + (size_t)(c0 + k) * ld + c0;
+                float acc = v[k];
+#pragma unroll
+                for (int l = 0; l < k; ++l) acc -= v[l] * lk[l];
+                v[k] = acc * dinv[c0 + k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < CHOL_PB; ++k)
+            if (k < w) row[k] = v[k];
+    }
+}
+
+// trailing update A_ij -= sum_k L_ik L_jk over the panel's columns, for
+// c1 <= j <= i < ns, in 4 x 4 tiles (tile pairs tj <= ti, one per thread)
+__device__ __forceinline__ void chol_trailing(float *__restrict__ F, int ld, int c0, int w, int ns,
+                                              int tid) {
+    const int c1 = c0 + w, m = ns - c1, nt = (m + 3) / 4, npairs = nt * (nt + 1) / 2;
+    for (int p = tid; p < npairs; p += CHOL_T) {
+        int ti = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+        while ((ti + 1) * (ti + 2) / 2 <= p) ++ti;
+        while (ti * (ti + 1) / 2 > p) --ti;
+        const int tj = p - ti * (ti + 1) / 2;
+        const int i0 = c1 + 4 * ti, j0 = c1 + 4 * tj;
+        float acc[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[r][q] = 0.0f;
+        for (int k = 0; k < w; ++k) {
+            float a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                a[r] = i0 + r < ns ? F[(size_t)(i0 + r) * ld + c0 + k] : 0.0f;
+                b[r] = j0 + r < ns ? F[(size_t)(j0 + r) * ld + c0 + k] : 0.0f;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[r][q] += a[r] * b[q];
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int i = i0 + r, j = j0 + q;
+                if (i < ns && j <= i) F[(size_t)i * ld + j] -= acc[r][q];
+            }
+    }
+}
+
+// inverse of the diagonal block [b0, b0 + wb) of L by one warp (lane =
+// column c): X_rc for r > c goes to F[c][r], above the diagonal; X_cc is
+// dinv[c] already
+__device__ __forceinline__ void chol_diag_inverse(float *__restrict__ F, int ld, int b0, int wb,
+                                                  const float *__restrict__ dinv, int lane) {
+    float xc[CHOL_PB];
+#pragma unroll
+    for (int r = 0; r < CHOL_PB; ++r) {
+        float acc = r == lane ? 1.0f : 0.0f;
+        if (r < wb) {
+            const float *lr = F + (size_t)(b0 + r) * ld + b0;
+#pragma unroll
+            for (int l = 0; l < r; ++l) acc -= lr[l] * xc[l];
+            acc *= dinv[b0 + r];
+        }
+        xc[r] = acc;
+    }
+    if (lane < wb) {
+        float *out = F + (size_t)(b0 + lane) * ld + b0;
+#pragma unroll
+        for (int r = 0; r < CHOL_PB; ++r)
+            if (r > lane && r < wb) out[r] = xc[r];
     }
 }
 
@@ -280,10 +392,11 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
     extern __shared__ __align__(16) double sD[];
     double *sx = sD;                                 // [ns] solution
     float *F = reinterpret_cast<float *>(sx + ns);   // [ns][ld]: L on and below the diagonal,
-                                                     // X = L^-1 transposed above it
-    float *dinv = F + (size_t)ns * ld;               // [ns] 1 / L_jj, the diagonal of X
+                                                     // the inverses X_II of its 32 x 32
+                                                     // diagonal blocks transposed above it
+    float *dinv = F + (size_t)ns * ld;               // [ns] 1 / L_jj, the diagonal of X_II
     float *r32 = dinv + ns;                          // [ns] residual in FP32
-    float *st = r32 + ns;                            // [ns] X r
+    float *st = r32 + ns;                            // [ns] the triangular solves' vector
     __shared__ double s_red[CHOL_T / 32];
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -300,72 +413,23 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
         sx[k] = warm ? x[k] : 0.0;
     }
     __syncthreads();
-    // factor with unscaled columns: step j subtracts a_ij a_kj / a_jj from the
-    // trailing lower triangle and leaves column j as it is, so each column
-    // costs one barrier; the columns are scaled by 1/sqrt(a_jj) at the end.
-    // One warp per row, lanes along the row; a row's operands are all loaded
-    // before its stores.
-    for (int j = 0; j < ns; ++j) {
-        const float d = F[j * ld + j];
-        const float invd = d > 0.0f ? 1.0f / d : 0.0f;
-        if (tid == 0 && !(d > 0.0f)) s_bad = 1;
-        for (int i = j + 1 + warp; i < ns; i += CHOL_W) {
-            float *row = F + i * ld;
-            const float ci = row[j] * invd;
-            float a[CHOL_CC], b[CHOL_CC];
-#pragma unroll
-            for (int c = 0; c < CHOL_CC; ++c) {
-                const int kk = j + 1 + 32 * c + lane;
-                if (kk <= i) {
-                    a[c] = row[kk];
-                    b[c] = F[kk * ld + j];
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < CHOL_CC; ++c) {
-                const int kk = j + 1 + 32 * c + lane;
-                if (kk <= i) row[kk] = a[c] - ci * b[c];
-            }
-        }
+    // blocked Cholesky over 32-column panels, then the diagonal blocks' inverses
+    for (int c0 = 0; c0 < ns; c0 += CHOL_PB) {
+        const int w = min(CHOL_PB, ns - c0);
+        if (warp == 0) chol_diag_block(F, ld, c0, w, dinv, lane, &s_bad);
         __syncthreads();
-    }
-    for (int j = tid; j < ns; j += CHOL_T) {
-        const float d = F[(size_t)j * ld + j];
-        dinv[j] = d > 0.0f ? 1.0f / sqrtf(d) : 1.0f;
-    }
-    __syncthreads();
-    for (int i = tid; i < ns * ld; i += CHOL_T) {
-        const int r = i / ld, c = i - r * ld;
-        if (c < r) F[i] *= dinv[c];
-    }
-    __syncthreads();
-    // X = L^-1, right-looking: once row j of X is final, rows i > j take
-    // -L_ij X_jc (c <= j); row j+1 is then complete and is scaled by
-    // 1/L_{j+1,j+1}.  X_ic (c < i) lives at F[c][i]; X_jj = dinv[j].  One
-    // warp per row, lanes along c; row j of X is read once per step.
-    for (int j = 0; j + 1 < ns; ++j) {
-        float xj[CHOL_CC];
-#pragma unroll
-        for (int c = 0; c < CHOL_CC; ++c) {
-            const int cc = 32 * c + lane;
-            xj[c] = cc < j ? F[(size_t)cc * ld + j] : (cc == j ? dinv[j] : 0.0f);
+        if (c0 + w < ns) {
+            chol_panel_rows(F, ld, c0, w, ns, dinv, tid);
+            __syncthreads();
+            chol_trailing(F, ld, c0, w, ns, tid);
+            __syncthreads();
         }
-        const int nch = j >> 5;   // live chunks - 1, the same for every row of the step
-        for (int i = j + 1 + warp; i < ns; i += CHOL_W) {
-            const float li = F[i * ld + j];
-            const float sc = i == j + 1 ? dinv[i] : 1.0f;
-            switch (nch) {
-                case 0: inv_row<1>(F, ld, i, j, li, sc, xj, lane); break;
-                case 1: inv_row<2>(F, ld, i, j, li, sc, xj, lane); break;
-                case 2: inv_row<3>(F, ld, i, j, li, sc, xj, lane); break;
-                case 3: inv_row<4>(F, ld, i, j, li, sc, xj, lane); break;
-                default: inv_row<5>(F, ld, i, j, li, sc, xj, lane); break;
-            }
-        }
-        __syncthreads();
     }
+    if (warp * CHOL_PB < ns)
+        chol_diag_inverse(F, ld, warp * CHOL_PB, min(CHOL_PB, ns - warp * CHOL_PB), dinv, lane);
+    __syncthreads();
     // refinement: r = rhs - A~ x in FP64 from the ELL rows (one thread per
-    // row), x += X^T X r in FP32
+    // row), x += L^-T L^-1 r in FP32
     double rmax = 0.0, rprev = 0.0;
     int it = 0;
     for (;; ++it) {
@@ -382,32 +446,65 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
         rmax = block_max<CHOL_T>(lm, s_red);   // synchronizes
         if (!(rmax > 0.0) || (it > 0 && !(rmax < 0.5 * rprev)) || it == CHOL_REFINE_MAX) break;
         rprev = rmax;
-        for (int i = tid; i < ns; i += CHOL_T) {
-            float s0 = dinv[i] * r32[i], s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-            int c = 0;
-            for (; c + 4 <= i; c += 4) {
-                s0 += F[(size_t)c * ld + i] * r32[c];
-                s1 += F[(size_t)(c + 1) * ld + i] * r32[c + 1];
-                s2 += F[(size_t)(c + 2) * ld + i] * r32[c + 2];
-                s3 += F[(size_t)(c + 3) * ld + i] * r32[c + 3];
-            }
-            for (; c < i; ++c) s0 += F[(size_t)c * ld + i] * r32[c];
-            st[i] = (s0 + s1) + (s2 + s3);
-        }
+        // t = L^-1 r: per panel, t_I = X_II t_I (warp 0), then the rows
+        // below take -L_iI t_I
+        for (int i = tid; i < ns; i += CHOL_T) st[i] = r32[i];
         __syncthreads();
-        for (int c = tid; c < ns; c += CHOL_T) {
-            const float *row = F + (size_t)c * ld;
-            float s0 = dinv[c] * st[c], s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-            int i = c + 1;
-            for (; i + 4 <= ns; i += 4) {
-                s0 += row[i] * st[i];
-                s1 += row[i + 1] * st[i + 1];
-                s2 += row[i + 2] * st[i + 2];
-                s3 += row[i + 3] * st[i + 3];
+        for (int b0 = 0; b0 < ns; b0 += CHOL_PB) {
+            const int b1 = min(b0 + CHOL_PB, ns);
+            if (warp == 0) {
+                const int i = b0 + lane;
+                float y = 0.0f;
+                if (i < b1) {
+                    y = dinv[i] * st[i];
+                    for (int cq = b0; cq < i; ++cq) y += F[(size_t)cq * ld + i] * st[cq];
+                }
+                __syncwarp();
+                if (i < b1) st[i] = y;
             }
-            for (; i < ns; ++i) s0 += row[i] * st[i];
-            sx[c] += (double)((s0 + s1) + (s2 + s3));
+            __syncthreads();
+            for (int i = b1 + tid; i < ns; i += CHOL_T) {
+                const float *row = F + (size_t)i * ld;
+                float a0 = st[i], a1 = 0.0f;
+                int cq = b0;
+                for (; cq + 2 <= b1; cq += 2) {
+                    a0 -= row[cq] * st[cq];
+                    a1 -= row[cq + 1] * st[cq + 1];
+                }
+                if (cq < b1) a0 -= row[cq] * st[cq];
+                st[i] = a0 + a1;
+            }
+            __syncthreads();
         }
+        // z = L^-T t: per panel from the last, z_I = X_II^T t_I (warp 0),
+        // then the rows above take -L_Ic^T z_I
+        for (int b0 = ((ns - 1) / CHOL_PB) * CHOL_PB; b0 >= 0; b0 -= CHOL_PB) {
+            const int b1 = min(b0 + CHOL_PB, ns);
+            if (warp == 0) {
+                const int c = b0 + lane;
+                float z = 0.0f;
+                if (c < b1) {
+                    const float *row = F + (size_t)c * ld;
+                    z = dinv[c] * st[c];
+                    for (int i = c + 1; i < b1; ++i) z += row[i] * st[i];
+                }
+                __syncwarp();
+                if (c < b1) st[c] = z;
+            }
+            __syncthreads();
+            for (int c = tid; c < b0; c += CHOL_T) {
+                float a0 = st[c], a1 = 0.0f;
+                int i = b0;
+                for (; i + 2 <= b1; i += 2) {
+                    a0 -= F[(size_t)i * ld + c] * st[i];
+                    a1 -= F[(size_t)(i + 1) * ld + c] * st[i + 1];
+                }
+                if (i < b1) a0 -= F[(size_t)i * ld + c] * st[i];
+                st[c] = a0 + a1;
+            }
+            __syncthreads();
+        }
+        for (int c = tid; c < ns; c += CHOL_T) sx[c] += (double)st[c];
         __syncthreads();
     }
     for (int k = tid; k < ns; k += CHOL_T) x[k] = sx[k];
