@@ -383,7 +383,10 @@ __device__ __forceinline__ void chol_diag_inverse(float *__restrict__ F, int ld,
     }
 }
 
-__global__ void __launch_bounds__(CHOL_T)
+// one CTA per launch: the register file is the CTA's alone, so the
+// registers a thread may take are bounded for one resident block (the
+// diagonal-block factor keeps a 32-float row per lane)
+__global__ void __launch_bounds__(CHOL_T, 1)
 chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rhs, double tol,
             int maxit, int warm, int *err) {
     // rows have an odd stride, so a warp walking a column (consecutive rows)
