@@ -9,7 +9,7 @@
 //   - the van Leer limiter, the Rusanov max and |u| take the branch of the
 //     forward evaluation;
 //   - eps~ = A~^{-1} 1 is differentiated exactly: one extra solve A~ z =
-//     dJ/deps~ with the same CG and dA~/dX from the kernel derivative.
+//     dJ/deps~ with the forward solver and dA~/dX from the kernel derivative.
 //
 // One forward step (App. B) is U1 = U + dt L(U), U* = U/2 + (U1 + dt L(U1))/2,
 // G = rho_L U_b - I[rho u], H = rho_L c_v T_w - I[rho e] (Eqs. interp,
@@ -28,8 +28,9 @@
 // adjoints of its stencil cells (ghost cells mapped to their sources, with
 // the slip flips; free-stream ghosts are constants), then chained to the
 // conserved variables cell by cell (the sums in the grid's type: FP32 grids
-// run the whole reverse sweep in FP32).  The forward states of a step are
-// recomputed from checkpoints taken every `every` steps.
+// run the reverse sweep in FP32, with the per-marker gradient accumulators
+// in FP64).  The forward states of each segment are replayed from
+// checkpoints taken every `every` steps.
 #include <math.h>
 #include <string.h>
 
