@@ -169,7 +169,7 @@ ibm_status ibm_forces_and_nusselt(ibm_grid *g, double force[3], double *heat_rat
  * App. B), under these conventions: the step sizes of the recorded run are
  * held fixed; bins, kept markers and the band do not move; the limiter and
  * the max/abs of the Rusanov flux take the branch of the forward run; the
- * weights eps~ = A~^{-1} 1 are differentiated exactly (one extra CG solve).
+ * weights eps~ = A~^{-1} 1 are differentiated exactly (one extra solve with A~).
  * Static markers only.  The forward states are recomputed from checkpoints
  * taken every `every` steps. */
 
