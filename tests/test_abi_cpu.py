@@ -36,6 +36,21 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, name), name
 
 
+def test_library_exports_nothing_the_header_does_not_declare(lib):
+    """No undeclared entry point (a debug hook, a stray helper) leaves the
+    library: its exported ibm_* text symbols are exactly the header's."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    out = subprocess.run([nm, "-D", "--defined-only", build.LIB], capture_output=True,
+                         text=True, check=True).stdout
+    exported = sorted({f[2] for f in (l.split() for l in out.splitlines())
+                       if len(f) == 3 and f[1] == "T" and f[2].startswith("ibm_")})
+    assert exported == declared_functions()
+
+
 def test_binding_covers_the_header(lib):
     assert sorted(n for n, _, _ in ibm.SIGNATURES) == declared_functions()
 
