@@ -1,7 +1,7 @@
 """CPU: bench.py's host helpers - the DRAM-traffic lookup keyed by the kernel
 source it was captured on, the clock-sample summary that decides whether a
 timed run is kept, the HBM peak lookup and the oracle's z-slab sample of the
-sphere workload."""
+sphere workload, and the reference arm on ranks other than 0."""
 import json
 import os
 import sys
@@ -108,3 +108,14 @@ def test_oracle_slab_keeps_the_sphere_markers_whose_support_fits():
         assert len(X) == int(((cz_all >= 2) & (cz_all <= want - 3)).sum())
     gs, X, _ = bench.oracle_slab(c, c.grid.n[2])
     assert len(X) == len(c.X)          # the whole grid keeps every marker
+
+
+def test_reference_arm_runs_on_rank_0_only(capsys):
+    """Under torchrun the oracle arm is timed and printed by rank 0 alone;
+    every other rank exits 0 without work or output."""
+    import argparse
+    args = argparse.Namespace(gpus=2, steps=1, warmup=1, n=256, workload="sphere",
+                              impl="reference", cpu_seconds=1.0, no_cpu_baseline=True, every=50)
+    for run in (bench.run_reference, bench.run_reference_batched):
+        assert run(args, 1, 2) == 0
+    assert capsys.readouterr().out == ""
