@@ -106,3 +106,15 @@ def test_python_binding_raises_when_library_missing(monkeypatch):
     monkeypatch.setattr(ibm, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         ibm.lib()
+
+
+def test_build_compiles_every_cuda_unit_for_sm_103a_only():
+    """A .cu file left out of the unit list would be missing from the library
+    without any error; the flags name one architecture, sm_103a."""
+    units = sorted(f for f in os.listdir(build.SRC) if f.endswith(".cu"))
+    assert sorted(build.UNITS) == units
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert set(build.UNIT_FLAGS) <= set(build.UNITS)
+    # subnormal flushing and the fast FP32 division / square root only in the
+    # units whose FP32 arithmetic was measured and parity-tested with them
+    assert set(build.UNIT_FLAGS) == {"flux.cu", "flux_zm.cu", "adjoint.cu"}
