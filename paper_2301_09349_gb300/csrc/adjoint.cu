@@ -895,13 +895,9 @@ cudaError_t rhs_vjp_t(const GridParams &g, const void *U, const void *V, void *l
     const T *u = (const T *)U, *v = (const T *)V;
     T *lamW = (T *)lamW_;
     using B = AdjBox<DIM, T>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(adj_flux_tile_kernel<DIM, T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)B::SMEM);
+    {
+        cudaError_t e = func_smem_attr((const void *)adj_flux_tile_kernel<DIM, T>, B::SMEM);
         if (e != cudaSuccess) return e;
-        configured = true;
     }
     const dim3 grid((g.n[0] + B::BX - 1) / B::BX, (g.n[1] + B::BY - 1) / B::BY,
                     DIM == 3 ? (g.n[2] + B::BZ - 1) / B::BZ : 1);

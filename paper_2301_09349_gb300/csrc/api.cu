@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/ibm.h"
+#include "device_table.h"
 #include "handle.h"
 #include "internal.h"
 
@@ -273,7 +274,25 @@ ibm_status rebuild_markers(ibm_grid *g, int warm) { return rebuild_markers(g, wa
 }  // namespace
 
 namespace ibmk {
+cudaError_t func_smem_attr(const void *func, size_t smem, int carveout) {
+    if (smem <= 48 * 1024 && carveout < 0) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    static DeviceAttrTable table;
+    const int rc = table.ensure(func, dev, smem, [&]() -> int {
+        cudaError_t r = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (r == cudaSuccess && carveout >= 0)
+            r = cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     carveout);
+        return (int)r;
+    });
+    return (cudaError_t)rc;
+}
+
 GridParams params_from_desc(const ibm_grid_desc &d) { return make_params(d); }
+const char *desc_problem(const ibm_grid_desc *d) { return check_desc(d); }
 void set_handle_free_error(const char *msg) { g_create_error = msg; }
 
 // Eq. Bulk: F_body = -h^d sum_k eps~_k F_k, Q_body = h^d sum_k eps~_k Q_k with

@@ -15,6 +15,7 @@
 // the fly), converts to primitives in shared memory, then evaluates every
 // face of the tile exactly once per direction into a shared face buffer and
 // accumulates the flux differences in registers.
+#include <atomic>
 #include <float.h>
 
 #include <type_traits>
@@ -651,14 +652,8 @@ template <int DIM, typename T, int MODE, bool SMALL>
 cudaError_t launch_box(const GridParams &g, const void *Uin, const void *Un, void *out,
                        const FluidBuffers &fb, double dt_fixed, cudaStream_t s) {
     using B = StageBox<DIM, T, SMALL>;
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(stage_kernel<DIM, T, MODE, SMALL>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)B::SMEM);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = func_smem_attr((const void *)stage_kernel<DIM, T, MODE, SMALL>, B::SMEM);
+    if (e != cudaSuccess) return e;
     stage_kernel<DIM, T, MODE, SMALL><<<stage_grid<DIM, T, SMALL>(g), NT, B::SMEM, s>>>(
         g, (const T *)Uin, (const T *)Un, (T *)out, fb.blockmax, fb.dt, fb.err, fb.band_bits,
         dt_fixed);
@@ -688,16 +683,19 @@ template <typename T, int S, int MODE>
 cudaError_t batch_stage_t(const BatchCase *cases, const int2 *items, int n_items,
                           double *item_max, double dt_fixed, int n_sm, cudaStream_t s) {
     using B = typename Shape2<T, S>::type;
-    static int per_sm = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = func_smem_attr((const void *)batch_stage_kernel<T, S, MODE>, B::SMEM);
+    if (e != cudaSuccess) return e;
+    // resident blocks per SM, per device ordinal (0: not yet asked)
+    static std::atomic<int> per_sm_of[64];
+    int per_sm = dev < 64 ? per_sm_of[dev].load() : 0;
     if (per_sm == 0) {
-        cudaError_t e = cudaFuncSetAttribute(batch_stage_kernel<T, S, MODE>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)B::SMEM);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &per_sm, batch_stage_kernel<T, S, MODE>, NT, B::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_stage_kernel<T, S, MODE>,
+                                                          NT, B::SMEM);
         if (e != cudaSuccess) return e;
         if (per_sm < 1) per_sm = 1;
+        if (dev < 64) per_sm_of[dev].store(per_sm);
     }
     long long ctas = (long long)per_sm * (n_sm > 0 ? n_sm : 1);
     if (ctas > n_items) ctas = n_items;

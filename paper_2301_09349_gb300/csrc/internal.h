@@ -9,6 +9,13 @@
 
 namespace ibmk {
 
+// Opt `func` in to `smem` bytes of dynamic shared memory on the current
+// device (and, with carveout >= 0, set its preferred shared-memory carveout
+// in percent).  Kernel attributes belong to one device, so the applied limit
+// is recorded per (kernel, device ordinal) under a mutex (api.cu); requests of
+// at most 48 KB need no opt-in and return at once.
+cudaError_t func_smem_attr(const void *func, size_t smem, int carveout = -1);
+
 // ---- fluid stages (flux.cu, flux_zm.cu) ------------------------------------
 // Stage 1: out = U1 = U + dt L(U), dt = dt_fixed if > 0 else *dt.
 // Stage 2: out = U* = Un/2 + (U1 + dt L(U1))/2; per-CTA maximum of the

@@ -987,13 +987,8 @@ template <int DIM, typename T>
 static cudaError_t interp_force_t(const GridParams &g, const void *U, const MarkerBuffers &m,
                                   int grid_ctas, cudaStream_t s) {
     const size_t smem = interp_smem<T>(g);
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && configured < smem) {
-        cudaError_t e = cudaFuncSetAttribute(interp_force_kernel<DIM, T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    cudaError_t e = func_smem_attr((const void *)interp_force_kernel<DIM, T>, smem);
+    if (e != cudaSuccess) return e;
     interp_force_kernel<DIM, T><<<grid_ctas, IF_T<DIM>, smem, s>>>(g, (const T *)U, m, m.perm[m.sorted]);
     return cudaGetLastError();
 }
@@ -1012,13 +1007,8 @@ template <int DIM, typename T>
 static cudaError_t spread_apply_t(const GridParams &g, void *U, const MarkerBuffers &m,
                                   int grid_ctas, cudaStream_t s) {
     const size_t smem = spread_smem_bytes<T>(g);
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && configured < smem) {
-        cudaError_t e = cudaFuncSetAttribute(spread_apply_kernel<DIM, T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    cudaError_t e = func_smem_attr((const void *)spread_apply_kernel<DIM, T>, smem);
+    if (e != cudaSuccess) return e;
     spread_apply_kernel<DIM, T><<<grid_ctas, SP_T<DIM>, smem, s>>>(g, (T *)U, m, m.keys[m.sorted],
                                                                 m.perm[m.sorted]);
     return cudaGetLastError();
@@ -1059,13 +1049,8 @@ size_t batch_spread_smem(const GridParams &g, int fp_bytes) {
 template <typename T>
 static cudaError_t batch_spread_t(size_t smem, const BatchCase *cases, const int2 *items,
                                   int n_items, double *band_max, int ctas, cudaStream_t s) {
-    static size_t configured = 0;
-    if (smem > 48 * 1024 && configured < smem) {
-        cudaError_t e = cudaFuncSetAttribute(batch_spread_kernel<2, T>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    cudaError_t e = func_smem_attr((const void *)batch_spread_kernel<2, T>, smem);
+    if (e != cudaSuccess) return e;
     batch_spread_kernel<2, T><<<ctas, SP_T<2>, smem, s>>>(cases, items, n_items, band_max);
     return cudaGetLastError();
 }

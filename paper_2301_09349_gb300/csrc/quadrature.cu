@@ -538,14 +538,8 @@ static cudaError_t launch_quadrature_solve_w(int ns, const QuadBuffers &qb, cons
                                             cudaStream_t s) {
     if (ns <= 0) return cudaSuccess;
     if (ns <= CHOL_MAX) {
-        static bool configured = false;
-        if (!configured) {
-            cudaError_t e = cudaFuncSetAttribute(chol_kernel,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)chol_smem(CHOL_MAX));
-            if (e != cudaSuccess) return e;
-            configured = true;
-        }
+        cudaError_t e = func_smem_attr((const void *)chol_kernel, chol_smem(CHOL_MAX));
+        if (e != cudaSuccess) return e;
         chol_kernel<<<1, CHOL_T, chol_smem(ns), s>>>(ns, qb, x, rhs, tol, maxit, warm, err);
     } else if (ns <= 2048) {
         pcg_kernel<256><<<1, 256, 0, s>>>(ns, qb, x, rhs, tol, maxit, warm, err);
