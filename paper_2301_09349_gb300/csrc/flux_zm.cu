@@ -420,15 +420,25 @@ zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, cons
     const unsigned mbar = smem_u32(stage + STAGE);
     unsigned parity = 0;
     const int nz = g.n[2];
-    // a copy that never completes switches the CTA to thread loads; the
-    // phase still outstanding is drained (bounded) before the CTA exits
+    // A copy that does not complete within the bounded wait switches the CTA
+    // to thread loads.  Each thread decides for the cells it converts: a
+    // thread whose wait gave up loads its own cells of the plane from global
+    // memory, one whose wait completed converts the staged copy; both give
+    // the same values, so threads may decide differently within one plane.
+    // The shared flag only stops further copies; thread 0 reads it after the
+    // plane's barrier.  Thread 0 tracks the copy it issued last and, if it
+    // never saw that copy complete, drains it (bounded) before the CTA exits.
     __shared__ int s_tma_dead;
-    int pending = -1;
+    volatile int *tma_dead = &s_tma_dead;
+    bool outstanding = false;   // thread 0 only
     if (TMA) {
         if (tid == 0) {
-            s_tma_dead = 0;
+            *tma_dead = 0;
             mbar_init(mbar);
-            if (z0 + 2 < nz) tma_issue(&tmap, st_addr, mbar, ox - 4, oy - 2, z0 + 2);
+            if (z0 + 2 < nz) {
+                tma_issue(&tmap, st_addr, mbar, ox - 4, oy - 2, z0 + 2);
+                outstanding = true;
+            }
         }
         __syncthreads();
     }
@@ -462,20 +472,23 @@ zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, cons
     float smaxf = 0.0f;
     bool ok = true;
     for (int z = z0; z < z1; ++z) {
-        const bool staged = TMA && z + 2 < nz && !s_tma_dead;
-        if (staged && !tma_wait(mbar, parity, err)) {
-            s_tma_dead = 1;
-            if (tid == 0) pending = (int)parity;
+        bool use_stage = TMA && z + 2 < nz && !*tma_dead;
+        if (use_stage && !tma_wait(mbar, parity, err)) {
+            use_stage = false;
+            *tma_dead = 1;
         }
-        if (staged && !s_tma_dead) {
+        if (use_stage) {
             parity ^= 1u;
+            if (tid == 0) outstanding = false;
             convert_staged(g, c, Uin, stage, ring + slot_of(z + 2), ox, oy, z + 2, xyint);
         } else {
             load_plane(g, c, Uin, ring + slot_of(z + 2), ox, oy, z + 2, xyint);
         }
         __syncthreads();
-        if (TMA && tid == 0 && !s_tma_dead && z + 1 < z1 && z + 3 < nz)
+        if (TMA && tid == 0 && !*tma_dead && z + 1 < z1 && z + 3 < nz) {
             tma_issue(&tmap, st_addr, mbar, ox - 4, oy - 2, z + 3);
+            outstanding = true;
+        }
 #if IBM_ZM_PREFETCH
         // stage 2 reads U^n at its output cells, which nothing has touched:
         // start those lines toward L2 two planes ahead
@@ -568,7 +581,9 @@ zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, cons
         }
     }
 
-    if (TMA && tid == 0 && pending >= 0) tma_wait(mbar, (unsigned)pending, err);
+    // thread 0 flips its parity only on copies it saw complete, so `parity`
+    // is the phase of a copy still outstanding
+    if (TMA && tid == 0 && outstanding) tma_wait(mbar, parity, err);
 
     if (MODE == 2) {
         const double smax = warp_max_d((double)smaxf);
@@ -602,18 +617,17 @@ size_t zmarch_blocks(const GridParams &g) {
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point
+// (a driver function, the same for every device; resolved once, thread-safe)
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static bool tried = false;
-    if (!tried) {
-        tried = true;
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
                                              &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
-    }
+            return (PFN_cuTensorMapEncodeTiled_v12000)p;
+        return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }();
     return fn;
 }
 
@@ -636,16 +650,8 @@ template <int MODE, bool TMA>
 static cudaError_t zm_launch_t(const GridParams &g, const CUtensorMap &map, const void *Uin,
                                const void *Un, void *out, const FluidBuffers &fb, double dt_fixed,
                                cudaStream_t s) {
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(zmarch_kernel<MODE, TMA>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(zmarch_kernel<MODE, TMA>,
-                                     cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    cudaError_t e = func_smem_attr((const void *)zmarch_kernel<MODE, TMA>, SMEM, 100);
+    if (e != cudaSuccess) return e;
     const int zc = zmarch_chunk(g);
     dim3 grid((g.n[0] + TX - 1) / TX, (g.n[1] + TY - 1) / TY, (g.n[2] + zc - 1) / zc);
     zmarch_kernel<MODE, TMA><<<grid, NTH, SMEM, s>>>(map, g, make_fc(g), zc, (const float *)Uin,
