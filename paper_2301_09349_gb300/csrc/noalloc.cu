@@ -20,6 +20,7 @@
 
 namespace ibmk {
 GridParams params_from_desc(const ibm_grid_desc &d);
+const char *desc_problem(const ibm_grid_desc *d);
 void set_handle_free_error(const char *msg);
 }  // namespace ibmk
 
@@ -66,8 +67,7 @@ ibm_status fail(ibm_status st, const char *msg) {
 
 extern "C" ibm_status ibm_rhs_dt_noalloc(const ibm_grid_desc *desc, const void *U, void *L,
                                          double *dt, void *stream) {
-    if (!desc || ibm_workspace_bytes(desc, 0) == 0)
-        return fail(IBM_ERR_ARG, "invalid grid description");
+    if (const char *why = desc_problem(desc)) return fail(IBM_ERR_ARG, why);
     if (!U || !L || !dt) return fail(IBM_ERR_ARG, "null buffer");
     const GridParams g = params_from_desc(*desc);
     const size_t ctas = dt_init_blocks(g);
@@ -92,5 +92,6 @@ extern "C" ibm_status ibm_rhs_dt_noalloc(const ibm_grid_desc *desc, const void *
     if (e == cudaSuccess) e = launch_rhs(g, desc->fp_bytes, U, L, fb, s);
     if (e == cudaSuccess) e = launch_dt_init(g, desc->fp_bytes, U, fb, s);
     if (e != cudaSuccess) return fail(IBM_ERR_CUDA, cudaGetErrorString(e));
+    set_handle_free_error("");   // no stale message after a successful call
     return IBM_OK;
 }
