@@ -13,6 +13,11 @@ With N > 1 (torchrun, one process per GPU) every rank runs its own
 independent sphere case (Mach x wall-temperature variants): weak scaling,
 no collective on the data path.  Rank 0 prints one JSON line.
 
+At N = 1 the sphere line also carries two short passes of the other forms
+on the same GPU (skip with --no-extras): "batched" (20 steps of the 64-case
+batch against the plain per-case loop) and "adjoint" (50 recorded steps of
+the 128^3 sphere, checkpoint every 10, reversed by ibm_backward).
+
 --impl reference times the FP64 CPU oracle on this host's cores on a slab
 sample of the same workload (rank 0 only).
 
@@ -60,6 +65,8 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target seconds of oracle work for the cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="sphere line without the short batched and adjoint passes")
     p.add_argument("--workload", default="sphere",
                    choices=["sphere", "batched", "adjoint", "cylinders"])
     p.add_argument("--every", type=int, default=50, help="adjoint checkpoint interval")
@@ -352,6 +359,12 @@ def run_ours(args, rank, world, local):
             "clocks": clk,
             "result": {"Cd": res["Cd"], "Cl": res["Cl"], "Nu": res["Nu"]},
         }
+        if world == 1 and not args.no_extras:
+            # the batched and adjoint forms, timed briefly on the same GPU so
+            # that every run of the default line carries them
+            grid.close()
+            line["batched"] = extra_batched(20, 3, gpu_id)
+            line["adjoint"] = extra_adjoint(50, 10, gpu_id)
         if world == 1 and not args.no_cpu_baseline:
             threads = os.cpu_count() or 1
             rate, det = oracle_rate(c, args.cpu_seconds, 1, 0, threads)
@@ -431,6 +444,95 @@ def run_reference_batched(args, rank, world):
     return 0
 
 
+def batch_and_loop(cs, stream, steps, warmup, barrier, tune_reps, gpu_id=None, profile=False):
+    """Set up the cases as one batch (autotuned), time `steps` batched steps,
+    then the plain per-case loop of single-grid steps on the same cases.
+    Returns the batch (still open), both times in ms, the kept marker counts,
+    the tuning, the kernel split (profile=True) and the clock samples taken
+    during the batched steps (gpu_id given)."""
+    import torch
+    from paper_2301_09349_gb300 import ibm
+    b = ibm.Batch([c.grid for c in cs], [len(c.X) for c in cs], stream=stream)
+    kept = []
+    for cg, c in zip(b.cases, cs):
+        kept.append(cg.set_markers(c.X, c.Tw))
+        cg.set_state(C.initial_state(c.grid, c.seed).astype(np.float32))
+    tune_ms = b.autotune(reps=tune_reps)
+    tuning = b.tuning()
+
+    def timed(fn, k):
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return e0.elapsed_time(e1)
+
+    b.step(warmup)
+    b.sync()
+    clocks = ClockSampler(gpu_id) if gpu_id else None
+    if clocks is not None:
+        time.sleep(0.3)
+    ms = timed(b.step, steps)
+    clk = clocks.stop() if clocks is not None else None
+    b.sync()
+
+    prof = None
+    if profile:
+        # the same steps launched kernel by kernel with event pairs: the split
+        ibm.ibm_batch_profile(b.h, True)
+        b.step(steps)
+        prof = ibm.ibm_batch_profile_read(b.h)
+        ibm.ibm_batch_profile(b.h, False)
+        b.sync()
+
+    # the plain per-case loop: one single-grid step per case per step
+    loop = []
+    for c in cs:
+        gr = ibm.Grid(c.grid, max_markers=len(c.X), stream=stream)
+        gr.set_markers(c.X, c.Tw)
+        gr.set_state(C.initial_state(c.grid, c.seed).astype(np.float32))
+        loop.append(gr)
+
+    def loop_steps(k):
+        for _ in range(k):
+            for gr in loop:
+                gr.step(1)
+
+    loop_steps(warmup)
+    ms_loop = timed(loop_steps, steps)
+    for gr in loop:
+        gr.sync()
+    for gr in loop:
+        gr.close()
+    return {"batch": b, "ms": ms, "ms_loop": ms_loop, "kept": kept, "tune_ms": tune_ms,
+            "tuning": tuning, "prof": prof, "clocks": clk}
+
+
+def extra_batched(steps: int, warmup: int, gpu_id: str):
+    """Short pass of the 64-case batch beside the sphere line: batched step
+    against the plain per-case loop, same GPU, same cases."""
+    import torch
+    cs = C.batched_cylinders()
+    stream = torch.cuda.Stream()
+    bm = batch_and_loop(cs, stream, steps, warmup, lambda: None, tune_reps=3, gpu_id=gpu_id)
+    bm["batch"].close()
+    N = float(sum(c.grid.ncells for c in cs))
+    return {"workload": batch_workload_name(cs), "steps": steps, "warmup": warmup,
+            "tuning": bm["tuning"],
+            "batched_ms_per_step": bm["ms"] / steps,
+            "per_case_loop_ms_per_step": bm["ms_loop"] / steps,
+            "speedup_of_batch": bm["ms_loop"] / bm["ms"],
+            "batched_cell_updates_per_s": N * steps / (bm["ms"] * 1e-3),
+            "per_case_loop_cell_updates_per_s": N * steps / (bm["ms_loop"] * 1e-3),
+            "timing": "CUDA events on the batch's stream around each loop of steps",
+            "clocks": bm["clocks"]}
+
+
 def run_batched(args, rank, world, local):
     import torch
     from paper_2301_09349_gb300 import build, ibm
@@ -447,63 +549,14 @@ def run_batched(args, rank, world, local):
 
     cs = batch_cases(rank, world)
     stream = torch.cuda.Stream()
-    b = ibm.Batch([c.grid for c in cs], [len(c.X) for c in cs], stream=stream)
-    kept = []
-    for cg, c in zip(b.cases, cs):
-        kept.append(cg.set_markers(c.X, c.Tw))
-        cg.set_state(C.initial_state(c.grid, c.seed).astype(np.float32))
-    N = float(sum(c.grid.ncells for c in cs))
-    tune_ms = b.autotune(reps=10)
-    tuning = b.tuning()
-
-    def timed(fn, steps):
-        barrier()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        fn(steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        return e0.elapsed_time(e1)
-
-    b.step(args.warmup)
-    b.sync()
     uuid = str(torch.cuda.get_device_properties(local).uuid)
     gpu_id = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
-    clocks = ClockSampler(gpu_id)
-    time.sleep(0.3)
-    ms = timed(b.step, args.steps)
-    clk = clocks.stop()
-    b.sync()
-
-    # the same steps launched kernel by kernel with event pairs: the split
-    ibm.ibm_batch_profile(b.h, True)
-    b.step(args.steps)
-    prof = ibm.ibm_batch_profile_read(b.h)
-    ibm.ibm_batch_profile(b.h, False)
-    b.sync()
-
-    # the plain per-case loop: one single-grid step per case per step
-    loop = []
-    for c in cs:
-        gr = ibm.Grid(c.grid, max_markers=len(c.X), stream=stream)
-        gr.set_markers(c.X, c.Tw)
-        gr.set_state(C.initial_state(c.grid, c.seed).astype(np.float32))
-        loop.append(gr)
-
-    def loop_steps(k):
-        for _ in range(k):
-            for gr in loop:
-                gr.step(1)
-
-    loop_steps(args.warmup)
-    ms_loop = timed(loop_steps, args.steps)
-    for gr in loop:
-        gr.sync()
-    for gr in loop:
-        gr.close()
+    bm = batch_and_loop(cs, stream, args.steps, args.warmup, barrier, tune_reps=10,
+                        gpu_id=gpu_id, profile=True)
+    b, ms, ms_loop, kept, tune_ms, tuning, prof, clk = (
+        bm["batch"], bm["ms"], bm["ms_loop"], bm["kept"], bm["tune_ms"], bm["tuning"],
+        bm["prof"], bm["clocks"])
+    N = float(sum(c.grid.ncells for c in cs))
 
     # end to end through the C ABI with host buffers: per step the wall
     # temperatures of every case go up from page-locked memory in one copy,
@@ -608,30 +661,13 @@ def run_adjoint(args, rank, world, local):
     torch.cuda.set_device(local)
     if rank != 0:
         return 0
-    c = C.adjoint_sphere()
-    g = c.grid
-    stream = torch.cuda.Stream()
-    grid = ibm.Grid(g, max_markers=len(c.X), stream=stream)
-    n_kept = grid.set_markers(c.X, c.Tw)
-    grid.set_state(C.initial_state(g, c.seed).astype(np.float32))
-    S = args.steps
-    grid.record(S, args.every)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    grid.step(S)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    fwd_ms = e0.elapsed_time(e1)
-    f = grid.forces()
     uuid = str(torch.cuda.get_device_properties(local).uuid)
-    clocks = ClockSampler(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
-    time.sleep(0.3)
-    t0 = time.perf_counter()
-    gX, gT = grid.backward(1.0, 1.0)        # synchronizing
-    bwd_s = time.perf_counter() - t0
-    clk = clocks.stop()
-    N = g.ncells
+    am = adjoint_measure(args.steps, args.every, "GPU-" + uuid if not uuid.startswith("GPU-")
+                         else uuid)
+    c, n_kept, S, fwd_ms, bwd_s, f, gX, gT, clk = (
+        am["case"], am["n_kept"], am["steps"], am["fwd_ms"], am["bwd_s"], am["forces"],
+        am["gX"], am["gT"], am["clocks"])
+    N = c.grid.ncells
     line = {
         "metric": ADJ_METRIC, "value": N * S / bwd_s, "unit": UNIT, "n_gpus": 1,
         "steps": S, "warmup": 0, "ms_per_step": 1e3 * bwd_s / S, "higher_is_better": True,
@@ -648,8 +684,56 @@ def run_adjoint(args, rank, world, local):
         "timing": "host wall clock around the synchronizing ibm_backward call",
     }
     print(json.dumps(line), flush=True)
-    grid.close()
     return 0
+
+
+def adjoint_measure(S: int, every: int, gpu_id=None):
+    """Record S steps of the 128^3 adjoint sphere (checkpoint every `every`),
+    then time ibm_backward over all of them (host wall clock around the
+    synchronizing call)."""
+    import torch
+    from paper_2301_09349_gb300 import ibm
+    c = C.adjoint_sphere()
+    g = c.grid
+    stream = torch.cuda.Stream()
+    grid = ibm.Grid(g, max_markers=len(c.X), stream=stream)
+    n_kept = grid.set_markers(c.X, c.Tw)
+    grid.set_state(C.initial_state(g, c.seed).astype(np.float32))
+    grid.record(S, every)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    grid.step(S)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = e0.elapsed_time(e1)
+    f = grid.forces()
+    clocks = ClockSampler(gpu_id) if gpu_id else None
+    if clocks is not None:
+        time.sleep(0.3)
+    t0 = time.perf_counter()
+    gX, gT = grid.backward(1.0, 1.0)        # synchronizing
+    bwd_s = time.perf_counter() - t0
+    clk = clocks.stop() if clocks is not None else None
+    grid.close()
+    return {"case": c, "n_kept": n_kept, "steps": S, "every": every, "fwd_ms": fwd_ms,
+            "bwd_s": bwd_s, "forces": f, "gX": gX, "gT": gT, "clocks": clk}
+
+
+def extra_adjoint(S: int, every: int, gpu_id: str):
+    """Short adjoint pass beside the sphere line."""
+    am = adjoint_measure(S, every, gpu_id)
+    c = am["case"]
+    N = c.grid.ncells
+    return {"workload": "3D sphere 128^3 FP32, Ma 0.5, Re 100, T_w 1.5, %d markers (%d kept), "
+                        "%d recorded steps, checkpoint every %d"
+                        % (len(c.X), am["n_kept"], S, every),
+            "reversed_ms_per_step": 1e3 * am["bwd_s"] / S,
+            "forward_ms_per_step_recording": am["fwd_ms"] / S,
+            "backward_over_forward": 1e3 * am["bwd_s"] / am["fwd_ms"],
+            "reversed_cell_steps_per_s": N * S / am["bwd_s"],
+            "timing": "host wall clock around the synchronizing ibm_backward call",
+            "clocks": am["clocks"]}
 
 
 # ---------------------------------------------------------------------------
