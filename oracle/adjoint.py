@@ -38,6 +38,10 @@ from . import oracle as O
 
 _F64 = torch.float64
 
+# largest fraction of a forced cell's internal energy the heat source removes
+# in one step (the C oracle's HEAT_SOURCE_CAP)
+HEAT_SOURCE_CAP = 0.9
+
 
 # ---------------------------------------------------------------------------
 # grid bookkeeping (integer index maps, no arithmetic of the method)
@@ -321,6 +325,10 @@ def spread_apply(g, sup, Phi, eps, G, H, U, energy_reading=0):
     m1 = m0 + r[:dim]
     E = U[dim + 1]
     q = r[dim]
+    # positivity reading of the forced update: the heat source removes at
+    # most HEAT_SOURCE_CAP of the cell's internal energy in one step
+    rhoe0 = E - 0.5 * (m0 * m0).sum(0) / rho
+    q = torch.maximum(q, -HEAT_SOURCE_CAP * rhoe0)
     if energy_reading == 1:
         En = E + q
     else:

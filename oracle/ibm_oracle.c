@@ -25,6 +25,10 @@
  */
 #include "ibm_oracle.h"
 
+/* Largest fraction of a forced cell's internal energy the heat source may
+ * remove in one step (positivity reading of the forced update). */
+#define HEAT_SOURCE_CAP 0.9
+
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -740,6 +744,12 @@ void or_spread_apply(const or_desc *g, int ns, const double *X, const double *ep
         }
         double E = U[(long)(dim + 1) * N + j];
         double q = r[(long)dim * N + j];
+        /* positivity reading (the paper is silent): the heat source removes
+         * at most HEAT_SOURCE_CAP of the cell's internal energy in one step,
+         * dt q >= -HEAT_SOURCE_CAP rho e*.  Inactive unless a cold wall
+         * would otherwise drive a forced cell to non-positive pressure. */
+        double rhoe0 = E - 0.5 * ke0 / rho;
+        if (q < -HEAT_SOURCE_CAP * rhoe0) q = -HEAT_SOURCE_CAP * rhoe0;
         if (g->energy_reading == 1)
             U[(long)(dim + 1) * N + j] = E + q;
         else

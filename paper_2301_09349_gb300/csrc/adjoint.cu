@@ -642,6 +642,15 @@ adj_apply_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__re
         const T irho = T(1) / Us[j];
         const T lE = lam[(DIM + 1) * N + j];
         const T lEr = lE * irho;
+        // the heat-source cap of the forward update: where it binds, q is
+        // replaced by -cap (rho e)* = -cap (E* - |m*|^2 / (2 rho)), so the
+        // adjoint of q is 0 and E*, m* and rho receive the cap's terms
+        T ke0 = T(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) ke0 += Us[(1 + d) * N + j] * Us[(1 + d) * N + j];
+        const T cap = (T)kHeatSourceCap;
+        const bool act = q < -cap * (Us[(DIM + 1) * N + j] - T(0.5) * ke0 * irho);
+        const T a = act ? cap : T(0);
         T dk = T(0);   // |m1|^2 - |m0|^2
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
@@ -651,13 +660,18 @@ adj_apply_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__re
             dk += f[d] * (ms + m1);
             if (g.energy_reading == 1) {
                 lfq[d * N + j] = lm;
+                if (act) lam[(1 + d) * N + j] = lm + lEr * a * ms;
             } else {
                 lfq[d * N + j] = lm + lEr * m1;
-                lam[(1 + d) * N + j] = lm + lEr * f[d];
+                lam[(1 + d) * N + j] = lm + lEr * (f[d] + a * ms);
             }
         }
-        lfq[DIM * N + j] = lE;
-        if (g.energy_reading != 1) lam[j] = lam[j] - T(0.5) * lEr * irho * dk;
+        lfq[DIM * N + j] = act ? T(0) : lE;
+        if (g.energy_reading != 1)
+            lam[j] = lam[j] - T(0.5) * lEr * irho * (dk + a * ke0);
+        else if (act)
+            lam[j] = lam[j] - T(0.5) * lEr * irho * a * ke0;
+        if (act) lam[(DIM + 1) * N + j] = lE * (T(1) - a);
     });
 }
 

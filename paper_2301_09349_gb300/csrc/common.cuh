@@ -21,6 +21,13 @@ enum : int {
 
 enum : int { BC_FREESTREAM = 0, BC_ZEROGRAD = 1, BC_SLIP = 2, BC_PERIODIC = 3 };
 
+// Positivity reading of the forced update (the paper is silent on it): the
+// heat source of one step removes at most this fraction of a forced cell's
+// internal energy, dt q_j >= -0.9 (rho e)*_j.  It never binds in the Mach 0.3
+// cases or with a hot wall; it keeps the pressure positive when a cold wall
+// meets an impulsive Mach 2 start.
+constexpr double kHeatSourceCap = 0.9;
+
 // Single-precision copies of the gas and grid constants, each rounded once
 // from its double value on the host, for kernels that compute in FP32
 // (double arithmetic runs at a small fraction of the FP32 rate on this GPU,

@@ -406,22 +406,26 @@ size_t spread_smem_bytes(const GridParams &g) {
 // Forced update of one band cell (App. B, Eqs. u_centralF2 and e_centralF2;
 // f.u dropped): momentum += dt f, internal energy += dt q, rho unchanged, so
 // rho E gains dt q + (|m1|^2 - |m0|^2) / (2 rho), the difference taken as
-// sum_d f_d (m0_d + m1_d) (no cancellation).  In the spreading precision R
-// (the field precision).
+// sum_d f_d (m0_d + m1_d) (no cancellation).  The heat source is capped at
+// kHeatSourceCap of the cell's internal energy (positivity reading).  In the
+// spreading precision R (the field precision).
 template <int DIM, typename T, typename R>
 __device__ __forceinline__ void apply_forcing(const GridParams &g, T *__restrict__ U, long long j,
                                               const R *f, R qh) {
     const long long N = g.N;
     const R rho = (R)U[j];
-    R dke = R(0);
+    R dke = R(0), ke0 = R(0);
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
         const R m0 = (R)U[(1 + d) * N + j];
         const R m1 = m0 + f[d];
         dke += f[d] * (m0 + m1);
+        ke0 += m0 * m0;
         U[(1 + d) * N + j] = (T)m1;
     }
     const R E = (R)U[(DIM + 1) * N + j];
+    const R qmin = -(R)kHeatSourceCap * (E - R(0.5) * ke0 / rho);
+    if (qh < qmin) qh = qmin;
     const R En = g.energy_reading == 1 ? E + qh : E + (qh + R(0.5) * dke / rho);
     U[(DIM + 1) * N + j] = (T)En;
 }

@@ -130,6 +130,17 @@ def test_backward_fp64_2d_many_steps_with_checkpoints():
     compare(g, X, Tw, seed, steps=12, every=5, a=1.0, b=0.2, tol=1e-7)
 
 
+@pytest.mark.parametrize("energy_reading", [0, 1])
+def test_backward_fp64_2d_with_the_heat_source_cap(energy_reading):
+    """A cold wall (T_w 0.25-0.35 at Mach 0.3) whose cooling the heat-source
+    cap limits in a dozen forced cells (counted in the oracle's pins): the
+    reverse of the capped update against the oracle's autograd."""
+    g, X, _, seed = cylinder(8)
+    Tw = np.linspace(0.25, 0.35, len(X))
+    compare(g, X, Tw, seed, steps=3, every=2, a=1.0, b=0.3, tol=1e-7,
+            energy_reading=energy_reading)
+
+
 def test_backward_fp64_3d_matches_oracle(oracle):
     g = C.small_grid(3, (12, 12, 12), h=0.125, fp_bytes=8, Re=80.0, Mach=0.4)
     X = C.fibonacci_sphere_markers(120, 0.4)

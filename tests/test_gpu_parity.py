@@ -250,42 +250,66 @@ def test_sphere_fp32_per_step(oracle):
 
 
 def test_supersonic_cold_sphere_fp32(oracle):
-    # an impulsive Mach-2 start against a cold wall drives a forced cell to
-    # non-positive pressure at step 5 in the oracle as well (the fluid inside
-    # the body starts at Mach 2); compare the physical first three steps
+    """The impulsive Mach 2 start against a cold wall (T_w = 0.5), whose
+    forced cells need the heat-source cap in their first steps: 100 steps
+    compared step by step, the oracle at the GPU's step size."""
     c = C.heated_sphere(n=48, mach=2.0, Tw=0.5)
-    _compare_run(oracle, c, 3, 1e-5, tol_force=1e-3)
+    _compare_run(oracle, c, 100, 1e-5, tol_force=1e-3)
 
 
 def test_supersonic_hot_sphere_fp32(oracle):
     c = C.heated_sphere(n=48, mach=2.0, Tw=1.5)
-    _compare_run(oracle, c, 5, 1e-5, tol_force=1e-3)
+    _compare_run(oracle, c, 100, 1e-5, tol_force=1e-3)
 
 
-def test_nonpositive_state_is_reported_like_the_oracle(oracle):
-    # the same cold Mach-2 start, run past step 5: the GPU reports
-    # IBM_ERR_NONFINITE exactly when the oracle's pressure turns non-positive
+def test_supersonic_cold_sphere_1000_steps(oracle):
+    """The cold-wall Mach 2 sphere at 48^3 over 1000 steps, each side on its
+    own step sizes and weights: finite and within the long-run gate."""
     c = C.heated_sphere(n=48, mach=2.0, Tw=0.5)
-    g = c.grid
-    run = oracle.Run(g, c.X, c.Tw)
-    U = C.initial_state(g, c.seed).astype(np.float32).astype(np.float64).reshape(5, -1)
-    first_bad = None
-    for s in range(8):
-        U = run.step(U)
+    errs = _independent_run(oracle, c, 1000, 250)
+    for done, err, tg, to in errs:
+        assert np.all(err < 1e-3), (done, err)
+
+
+@pytest.mark.parametrize("ub,fails", [(2.3, False), (2.4, True)])
+def test_nonpositive_state_is_reported_like_the_oracle(oracle, ub, fails):
+    """Energy reading B (the heat source on total energy) with a body moving
+    impulsively through gas at rest: the momentum forcing adds kinetic
+    energy that reading B does not pay for, so fast enough a body drives
+    its forced cells to non-positive pressure.  The oracle fails at body
+    speed 2.4 (Mach 1.2) in the first step and stays positive for 30 steps
+    at 2.3; the GPU reports IBM_ERR_NONFINITE exactly in the first case."""
+    g = C.small_grid(3, (24, 24, 24), h=0.125, fp_bytes=4, bc=(C.BC_PERIODIC,) * 6, Mach=0.5,
+                     Re=100.0)
+    X = C.fibonacci_sphere_markers(200, radius=0.8)
+    Ub = np.zeros_like(X)
+    Ub[:, 0] = ub
+    U0 = np.zeros(g.shape())
+    U0[0] = 1.0
+    U0[-1] = 1.0 / (g.gamma * g.Mach ** 2) / (g.gamma - 1.0)
+    U0 = U0.astype(np.float32)
+    run = oracle.Run(g, X, np.ones(len(X)), Ub_in=Ub, energy_reading=1)
+    U = U0.astype(np.float64)
+    bad = []
+    for s in range(30):
+        U = run.step(U).reshape(5, -1)
         p = 0.4 * (U[4] - 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0])
-        if not np.all(p > 0):
-            first_bad = s
+        if not (np.all(p > 0) and np.all(U[0] > 0)):
+            bad.append(s)
             break
-    assert first_bad is not None
-    grid = ibm.Grid(g, max_markers=len(c.X))
-    grid.set_markers(c.X, c.Tw)
-    grid.set_state(C.initial_state(g, c.seed).astype(np.float32))
-    grid.step(first_bad)
-    grid.sync()
-    grid.step(1)
-    with pytest.raises(ibm.IbmError) as e:
+    assert bad == ([0] if fails else [])
+    grid = ibm.Grid(g, max_markers=len(X), energy_reading=1)
+    grid.set_markers(X, np.ones(len(X)), Ub=Ub)
+    grid.set_state(U0)
+    if fails:
+        grid.step(1)
+        with pytest.raises(ibm.IbmError) as e:
+            grid.sync()
+        assert e.value.status == 3
+    else:
+        grid.step(30)
         grid.sync()
-    assert e.value.status == 3
+    grid.close()
 
 
 def test_moving_cylinder_fp32(oracle):

@@ -122,3 +122,40 @@ def test_gradient_matches_central_differences_3d(oracle):
     U0 = C.initial_state(g, 9)
     dt = oracle.dt(g, U0)
     _fd_check(oracle, g, X, Tw, U0, [dt, dt], 0.5, 1.0, 6, 4)
+
+
+def _capped_cells(oracle, g, X, Tw, U0):
+    """cells whose heat source the cap limits in the first step"""
+    run = oracle.Run(g, X, Tw, dedup_markers=False)
+    _, Us = oracle.predictor(g, U0)
+    Un = run.step(U0)
+    nc = g.ncomp
+
+    def internal(U):
+        U = U.reshape(nc, -1)
+        return U[-1] - 0.5 * (U[1:nc - 1] ** 2).sum(0) / U[0]
+    return int(np.sum(np.isclose(internal(Un) / internal(Us), 0.1, rtol=1e-12)))
+
+
+@pytest.mark.parametrize("energy_reading", [0, 1])
+def test_forward_and_gradient_with_the_heat_source_cap(oracle, energy_reading):
+    """A cold wall (T_w 0.25-0.35 at Mach 0.3) whose cooling the heat-source
+    cap limits in a dozen forced cells: the torch restatement equals the C
+    oracle's states, and its gradient equals central differences of the C
+    oracle's J (the cap is a max, differentiated on its branch)."""
+    g, X, _, seed = cyl_case()
+    X = kept(oracle, g, X)
+    Tw = np.linspace(0.25, 0.35, len(X))
+    U0 = C.initial_state(g, seed)
+    assert _capped_cells(oracle, g, X, Tw, U0) >= 10
+    dt = oracle.dt(g, U0)
+    U, G, H, eps = A.run(g, torch.tensor(X), torch.tensor(Tw), U0, [dt, dt],
+                         energy_reading=energy_reading)
+    Uc = U0
+    for _ in range(2):
+        _, Uc, _, _, _ = oracle.step(g, X, None, Tw, eps.detach().numpy(), Uc, dt_fixed=dt,
+                                     energy_reading=energy_reading)
+    Ut = U.detach().numpy().reshape(Uc.shape)
+    assert np.linalg.norm(Ut - Uc) / np.linalg.norm(Uc) < 1e-13
+    if energy_reading == 0:
+        _fd_check(oracle, g, X, Tw, U0, [dt, dt], 1.0, 0.3, 8, 7)
