@@ -738,13 +738,49 @@ __device__ __forceinline__ void finish_grid(const GridParams &g, int ns, const M
                                             double dt_fixed, double (*s)[FIN_T / 32]) {
     const int dim = g.dim;
     double a[5] = {0, 0, 0, 0, 0};   // sums of eps~ G (dim), eps~ H; a[4] = max rate
-    for (int k = threadIdx.x; k < ns; k += FIN_T) {
-        const double e = __ldg(m.eps + k);
-        for (int d = 0; d < dim; ++d) a[d] += e * __ldg(m.G + (long long)k * dim + d);
-        a[3] += e * __ldg(m.H + k);
+    // markers k = tid, tid + FIN_T, ... summed in that order; the loads of
+    // FIN_B of them are issued together, so the latency is paid once per
+    // batch rather than once per marker
+    constexpr int FIN_B = 4;
+    for (int k0 = threadIdx.x; k0 < ns; k0 += FIN_B * FIN_T) {
+        double e[FIN_B], gq[FIN_B][4];
+#pragma unroll
+        for (int i = 0; i < FIN_B; ++i) {
+            const int k = k0 + i * FIN_T;
+            e[i] = 0.0;
+            gq[i][0] = gq[i][1] = gq[i][2] = gq[i][3] = 0.0;
+            if (k < ns) {
+                e[i] = __ldg(m.eps + k);
+#pragma unroll
+                for (int d = 0; d < 3; ++d)
+                    if (d < dim) gq[i][d] = __ldg(m.G + (long long)k * dim + d);
+                gq[i][3] = __ldg(m.H + k);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < FIN_B; ++i) {
+            if (k0 + i * FIN_T >= ns) break;
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+                if (d < dim) a[d] += e[i] * gq[i][d];
+            a[3] += e[i] * gq[i][3];
+        }
     }
-    for (int b = threadIdx.x; b < nb; b += FIN_T) a[4] = fmax(a[4], __ldg(blockmax + b));
-    for (int b = threadIdx.x; b < nbs; b += FIN_T) a[4] = fmax(a[4], __ldg(bandmax + b));
+    // maxima: the order does not matter
+    for (int b = threadIdx.x; b < nb; b += FIN_B * FIN_T) {
+        double v[FIN_B];
+#pragma unroll
+        for (int i = 0; i < FIN_B; ++i) v[i] = b + i * FIN_T < nb ? __ldg(blockmax + b + i * FIN_T) : 0.0;
+#pragma unroll
+        for (int i = 0; i < FIN_B; ++i) a[4] = fmax(a[4], v[i]);
+    }
+    for (int b = threadIdx.x; b < nbs; b += FIN_B * FIN_T) {
+        double v[FIN_B];
+#pragma unroll
+        for (int i = 0; i < FIN_B; ++i) v[i] = b + i * FIN_T < nbs ? __ldg(bandmax + b + i * FIN_T) : 0.0;
+#pragma unroll
+        for (int i = 0; i < FIN_B; ++i) a[4] = fmax(a[4], v[i]);
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
 #pragma unroll
