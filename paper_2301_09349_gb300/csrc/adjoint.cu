@@ -385,82 +385,104 @@ __device__ __forceinline__ void tile_faces(const GridParams &g, const AdjK<T> &k
     if (o[D] + bsz[D] >= g.n[D]) cnt[D] += 1;   // the last tile owns the domain face b = n
     const int nf = cnt[0] * cnt[1] * cnt[2];
     const long long N = g.N;
-    for (int f = threadIdx.x; f < nf; f += FT) {
-        int l[3];
-        l[0] = f % cnt[0];
-        l[1] = (f / cnt[0]) % cnt[1];
-        l[2] = f / (cnt[0] * cnt[1]);
-        const int gb = o[D] + l[D];
-        const bool b_in = gb < g.n[D], a_in = gb >= 1;
-        long long jb = 0, ja = 0;
-        {
-            int c[3] = {o[0] + l[0], o[1] + l[1], o[2] + l[2]};
-            jb = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
-            c[D] -= 1;
-            ja = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
-        }
-        R Fb[NC];
-        bool any = false;
-#pragma unroll
-        for (int q = 0; q < NC; ++q) {
-            const R vb = b_in ? V[q * N + jb] : R(0);
-            const R va = a_in ? V[q * N + ja] : R(0);
-            Fb[q] = (vb - va) * k.inv_h;
-            any |= Fb[q] != R(0);
-        }
-        if (!any) continue;
-        const int qb = (l[0] + 2) + B::PX * ((l[1] + 2) + B::PY * (DIM == 3 ? l[2] + 2 : 0));
-        const int sD = str[D];
+    // Faces go in batches of one per thread.  Each face adds to 4 cells along
+    // its normal and 4 cells per tangent; for one such stencil slot the map
+    // face -> cell is one-to-one, so the slots are added in a fixed order
+    // with a barrier between them and no two faces of a batch ever touch the
+    // same accumulator at once: the sums are bitwise reproducible.
+    for (int base = 0; base < nf; base += FT) {
+        const int f = base + threadIdx.x;
+        bool act = false;
         int qs[4];
-        R w[4][NC], wb[4][NC];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            qs[i] = qb + (i - 2) * sD;
-#pragma unroll
-            for (int c = 0; c < NC; ++c) {
-                w[i][c] = Wsm[c * PN + qs[i]];
-                wb[i][c] = R(0);
-            }
-        }
-        R ut[NT2][4][DIM], utb[NT2][4][DIM];
         int qt[NT2][4];
-        {
-            int ti = 0;
+        R wb[4][NC];
+        R utb[NT2][4][DIM];
+        if (f < nf) {
+            int l[3];
+            l[0] = f % cnt[0];
+            l[1] = (f / cnt[0]) % cnt[1];
+            l[2] = f / (cnt[0] * cnt[1]);
+            const int gb = o[D] + l[D];
+            const bool b_in = gb < g.n[D], a_in = gb >= 1;
+            long long jb = 0, ja = 0;
+            {
+                int c[3] = {o[0] + l[0], o[1] + l[1], o[2] + l[2]};
+                jb = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+                c[D] -= 1;
+                ja = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+            }
+            R Fb[NC];
+            bool any = false;
 #pragma unroll
-            for (int e = 0; e < DIM; ++e) {
-                if (e == D) continue;
+            for (int q = 0; q < NC; ++q) {
+                const R vb = b_in ? V[q * N + jb] : R(0);
+                const R va = a_in ? V[q * N + ja] : R(0);
+                Fb[q] = (vb - va) * k.inv_h;
+                any |= Fb[q] != R(0);
+            }
+            if (any) {
+                act = true;
+                const int qb =
+                    (l[0] + 2) + B::PX * ((l[1] + 2) + B::PY * (DIM == 3 ? l[2] + 2 : 0));
+                const int sD = str[D];
+                R w[4][NC];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    qt[ti][i] = (i < 2 ? qb - sD : qb) + ((i & 1) ? str[e] : -str[e]);
+                    qs[i] = qb + (i - 2) * sD;
 #pragma unroll
-                    for (int m = 0; m < DIM; ++m) {
-                        ut[ti][i][m] = Wsm[(1 + m) * PN + qt[ti][i]];
-                        utb[ti][i][m] = R(0);
+                    for (int c = 0; c < NC; ++c) {
+                        w[i][c] = Wsm[c * PN + qs[i]];
+                        wb[i][c] = R(0);
                     }
                 }
-                ++ti;
+                R ut[NT2][4][DIM];
+                {
+                    int ti = 0;
+#pragma unroll
+                    for (int e = 0; e < DIM; ++e) {
+                        if (e == D) continue;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            qt[ti][i] = (i < 2 ? qb - sD : qb) + ((i & 1) ? str[e] : -str[e]);
+#pragma unroll
+                            for (int m = 0; m < DIM; ++m) {
+                                ut[ti][i][m] = Wsm[(1 + m) * PN + qt[ti][i]];
+                                utb[ti][i][m] = R(0);
+                            }
+                        }
+                        ++ti;
+                    }
+                }
+                face_vjp<DIM, D, R>(k, w, ut, Fb, wb, utb);
             }
         }
-        face_vjp<DIM, D, R>(k, w, ut, Fb, wb, utb);
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+        for (int i = 0; i < 4; ++i) {
+            if (act) {
 #pragma unroll
-            for (int c = 0; c < NC; ++c)
-                if (wb[i][c] != R(0)) atomicAdd(Acc + c * PN + qs[i], wb[i][c]);
+                for (int c = 0; c < NC; ++c)
+                    if (wb[i][c] != R(0)) Acc[c * PN + qs[i]] += wb[i][c];
+            }
+            __syncthreads();
+        }
 #pragma unroll
         for (int ti = 0; ti < (DIM > 1 ? DIM - 1 : 0); ++ti)
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 4; ++i) {
+                if (act) {
 #pragma unroll
-                for (int m = 0; m < DIM; ++m)
-                    if (utb[ti][i][m] != R(0)) atomicAdd(Acc + (1 + m) * PN + qt[ti][i], utb[ti][i][m]);
+                    for (int m = 0; m < DIM; ++m)
+                        if (utb[ti][i][m] != R(0)) Acc[(1 + m) * PN + qt[ti][i]] += utb[ti][i][m];
+                }
+                __syncthreads();
+            }
     }
 }
 
 template <int DIM, typename T>
 __global__ void __launch_bounds__(FT, IBM_ADJ_FT_MIN)
 adj_flux_tile_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ V,
-                     T *__restrict__ lamW) {
+                     T *__restrict__ tbuf) {
     using B = AdjBox<DIM, T>;
     using R = T;
     constexpr int NC = DIM + 2;
@@ -489,26 +511,110 @@ adj_flux_tile_kernel(const GridParams g, const T *__restrict__ U, const T *__res
     tile_faces<DIM, 1, T>(g, k, V, Wsm, Acc, ox, oy, oz);
     if constexpr (DIM == 3) tile_faces<DIM, (DIM == 3 ? 2 : 0), T>(g, k, V, Wsm, Acc, ox, oy, oz);
     __syncthreads();
-    const long long N = g.N;
-    for (int q = threadIdx.x; q < PN; q += FT) {
-        const int lx = q % B::PX, ly = (q / B::PX) % B::PY, lz = q / (B::PX * B::PY);
-        int flip = 0, fs = 0;
-        const int sx = map_axis(ox + lx - 2, g.n[0], g.bc[0], g.bc[1], 0, flip, fs);
-        const int sy = map_axis(oy + ly - 2, g.n[1], g.bc[2], g.bc[3], 1, flip, fs);
-        const int sz = DIM == 3 ? map_axis(oz + lz - 2, g.n[2], g.bc[4], g.bc[5], 2, flip, fs) : 0;
-        if (fs) continue;
-        const long long src = sx + (long long)g.n[0] * (sy + (long long)g.n[1] * sz);
+    // the tile-plus-halo sums go to this tile's own slice of the buffer; the
+    // chain kernel gathers them per cell in a fixed order
+    const size_t tile = blockIdx.x + (size_t)gridDim.x * (blockIdx.y + (size_t)gridDim.y * blockIdx.z);
+    T *dst = tbuf + tile * NC * PN;
+    for (int q = threadIdx.x; q < NC * PN; q += FT) dst[q] = Acc[q];
+}
+
+// The primitive adjoints of cell c from the tile buffers: every tile whose
+// halo-extended box holds the cell, or a ghost image of it (slip mirror,
+// zero gradient or periodic image; free-stream ghosts are constants and drop
+// out), summed in a fixed order - per axis the boxes holding the cell itself
+// by ascending tile, then those holding its ghost images - with the slip
+// flips of the momentum components applied.  Up to six candidates per axis
+// (a ragged last tile of one cell adds a box), kept in registers as packed
+// (tile << 8 | position << 1 | flip) words and picked by selects.
+struct AxisCands {
+    unsigned v0 = 0, v1 = 0, v2 = 0, v3 = 0, v4 = 0, v5 = 0;
+    int n = 0;
+    __device__ __forceinline__ void add(unsigned w) {
+        v5 = n == 5 ? w : v5;
+        v4 = n == 4 ? w : v4;
+        v3 = n == 3 ? w : v3;
+        v2 = n == 2 ? w : v2;
+        v1 = n == 1 ? w : v1;
+        v0 = n == 0 ? w : v0;
+        n = n < 6 ? n + 1 : 6;
+    }
+    __device__ __forceinline__ unsigned get(int k) const {
+        unsigned r = v0;
+        r = k == 1 ? v1 : r;
+        r = k == 2 ? v2 : r;
+        r = k == 3 ? v3 : r;
+        r = k == 4 ? v4 : r;
+        r = k == 5 ? v5 : r;
+        return r;
+    }
+};
+
+template <int DIM, typename T>
+__device__ __forceinline__ void gather_tiles(const GridParams &g, const T *__restrict__ tbuf,
+                                             const int (&c)[3], T (&wv)[DIM + 2]) {
+    using B = AdjBox<DIM, T>;
+    constexpr int NC = DIM + 2;
+    constexpr int PN = B::PN;
+    const int bs[3] = {B::BX, B::BY, B::BZ};
+    const int ps[3] = {B::PX, B::PY, B::PZ};
+    int nt[3] = {1, 1, 1};
+    AxisCands ax[3];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            R v = Acc[c * PN + q];
-            if (v == R(0)) continue;
-            if (c >= 1 && c <= DIM && ((flip >> (c - 1)) & 1)) v = -v;
-            atomicAdd(lamW + c * N + src, v);
+    for (int e = 0; e < 3; ++e) {
+        if (e >= DIM) {
+            ax[e].add(0u);
+            continue;
+        }
+        const int n = g.n[e], be = bs[e];
+        nt[e] = (n + be - 1) / be;
+        // the cell itself, then the ghost positions whose image it is
+        const int cand[5] = {c[e], -2, -1, n, n + 1};
+#pragma unroll
+        for (int pi = 0; pi < 5; ++pi) {
+            const int p = cand[pi];
+            int flip = 0;
+            if (pi > 0) {
+                int fs = 0;
+                const int src = map_axis(p, n, g.bc[2 * e], g.bc[2 * e + 1], e, flip, fs);
+                if (fs || src != c[e]) continue;
+            }
+            // tiles te whose box [te be - 2, te be + be + 1] holds p (p >= -2;
+            // at most two, since be >= 4)
+            const int thi = (p + 2) / be;
+#pragma unroll
+            for (int te = thi - 1; te <= thi; ++te) {
+                const int l = p - te * be + 2;
+                if (te < 0 || te >= nt[e] || l < 0 || l >= ps[e]) continue;
+                ax[e].add(((unsigned)te << 8) | ((unsigned)l << 1) | (flip ? 1u : 0u));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NC; ++q) wv[q] = T(0);
+    for (int iz = 0; iz < ax[2].n; ++iz) {
+        const unsigned wz = ax[2].get(iz);
+        for (int iy = 0; iy < ax[1].n; ++iy) {
+            const unsigned wy = ax[1].get(iy);
+            for (int ix = 0; ix < ax[0].n; ++ix) {
+                const unsigned wx = ax[0].get(ix);
+                const size_t tile =
+                    (wx >> 8) + (size_t)nt[0] * ((wy >> 8) + (size_t)nt[1] * (wz >> 8));
+                const int q = (int)((wx >> 1) & 127u) +
+                              B::PX * ((int)((wy >> 1) & 127u) + B::PY * (int)((wz >> 1) & 127u));
+                const int flip = (int)(wx & 1u) | ((int)(wy & 1u) << 1) | ((int)(wz & 1u) << 2);
+                const T *src = tbuf + tile * NC * PN + q;
+#pragma unroll
+                for (int cc = 0; cc < NC; ++cc) {
+                    T v = src[(size_t)cc * PN];
+                    if (cc >= 1 && cc <= DIM && ((flip >> (cc - 1)) & 1)) v = -v;
+                    wv[cc] += v;
+                }
+            }
         }
     }
 }
 
-// w = (dW/dU)^T lamW at every cell (then lamW is cleared):
+// w = (dW/dU)^T W-bar at every cell, W-bar gathered from the tile buffers:
 // rho-bar = W_rho - sum_m W_um u_m / rho + W_p (gamma-1) |u|^2/2,
 // m-bar = W_u / rho - W_p (gamma-1) u, E-bar = W_p (gamma-1).
 // MODE -1 stores w in out; the reverse sweep's two SSP-RK2 updates take w
@@ -516,7 +622,7 @@ adj_flux_tile_kernel(const GridParams g, const T *__restrict__ U, const T *__res
 // In the grid's type throughout (double arithmetic is slow on this GPU).
 template <int DIM, typename T, int MODE>
 __global__ void __launch_bounds__(AT)
-adj_prim_kernel(const GridParams g, const T *__restrict__ U, T *__restrict__ lamW,
+adj_prim_kernel(const GridParams g, const T *__restrict__ U, const T *__restrict__ tbuf,
                 T *__restrict__ out, T *__restrict__ lam, T *__restrict__ mu, double dt_d) {
     using R = T;
     constexpr int NC = DIM + 2;
@@ -530,14 +636,16 @@ adj_prim_kernel(const GridParams g, const T *__restrict__ U, T *__restrict__ lam
 #pragma unroll
         for (int q = 0; q <= DIM; ++q) uc[q] = __ldg(U + q * N + j);
 #pragma unroll
-        for (int q = 0; q < NC; ++q) wbv[q] = lamW[q * N + j];
-#pragma unroll
         for (int q = 0; q < NC; ++q) {
             lv[q] = MODE >= 0 ? lam[q * N + j] : R(0);
             mv[q] = MODE == 1 ? mu[q * N + j] : R(0);
         }
-#pragma unroll
-        for (int q = 0; q < NC; ++q) lamW[q * N + j] = R(0);
+        {
+            const long long nxy = (long long)g.n[0] * g.n[1];
+            const int c[3] = {(int)(j % g.n[0]), (int)((j / g.n[0]) % g.n[1]),
+                              DIM == 3 ? (int)(j / nxy) : 0};
+            gather_tiles<DIM, T>(g, tbuf, c, wbv);
+        }
         const R rho = uc[0], inv = R(1) / rho;
         R v[DIM], ke = R(0);
 #pragma unroll
@@ -901,13 +1009,13 @@ int grid_for(long long work, int per_block = AT) {
     return (int)b;
 }
 
-// out = J_L(U)^T V (lamW must be zero on entry; it is zero again on exit)
+// out = J_L(U)^T V (tbuf: the per-tile accumulators, adj_tile_buf_bytes)
 template <int DIM, typename T>
-cudaError_t rhs_vjp_t(const GridParams &g, const void *U, const void *V, void *lamW_, void *out,
+cudaError_t rhs_vjp_t(const GridParams &g, const void *U, const void *V, void *tbuf_, void *out,
                       cudaStream_t s, int mode = -1, void *lam = nullptr, void *mu = nullptr,
                       double dt = 0.0) {
     const T *u = (const T *)U, *v = (const T *)V;
-    T *lamW = (T *)lamW_;
+    T *tbuf = (T *)tbuf_;
     using B = AdjBox<DIM, T>;
     {
         cudaError_t e = func_smem_attr((const void *)adj_flux_tile_kernel<DIM, T>, B::SMEM);
@@ -915,16 +1023,16 @@ cudaError_t rhs_vjp_t(const GridParams &g, const void *U, const void *V, void *l
     }
     const dim3 grid((g.n[0] + B::BX - 1) / B::BX, (g.n[1] + B::BY - 1) / B::BY,
                     DIM == 3 ? (g.n[2] + B::BZ - 1) / B::BZ : 1);
-    adj_flux_tile_kernel<DIM, T><<<grid, FT, B::SMEM, s>>>(g, u, v, lamW);
+    adj_flux_tile_kernel<DIM, T><<<grid, FT, B::SMEM, s>>>(g, u, v, tbuf);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int nb = grid_for(g.N);
     if (mode == 0)
-        adj_prim_kernel<DIM, T, 0><<<nb, AT, 0, s>>>(g, u, lamW, nullptr, (T *)lam, (T *)mu, dt);
+        adj_prim_kernel<DIM, T, 0><<<nb, AT, 0, s>>>(g, u, tbuf, nullptr, (T *)lam, (T *)mu, dt);
     else if (mode == 1)
-        adj_prim_kernel<DIM, T, 1><<<nb, AT, 0, s>>>(g, u, lamW, nullptr, (T *)lam, (T *)mu, dt);
+        adj_prim_kernel<DIM, T, 1><<<nb, AT, 0, s>>>(g, u, tbuf, nullptr, (T *)lam, (T *)mu, dt);
     else
-        adj_prim_kernel<DIM, T, -1><<<nb, AT, 0, s>>>(g, u, lamW, (T *)out, nullptr, nullptr, 0.0);
+        adj_prim_kernel<DIM, T, -1><<<nb, AT, 0, s>>>(g, u, tbuf, (T *)out, nullptr, nullptr, 0.0);
     return cudaGetLastError();
 }
 
@@ -947,9 +1055,9 @@ cudaError_t reverse_step_t(const GridParams &g, const MarkerBuffers &m, const Ad
         if (e != cudaSuccess) return e;
     }
     // mu = lam/2 + (dt/2) J_L(U1)^T lam, then lam = lam/2 + mu + dt J_L(U)^T mu
-    e = rhs_vjp_t<DIM, T>(g, a.A, lam, a.lamW, nullptr, s, 0, lam, mu, dt);
+    e = rhs_vjp_t<DIM, T>(g, a.A, lam, a.tbuf, nullptr, s, 0, lam, mu, dt);
     if (e != cudaSuccess) return e;
-    return rhs_vjp_t<DIM, T>(g, Un, mu, a.lamW, nullptr, s, 1, lam, mu, dt);
+    return rhs_vjp_t<DIM, T>(g, Un, mu, a.tbuf, nullptr, s, 1, lam, mu, dt);
 }
 
 template <int DIM>
@@ -968,12 +1076,12 @@ cudaError_t eps_adjoint_x(const GridParams &g, const MarkerBuffers &m, const Adj
 }  // namespace
 
 cudaError_t launch_rhs_vjp(const GridParams &g, int fp_bytes, const void *U, const void *V,
-                           void *lamW, void *out, cudaStream_t s) {
+                           void *tbuf, void *out, cudaStream_t s) {
     if (g.dim == 3)
-        return fp_bytes == 4 ? rhs_vjp_t<3, float>(g, U, V, lamW, out, s)
-                             : rhs_vjp_t<3, double>(g, U, V, lamW, out, s);
-    return fp_bytes == 4 ? rhs_vjp_t<2, float>(g, U, V, lamW, out, s)
-                         : rhs_vjp_t<2, double>(g, U, V, lamW, out, s);
+        return fp_bytes == 4 ? rhs_vjp_t<3, float>(g, U, V, tbuf, out, s)
+                             : rhs_vjp_t<3, double>(g, U, V, tbuf, out, s);
+    return fp_bytes == 4 ? rhs_vjp_t<2, float>(g, U, V, tbuf, out, s)
+                         : rhs_vjp_t<2, double>(g, U, V, tbuf, out, s);
 }
 
 cudaError_t launch_reverse_step(const GridParams &g, int fp_bytes, const MarkerBuffers &m,
@@ -1003,6 +1111,20 @@ using namespace ibmk;
 namespace {
 
 size_t aup(size_t x) { return (x + 255) / 256 * 256; }
+
+// bytes of the flux transpose's per-tile accumulators: every tile of the
+// reverse flux kernel keeps its tile-plus-halo sums (dim+2 fields)
+template <int DIM, typename T> size_t tile_buf_bytes_t(const int *n) {
+    using B = AdjBox<DIM, T>;
+    const size_t tiles = (size_t)((n[0] + B::BX - 1) / B::BX) * ((n[1] + B::BY - 1) / B::BY) *
+                         (DIM == 3 ? (n[2] + B::BZ - 1) / B::BZ : 1);
+    return tiles * (DIM + 2) * B::PN * sizeof(T);
+}
+size_t adj_tile_buf_bytes(const ibm_grid_desc &d) {
+    if (d.dim == 3)
+        return d.fp_bytes == 4 ? tile_buf_bytes_t<3, float>(d.n) : tile_buf_bytes_t<3, double>(d.n);
+    return d.fp_bytes == 4 ? tile_buf_bytes_t<2, float>(d.n) : tile_buf_bytes_t<2, double>(d.n);
+}
 
 size_t state_bytes_of(const ibm_grid_desc &d) {
     long long N = 1;
@@ -1042,6 +1164,7 @@ size_t adj_layout(const ibm_grid_desc &d, int cap, int max_steps, int every, cha
     b.jtv = take(SB);
     b.lfq = take(SB);
     b.lamW = take(sizeof(double) * (size_t)N * (d.dim + 2));
+    b.tbuf = take(adj_tile_buf_bytes(d));
     b.lamX = (double *)take(sizeof(double) * 3 * c1);
     b.lamTw = (double *)take(sizeof(double) * c1);
     b.lamEps = (double *)take(sizeof(double) * c1);
@@ -1141,7 +1264,7 @@ ibm_status ibm_rhs_vjp(ibm_grid *g, const void *U, const void *V, void *out) {
     if (!g) return IBM_ERR_ARG;
     if (!U || !V || !out) return afail(g, IBM_ERR_ARG, "null buffer");
     if (!g->recording) return afail(g, IBM_ERR_STATE, "ibm_record must come first (it holds the scratch)");
-    ACU(launch_rhs_vjp(g->gp, g->desc.fp_bytes, U, V, g->adj.lamW, out, g->stream), "rhs vjp");
+    ACU(launch_rhs_vjp(g->gp, g->desc.fp_bytes, U, V, g->adj.tbuf, out, g->stream), "rhs vjp");
     return IBM_OK;
 }
 

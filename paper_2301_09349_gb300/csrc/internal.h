@@ -239,8 +239,8 @@ struct AdjBuffers {
     void *mu = nullptr;          // adjoint of U1
     void *jtv = nullptr;         // scratch state
     void *lfq = nullptr;         // (dim+1) x N: adjoints of the spread sources
-    void *lamW = nullptr;        // (dim+2) x N accumulators of the primitive adjoints, in
-                                 // the grid's type (sized for doubles: also FP64 scratch)
+    void *lamW = nullptr;        // (dim+2) x N doubles of FP64 scratch (band-cell passes)
+    void *tbuf = nullptr;        // flux transpose: tile-plus-halo sums of every tile
     double *lamX = nullptr;      // cap x 3 marker-position gradient
     double *lamTw = nullptr;     // cap wall-temperature gradient
     double *lamEps = nullptr;    // cap adjoint of eps~
@@ -249,9 +249,9 @@ struct AdjBuffers {
     double *save = nullptr;      // cap x 5: rho_L, G (3), H of the last forward step
 };
 
-// out = J_L(U)^T V (lamW: accumulators, zero on entry and exit)
+// out = J_L(U)^T V (tbuf: the per-tile accumulators of the adjoint workspace)
 cudaError_t launch_rhs_vjp(const GridParams &g, int fp_bytes, const void *U, const void *V,
-                           void *lamW, void *out, cudaStream_t s);
+                           void *tbuf, void *out, cudaStream_t s);
 // one step reversed: a.A = U1, a.B = U* and the marker forcing of the step
 // must be current; a.lam holds the adjoint of U^{n+1} and receives that of
 // U^n; cd, nu: the direct terms of J (last step only)
