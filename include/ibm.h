@@ -138,6 +138,15 @@ ibm_status ibm_set_markers(ibm_grid *g, int n, const double *X0, const double *U
  * call (pageable memory is copied before the call returns). */
 ibm_status ibm_set_wall_temperature(ibm_grid *g, const double *Tw);
 
+/* Stopping rule of the quadrature solve A~ eps~ = 1 (Sec. 2.2): the
+ * iterative solver (more than 160 markers) stops when
+ * max_k |1 - (A~ eps~)_k| <= tol, after at most maxit iterations
+ * (IBM_ERR_NOCONV otherwise); the direct solver (up to 160 markers) refines
+ * to its rounding floor and checks the same bound.  Defaults 1e-12 and 4000.
+ * Takes effect from the next ibm_set_markers (and every step of a moving
+ * body).  Errors: IBM_ERR_ARG (tol outside (0, 1) or maxit < 1). */
+ibm_status ibm_set_quadrature(ibm_grid *g, double tol, int maxit);
+
 /* Advance nsteps IBM steps.  dt_fixed > 0 imposes the step size; otherwise
  * dt = cfl / max_j s_j is computed on the device from the state at the start
  * of each step (formed at the end of the previous step, or when the state is

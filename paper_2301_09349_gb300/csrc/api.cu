@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/ibm.h"
+#include <nvtx3/nvToolsExt.h>
 #include "device_table.h"
 #include "handle.h"
 #include "internal.h"
@@ -226,9 +227,20 @@ int persistent_ctas(const ibm_grid *g) {
 }
 
 // Event pair around a kernel group (no-op unless profiling is on).
+// Kernel groups of a step as named NVTX ranges (host-side markers for a
+// timeline profiler; the header-only NVTX v3 API costs nothing when no tool
+// is attached), opened and closed with the event pair of the group.
+// (indexed by IBM_PROF_*)
+const char *const kProfNames[IBM_PROF_GROUPS] = {"ibm: fluid stage 1", "ibm: fluid stage 2",
+                                                 "ibm: moving markers (bins, weights)",
+                                                 "ibm: interpolation + forcing",
+                                                 "ibm: spreading + forced update",
+                                                 "ibm: force sums, next dt"};
+
 cudaError_t prof_begin(ibm_grid *g, int group, int launches, long *rec) {
     *rec = -1;
     if (!g->prof) return cudaSuccess;
+    nvtxRangePushA(kProfNames[group]);
     while (g->ev_pool.size() < g->ev_used + 2) {
         cudaEvent_t e;
         cudaError_t err = cudaEventCreate(&e);
@@ -244,7 +256,9 @@ cudaError_t prof_begin(ibm_grid *g, int group, int launches, long *rec) {
 
 cudaError_t prof_end(ibm_grid *g, long rec) {
     if (rec < 0) return cudaSuccess;
-    return cudaEventRecord(g->ev_pool[g->recs[rec].ev + 1], g->stream);
+    const cudaError_t e = cudaEventRecord(g->ev_pool[g->recs[rec].ev + 1], g->stream);
+    nvtxRangePop();
+    return e;
 }
 
 // fold recorded pairs into the totals (requires the stream to be idle)
@@ -539,6 +553,15 @@ ibm_status ibm_set_markers(ibm_grid *g, int n, const double *X0, const double *U
     st = check_device(g);
     if (st != IBM_OK) return st;
     if (n_kept) *n_kept = ns;
+    return IBM_OK;
+}
+
+ibm_status ibm_set_quadrature(ibm_grid *g, double tol, int maxit) {
+    if (!g) return IBM_ERR_ARG;
+    if (!(tol > 0.0 && tol < 1.0) || maxit < 1)
+        return fail(g, IBM_ERR_ARG, "quadrature tolerance must be in (0, 1) and maxit >= 1");
+    g->cg_tol = tol;
+    g->cg_maxit = maxit;
     return IBM_OK;
 }
 

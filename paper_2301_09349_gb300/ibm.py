@@ -71,6 +71,7 @@ SIGNATURES = [
     ("ibm_set_markers", ctypes.c_int, [_vp, ctypes.c_int, _dp, _dp, _dp, ctypes.POINTER(MotionC),
                                        ctypes.c_int, _ip]),
     ("ibm_set_wall_temperature", ctypes.c_int, [_vp, _dp]),
+    ("ibm_set_quadrature", ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_int]),
     ("ibm_step", ctypes.c_int, [_vp, ctypes.c_int, ctypes.c_double]),
     ("ibm_step_graphs", ctypes.c_int, [_vp, ctypes.c_int]),
     ("ibm_forces_and_nusselt", ctypes.c_int, [_vp, _dp, _dp, _dp, _dp, _dp]),
@@ -227,6 +228,10 @@ def ibm_set_markers(h, X, Tw, Ub=None, motion: Optional[cases.Motion] = None,
 def ibm_set_wall_temperature(h, Tw):
     Tw = _f64(Tw)
     _check(lib().ibm_set_wall_temperature(h, _ptr(Tw)), h)
+
+
+def ibm_set_quadrature(h, tol: float, maxit: int):
+    _check(lib().ibm_set_quadrature(h, ctypes.c_double(tol), int(maxit)), h)
 
 
 def ibm_step(h, nsteps: int, dt_fixed: float = 0.0):
@@ -524,6 +529,10 @@ class Grid:
 
     def set_wall_temperature(self, Tw):
         ibm_set_wall_temperature(self.h, Tw)
+
+    def set_quadrature(self, tol: float, maxit: int = 4000):
+        """stopping rule of the A~ eps~ = 1 solve, from the next set_markers"""
+        ibm_set_quadrature(self.h, tol, maxit)
 
     def step(self, nsteps: int = 1, dt_fixed: float = 0.0):
         ibm_step(self.h, nsteps, dt_fixed)
