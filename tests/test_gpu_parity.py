@@ -271,6 +271,38 @@ def test_supersonic_cold_sphere_1000_steps(oracle):
         assert np.all(err < 1e-3), (done, err)
 
 
+def test_supersonic_sphere_full_size_stops_with_the_oracle(oracle):
+    """The configured Mach 2 sphere at 256^3 with a cold wall does not reach
+    1000 steps: a near-vacuum forms just inside the rear of the shell and
+    the fluid step turns it non-finite.  This is a property of the
+    discretisation, not of the CUDA path: the FP64 oracle from the same
+    (FP32-rounded) initial state stops at the same step as the GPU, which
+    reports IBM_ERR_NONFINITE there and not before."""
+    c = C.heated_sphere(n=256, mach=2.0, Tw=0.5)
+    g = c.grid
+    U0 = C.initial_state(g, c.seed).astype(np.float32)
+    run = oracle.Run(g, c.X, c.Tw)
+    U = U0.astype(np.float64).reshape(5, -1)
+    stop_o = None
+    for k in range(200):
+        U = run.step(U).reshape(5, -1)
+        p = 0.4 * (U[4] - 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0])
+        if not (np.all(np.isfinite(p)) and np.all(p > 0) and np.all(U[0] > 0)):
+            stop_o = k
+            break
+    assert stop_o is not None
+    grid = ibm.Grid(g, max_markers=len(c.X))
+    grid.set_markers(c.X, c.Tw)
+    grid.set_state(U0)
+    grid.step(stop_o)
+    grid.sync()                      # no error before the oracle's stop
+    grid.step(1)
+    with pytest.raises(ibm.IbmError) as e:
+        grid.sync()
+    assert e.value.status == 3
+    grid.close()
+
+
 @pytest.mark.parametrize("ub,fails", [(2.3, False), (2.4, True)])
 def test_nonpositive_state_is_reported_like_the_oracle(oracle, ub, fails):
     """Energy reading B (the heat source on total energy) with a body moving
