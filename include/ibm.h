@@ -57,6 +57,8 @@ typedef int ibm_status;
 #define IBM_ERR_TIMEOUT 6     /* a bounded device wait gave up */
 #define IBM_ERR_STATE 7       /* call out of order (e.g. step before set_state) */
 #define IBM_ERR_UNSUPPORTED 8 /* declared but not provided by this build */
+#define IBM_ERR_BOUNDS 9      /* (bounds-checked build only) a kernel met an index outside
+                                 its array; the access was skipped */
 
 /* boundary conditions per domain face */
 #define IBM_BC_FREESTREAM 0   /* Dirichlet: ghost cells hold the free stream (inlet, Sec. 3.1) */

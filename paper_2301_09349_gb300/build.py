@@ -15,6 +15,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "lib")
 LIB = os.path.join(LIBDIR, "libibm_gb300.so")
+# the bounds-checked variant (IBM_CHECKED): every instrumented global index
+# is checked, a violation is recorded in the device error word
+# (IBM_ERR_BOUNDS) and the access skipped; for tests, not for timing
+LIB_CHECKED = os.path.join(LIBDIR, "libibm_gb300_checked.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 UNITS = ["flux.cu", "flux_zm.cu", "markers.cu", "quadrature.cu", "api.cu", "noalloc.cu", "adjoint.cu",
          "batch.cu"]
@@ -45,25 +49,28 @@ def _sources():
     return deps
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _sources())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile the library (checked=True: the bounds-checked variant)."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(lib):
+        return lib
     os.makedirs(LIBDIR, exist_ok=True)
     cc = nvcc()
-    objdir = os.path.join(LIBDIR, "obj")
+    objdir = os.path.join(LIBDIR, "obj_checked" if checked else "obj")
     os.makedirs(objdir, exist_ok=True)
+    variant = ["-DIBM_CHECKED"] if checked else []
 
     def compile_one(unit):
         obj = os.path.join(objdir, unit.replace(".cu", ".o"))
-        cmd = [cc] + ARCH + FLAGS + UNIT_FLAGS.get(unit, []) + EXTRA + ["-c", os.path.join(SRC, unit),
-                                                                        "-o", obj]
+        cmd = [cc] + ARCH + FLAGS + UNIT_FLAGS.get(unit, []) + EXTRA + variant + \
+            ["-c", os.path.join(SRC, unit), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed on %s:\n%s" % (unit, r.stderr))
@@ -73,13 +80,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
         objs = list(ex.map(compile_one, UNITS))
-    tmp = LIB + ".tmp%d" % os.getpid()
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("nvcc link failed:\n%s" % r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -219,6 +219,8 @@ ibm_status check_device(ibm_grid *g) {
         return fail(g, IBM_ERR_ARG, "a marker left the admissible region (2 cells from the edges)");
     if (e & ERR_CAPACITY) return fail(g, IBM_ERR_WORKSPACE, "quadrature row capacity exceeded");
     if (e & ERR_TIMEOUT) return fail(g, IBM_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (e & ERR_BOUNDS)
+        return fail(g, IBM_ERR_BOUNDS, "a kernel met an index outside its array (checked build)");
     return IBM_OK;
 }
 

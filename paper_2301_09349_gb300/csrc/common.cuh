@@ -17,6 +17,7 @@ enum : int {
     ERR_MARKER_RANGE = 4,   // a (moving) marker left the admissible region
     ERR_CAPACITY = 8,       // a quadrature row exceeded its storage
     ERR_TIMEOUT = 16,       // a bounded wait gave up
+    ERR_BOUNDS = 32,        // (bounds-checked build) an index outside its array
 };
 
 enum : int { BC_FREESTREAM = 0, BC_ZEROGRAD = 1, BC_SLIP = 2, BC_PERIODIC = 3 };
@@ -126,6 +127,21 @@ __device__ __forceinline__ unsigned cell_key(const GridParams &g, int cx, int cy
 }
 
 __device__ __forceinline__ void record_error(int *err, int bits) { atomicOr(err, bits); }
+
+// Bounds-checked build (compiled with IBM_CHECKED, the stand-in for a memory
+// checker on this GPU): a global index outside [0, n) is recorded in the
+// device error word (ERR_BOUNDS, reported as IBM_ERR_BOUNDS) and the caller
+// skips the access; nothing traps.  The regular build compiles the checks
+// away.
+#ifdef IBM_CHECKED
+__device__ __forceinline__ bool in_bounds(long long i, long long n, int *err) {
+    if (i >= 0 && i < n) return true;
+    record_error(err, ERR_BOUNDS);
+    return false;
+}
+#else
+__device__ __forceinline__ bool in_bounds(long long, long long, int *) { return true; }
+#endif
 
 // a - b on both lanes of an FP32 pair in one packed instruction, rounded to
 // nearest, subnormal results flushed (the FP32 stage units are built with

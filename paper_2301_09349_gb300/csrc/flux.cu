@@ -405,7 +405,8 @@ __device__ __forceinline__ double stage_tile(const GridParams &g, int ox, int oy
                                              const T *__restrict__ Uin, const T *__restrict__ Un,
                                              T *__restrict__ out, const T dt,
                                              const unsigned *__restrict__ band_bits,
-                                             unsigned char *smem_raw, double *s_red, bool &bad) {
+                                             unsigned char *smem_raw, double *s_red, bool &bad,
+                                             int *err) {
     constexpr int DIM = B::DIM;
     constexpr int NC = DIM + 2;
     T *sW = reinterpret_cast<T *>(smem_raw);
@@ -433,8 +434,9 @@ __device__ __forceinline__ double stage_tile(const GridParams &g, int ox, int oy
         if (interior) {
             const long long j = (ox + lx - 2) +
                                 (long long)g.n[0] * ((oy + ly - 2) + (long long)g.n[1] * (oz + lz - 2 * (DIM == 3)));
+            const bool okj = in_bounds(j, N, err);
 #pragma unroll
-            for (int c = 0; c < NC; ++c) u[c] = __ldg(Uin + c * N + j);
+            for (int c = 0; c < NC; ++c) u[c] = okj ? __ldg(Uin + c * N + j) : T(0);
         } else {
             int flip = 0, fs = 0;
             const int sx = map_axis(ox + lx - 2, g.n[0], g.bc[0], g.bc[1], 0, flip, fs);
@@ -448,8 +450,9 @@ __device__ __forceinline__ double stage_tile(const GridParams &g, int ox, int oy
                 u[NC - 1] = p_inf_E;
             } else {
                 const long long j = sx + (long long)g.n[0] * (sy + (long long)g.n[1] * sz);
+                const bool okj = in_bounds(j, N, err);
 #pragma unroll
-                for (int c = 0; c < NC; ++c) u[c] = __ldg(Uin + c * N + j);
+                for (int c = 0; c < NC; ++c) u[c] = okj ? __ldg(Uin + c * N + j) : T(0);
 #pragma unroll
                 for (int d = 0; d < DIM; ++d)
                     if ((flip >> d) & 1) u[1 + d] = -u[1 + d];
@@ -500,6 +503,7 @@ __device__ __forceinline__ double stage_tile(const GridParams &g, int ox, int oy
         const int gx = ox + cx, gy = oy + cy, gz = oz + cz;
         if (gx >= g.n[0] || gy >= g.n[1] || (DIM == 3 && gz >= g.n[2])) continue;
         const long long j = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
+        if (!in_bounds(j, N, err)) continue;
         if (MODE == 0) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) out[c * N + j] = acc[i][c] * inv_h;
@@ -550,7 +554,7 @@ stage_kernel(const GridParams g, const T *__restrict__ Uin, const T *__restrict_
     const T dt = MODE == 0 ? T(0) : (T)(dt_fixed > 0.0 ? dt_fixed : *dt_ptr);
     bool bad = false;
     const double m = stage_tile<B, T, MODE>(g, ox, oy, oz, Uin, Un, out, dt, band_bits, smem_raw,
-                                            s_red, bad);
+                                            s_red, bad, err);
     if (MODE == 2 && threadIdx.x == 0) {
         blockmax[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = m;
         if (bad) record_error(err, ERR_NONFINITE);
@@ -583,7 +587,7 @@ batch_stage_kernel(const BatchCase *__restrict__ cases, const int2 *__restrict__
         T *out = (T *)(MODE == 2 ? bc.Us : bc.U1);
         bool bad = false;
         const double m = stage_tile<B, T, MODE>(g, ox, oy, 0, Uin, (const T *)bc.Un, out, dt,
-                                                bc.band_bits, smem_raw, s_red, bad);
+                                                bc.band_bits, smem_raw, s_red, bad, bc.err);
         if (MODE == 2 && threadIdx.x == 0) {
             item_max[it] = m;
             if (bad) record_error(bc.err, ERR_NONFINITE);

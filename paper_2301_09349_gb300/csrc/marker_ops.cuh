@@ -85,6 +85,7 @@ __device__ __forceinline__ bool gather_cell(const GridParams &g, const MarkerBuf
     bool any = false;
     for (int p = lo; p < end && keys[p] == key; ++p) {
         const int k = perm[p];
+        if (!in_bounds(k, m.ns, m.err)) continue;
         R w = R(1);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) w *= phi_r<R>(cell_offset<R>(oo[d], marker_frac<R>(m, k, d)));

@@ -128,11 +128,15 @@ __device__ __forceinline__ double block_max(double v, double *s_red) {
 }
 
 template <int NTH>
-__device__ __forceinline__ void spmv(int ns, const QuadBuffers &q, const double *x, double *y) {
+__device__ __forceinline__ void spmv(int ns, const QuadBuffers &q, const double *x, double *y,
+                                     int *err) {
     for (int k = threadIdx.x; k < ns; k += NTH) {
         const int c = q.cnt[k];
         double s = 0.0;
-        for (int i = 0; i < c; ++i) s += q.val[(long long)i * q.cap + k] * x[q.col[(long long)i * q.cap + k]];
+        for (int i = 0; i < c; ++i) {
+            const int l = q.col[(long long)i * q.cap + k];
+            if (in_bounds(l, ns, err)) s += q.val[(long long)i * q.cap + k] * x[l];
+        }
         y[k] = s;
     }
 }
@@ -143,7 +147,7 @@ __device__ __forceinline__ void spmv(int ns, const QuadBuffers &q, const double 
 template <int NTH>
 __device__ bool pcg_solve(int ns, const QuadBuffers &q, double *x, const double *__restrict__ rhs,
                           double tol, int maxit, int warm, double *s_red, int *iters,
-                          double *resid) {
+                          double *resid, int *err) {
     double *r = q.r, *z = q.z, *p = q.p, *qv = q.q;
     if (!warm)
         for (int k = threadIdx.x; k < ns; k += NTH) x[k] = 0.0;
@@ -152,7 +156,7 @@ __device__ bool pcg_solve(int ns, const QuadBuffers &q, double *x, const double 
     bool converged = false;
     double rmax = 0.0;
     for (int restart = 0; restart < 50 && it < maxit && !converged; ++restart) {
-        spmv<NTH>(ns, q, x, qv);
+        spmv<NTH>(ns, q, x, qv, err);
         __syncthreads();
         double lm = 0.0;
         for (int k = threadIdx.x; k < ns; k += NTH) {
@@ -170,7 +174,7 @@ __device__ bool pcg_solve(int ns, const QuadBuffers &q, double *x, const double 
         double rz = block_sum<NTH>(lrz, s_red);
         while (it < maxit) {
             __syncthreads();
-            spmv<NTH>(ns, q, p, qv);
+            spmv<NTH>(ns, q, p, qv, err);
             __syncthreads();
             double lpq = 0.0;
             for (int k = threadIdx.x; k < ns; k += NTH) lpq += p[k] * qv[k];
@@ -198,7 +202,7 @@ __device__ bool pcg_solve(int ns, const QuadBuffers &q, double *x, const double 
     }
     if (!converged) {
         __syncthreads();
-        spmv<NTH>(ns, q, x, qv);
+        spmv<NTH>(ns, q, x, qv, err);
         __syncthreads();
         double lm = 0.0;
         for (int k = threadIdx.x; k < ns; k += NTH) lm = fmax(lm, fabs((rhs ? rhs[k] : 1.0) - qv[k]));
@@ -217,7 +221,8 @@ pcg_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rh
     __shared__ double s_red[32];
     int it = 0;
     double rmax = 0.0;
-    const bool converged = pcg_solve<NTH>(ns, q, x, rhs, tol, maxit, warm, s_red, &it, &rmax);
+    const bool converged =
+        pcg_solve<NTH>(ns, q, x, rhs, tol, maxit, warm, s_red, &it, &rmax, err);
     if (threadIdx.x == 0) {
         *q.iters = it;
         *q.resid = rmax;
@@ -411,7 +416,7 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
         const int c = q.cnt[k];
         for (int i = 0; i < c; ++i) {
             const int l = q.col[(long long)i * q.cap + k];
-            if (l <= k) F[(size_t)k * ld + l] = (float)q.val[(long long)i * q.cap + k];
+            if (in_bounds(l, ns, err) && l <= k) F[(size_t)k * ld + l] = (float)q.val[(long long)i * q.cap + k];
         }
         sx[k] = warm ? x[k] : 0.0;
     }
@@ -440,8 +445,10 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
         for (int k = tid; k < ns; k += CHOL_T) {
             const int c = q.cnt[k];
             double sum = 0.0;
-            for (int i = 0; i < c; ++i)
-                sum += q.val[(long long)i * q.cap + k] * sx[q.col[(long long)i * q.cap + k]];
+            for (int i = 0; i < c; ++i) {
+                const int l = q.col[(long long)i * q.cap + k];
+                if (in_bounds(l, ns, err)) sum += q.val[(long long)i * q.cap + k] * sx[l];
+            }
             const double r = (rhs ? rhs[k] : 1.0) - sum;
             r32[k] = (float)r;
             lm = fmax(lm, fabs(r));
@@ -518,7 +525,7 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
         // the refined x when it is finite
         __shared__ double s_red32[32];
         const bool warm_x = !s_bad && rmax < 1.0;
-        ok = pcg_solve<CHOL_T>(ns, q, x, rhs, tol, maxit, warm_x, s_red32, &it, &rmax);
+        ok = pcg_solve<CHOL_T>(ns, q, x, rhs, tol, maxit, warm_x, s_red32, &it, &rmax, err);
     }
     if (tid == 0) {
         *q.iters = it;

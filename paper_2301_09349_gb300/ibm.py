@@ -22,7 +22,7 @@ from .build import LIB
 IBM_OK = 0
 _STATUS = {1: "IBM_ERR_ARG", 2: "IBM_ERR_CUDA", 3: "IBM_ERR_NONFINITE", 4: "IBM_ERR_NOCONV",
            5: "IBM_ERR_WORKSPACE", 6: "IBM_ERR_TIMEOUT", 7: "IBM_ERR_STATE",
-           8: "IBM_ERR_UNSUPPORTED"}
+           8: "IBM_ERR_UNSUPPORTED", 9: "IBM_ERR_BOUNDS"}
 
 
 class IbmError(RuntimeError):
