@@ -396,7 +396,7 @@ __device__ __forceinline__ void to_primitive(const FC &c, const float (&u)[NC],
 // conserved state of a ghost or interior cell through the boundary maps
 __device__ __forceinline__ void mapped_cell(const GridParams &g, const FC &c,
                                             const float *__restrict__ U, int gx, int gy, int gz,
-                                            float (&u)[NC]) {
+                                            float (&u)[NC], int *err) {
     int flip = 0, fs = 0;
     const int sx = map_axis(gx, g.n[0], g.bc[0], g.bc[1], 0, flip, fs);
     const int sy = map_axis(gy, g.n[1], g.bc[2], g.bc[3], 1, flip, fs);
@@ -411,8 +411,9 @@ __device__ __forceinline__ void mapped_cell(const GridParams &g, const FC &c,
     }
     const long long N = g.N;
     const long long j = sx + (long long)g.n[0] * (sy + (long long)g.n[1] * sz);
+    const bool okj = in_bounds(j, N, err);
 #pragma unroll
-    for (int m = 0; m < NC; ++m) u[m] = __ldg(U + m * N + j);
+    for (int m = 0; m < NC; ++m) u[m] = okj ? __ldg(U + m * N + j) : 0.0f;
 #pragma unroll
     for (int d = 0; d < 3; ++d)
         if ((flip >> d) & 1) u[1 + d] = -u[1 + d];
@@ -424,7 +425,7 @@ __device__ __forceinline__ void convert_staged(const GridParams &g, const FC &c,
                                                const float *__restrict__ U,
                                                const float *__restrict__ st,
                                                float *__restrict__ slot, int ox, int oy, int gz,
-                                               bool xy_interior) {
+                                               bool xy_interior, int *err) {
     for (int q = threadIdx.x; q < PP; q += NTH) {
         const int lx = q % PX, ly = q / PX;
         const int gx = ox + lx - 2, gy = oy + ly - 2;
@@ -433,7 +434,7 @@ __device__ __forceinline__ void convert_staged(const GridParams &g, const FC &c,
 #pragma unroll
             for (int m = 0; m < NC; ++m) u[m] = st[(m * SBY + ly) * SBX + lx + 2];
         } else {
-            mapped_cell(g, c, U, gx, gy, gz, u);
+            mapped_cell(g, c, U, gx, gy, gz, u, err);
         }
         to_primitive(c, u, slot, q);
     }
@@ -443,7 +444,7 @@ __device__ __forceinline__ void convert_staged(const GridParams &g, const FC &c,
 // primitives into one ring slot.
 __device__ __forceinline__ void load_plane(const GridParams &g, const FC &c,
                                            const float *__restrict__ U, float *__restrict__ slot,
-                                           int ox, int oy, int gz, bool xy_interior) {
+                                           int ox, int oy, int gz, bool xy_interior, int *err) {
     const long long N = g.N;
     const bool fast = xy_interior && gz >= 0 && gz < g.n[2];
     for (int q = threadIdx.x; q < PP; q += NTH) {
@@ -452,10 +453,11 @@ __device__ __forceinline__ void load_plane(const GridParams &g, const FC &c,
         if (fast) {
             const long long j =
                 (ox + lx - 2) + (long long)g.n[0] * ((oy + ly - 2) + (long long)g.n[1] * gz);
+            const bool okj = in_bounds(j, N, err);
 #pragma unroll
-            for (int m = 0; m < NC; ++m) u[m] = __ldg(U + m * N + j);
+            for (int m = 0; m < NC; ++m) u[m] = okj ? __ldg(U + m * N + j) : 0.0f;
         } else {
-            mapped_cell(g, c, U, ox + lx - 2, oy + ly - 2, gz, u);
+            mapped_cell(g, c, U, ox + lx - 2, oy + ly - 2, gz, u, err);
         }
         to_primitive(c, u, slot, q);
     }
@@ -533,7 +535,7 @@ zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, cons
     }
     // planes z0-2 .. z0+1 by threads; z0+2 comes from the copy just issued
     for (int zz = z0 - 2; zz <= z0 + 1; ++zz)
-        load_plane(g, c, Uin, ring + slot_of(zz), ox, oy, zz, xyint);
+        load_plane(g, c, Uin, ring + slot_of(zz), ox, oy, zz, xyint, err);
     __syncthreads();
 
     // carried from plane to plane: the halved limited z-slopes of the current
@@ -556,9 +558,9 @@ zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, cons
         if (use_stage) {
             parity ^= 1u;
             if (tid == 0) outstanding = false;
-            convert_staged(g, c, Uin, stage, ring + slot_of(z0 + 2), ox, oy, z0 + 2, xyint);
+            convert_staged(g, c, Uin, stage, ring + slot_of(z0 + 2), ox, oy, z0 + 2, xyint, err);
         } else {
-            load_plane(g, c, Uin, ring + slot_of(z0 + 2), ox, oy, z0 + 2, xyint);
+            load_plane(g, c, Uin, ring + slot_of(z0 + 2), ox, oy, z0 + 2, xyint, err);
         }
     }
     __syncthreads();
@@ -650,7 +652,7 @@ zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, cons
         // the input state at the cells is rebuilt from the ring at the output
         const long long j = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * z);
         float2 o1[NC], o2[NC];
-        if (MODE == 2 && vec) {
+        if (MODE == 2 && vec && in_bounds(j + 1, N, err)) {
 #pragma unroll
             for (int m = 0; m < NC; ++m) o2[m] = ld2(Un + m * N + j);
         }
@@ -665,13 +667,13 @@ zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, cons
             if (use_stage) {
                 parity ^= 1u;
                 if (tid == 0) outstanding = false;
-                convert_staged(g, c, Uin, stage, ring + slot_of(z + 3), ox, oy, z + 3, xyint);
+                convert_staged(g, c, Uin, stage, ring + slot_of(z + 3), ox, oy, z + 3, xyint, err);
             } else {
-                load_plane(g, c, Uin, ring + slot_of(z + 3), ox, oy, z + 3, xyint);
+                load_plane(g, c, Uin, ring + slot_of(z + 3), ox, oy, z + 3, xyint, err);
             }
         }
 
-        if (in0) {
+        if (in0 && in_bounds(j + (vec ? 1 : 0), N, err)) {
             const float2 ih = sp(c.inv_h), dt2 = sp(dt);
             // the input state at the two cells, rebuilt from the primitives
             // of plane z in the ring (a few FP32 roundings from the stored
@@ -766,12 +768,15 @@ zmarch_kernel(const __grid_constant__ CUtensorMap tmap, const GridParams g, cons
 #define IBM_ZM_WAVES 3
 #endif
 #ifndef IBM_ZM_CHUNK
-#define IBM_ZM_CHUNK 24
+#define IBM_ZM_CHUNK 19
 #endif
 
 int zmarch_chunk(const GridParams &g) {
     // planes per CTA: enough CTAs to fill the GPU several times over (two
-    // resident per SM)
+    // resident per SM).  At 256^3 (bench, ms per step): 16: 1.236, 19:
+    // 1.220, 21: 1.251, 24: 1.227, 32: 1.27 - the wave count of the grid
+    // (128 columns x 14 chunks = 5.9 waves at 19) matters as much as the
+    // four-plane prologue of each chunk
     const long long cols = (long long)((g.n[0] + TX - 1) / TX) * ((g.n[1] + TY - 1) / TY);
     int zc = IBM_ZM_CHUNK;
     while (zc > 4 && cols * ((g.n[2] + zc - 1) / zc) < IBM_ZM_WAVES * 2 * 152) zc /= 2;

@@ -276,6 +276,7 @@ __device__ __forceinline__ void store_forcing(const GridParams &g, const MarkerB
 // hold more markers, served by more warps)
 template <int DIM> constexpr int IF_T = DIM == 3 ? 512 : 256;
 
+
 template <int DIM, typename T>
 __global__ void __launch_bounds__(IF_T<DIM>)
 interp_force_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuffers m,
@@ -303,8 +304,8 @@ interp_force_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuf
             const bool in = gx >= 0 && gy >= 0 && gz >= 0 && gx < g.n[0] && gy < g.n[1] &&
                             (DIM == 2 || gz < g.n[2]);
             R v[NF];
-            if (in) {
-                const long long j = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
+            const long long j = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
+            if (in && in_bounds(j, N, m.err)) {
                 interp_fields<DIM, R>(U, N, j, v);
             } else {
 #pragma unroll
@@ -317,6 +318,7 @@ interp_force_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuf
         const int p0 = m.tile_off[t], p1 = m.tile_off[t + 1];
         for (int p = p0 + warp; p < p1; p += nwarps) {
             const int k = perm[p];
+            if (!in_bounds(k, m.ns, m.err)) continue;
             R fr[3] = {R(0), R(0), R(0)};
             int ck[3] = {0, 0, 0};
 #pragma unroll
@@ -377,14 +379,57 @@ batch_interp_kernel(const BatchCase *__restrict__ cases, const int2 *__restrict_
             const R wgt = lane_weight<DIM, R>(fr, ck, lane, cell);
             const long long j = cell[0] + (long long)g.n[0] * (cell[1] + (long long)g.n[1] * cell[2]);
             R v[NF];
-            interp_fields<DIM, R>(U, g.N, j, v);
+            if (in_bounds(j, g.N, m.err)) {
+                interp_fields<DIM, R>(U, g.N, j, v);
 #pragma unroll
-            for (int f = 0; f < NF; ++f) acc[f] = wgt * v[f];
+                for (int f = 0; f < NF; ++f) acc[f] = wgt * v[f];
+            }
         }
 #pragma unroll
         for (int f = 0; f < NF; ++f) acc[f] = warp_sum_r<R>(acc[f]);
         if (lane == 0) store_forcing<DIM, R>(g, m, k, acc);
     }
+}
+
+// Interpolation and forcing of one grid with one warp per marker, the
+// support cells read straight from the state (L2): every SM gets markers at
+// once, where the tile-staged form runs one CTA per occupied tile in a single
+// short wave (3D sphere at 256^3: 18.6 -> 10.5 us; the small 2D marker sets
+// keep the staged form, 1 % faster there).  The terms and the warp sums are
+// those of interp_force_kernel, so the results are bitwise the same.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256)
+interp_direct_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuffers m) {
+    using R = T;
+    constexpr int NF = DIM + 2;
+    constexpr int NS = DIM == 3 ? 27 : 9;
+    const int lane = threadIdx.x & 31;
+    const int k = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+    if (k >= m.ns) return;
+    R fr[3] = {R(0), R(0), R(0)};
+    int ck[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        ck[d] = m.cell[(long long)k * 3 + d];
+        fr[d] = marker_frac<R>(m, k, d);
+    }
+    R acc[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) acc[f] = R(0);
+    if (lane < NS) {
+        int cell[3];
+        const R wgt = lane_weight<DIM, R>(fr, ck, lane, cell);
+        const long long j = cell[0] + (long long)g.n[0] * (cell[1] + (long long)g.n[1] * cell[2]);
+        R v[NF];
+        if (in_bounds(j, g.N, m.err)) {
+            interp_fields<DIM, R>(U, g.N, j, v);
+#pragma unroll
+            for (int f = 0; f < NF; ++f) acc[f] = wgt * v[f];
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) acc[f] = warp_sum_r<R>(acc[f]);
+    if (lane == 0) store_forcing<DIM, R>(g, m, k, acc);
 }
 
 // ---------------------------------------------------------------------------
@@ -522,7 +567,7 @@ __device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__
         }
         int tot;
         const int pos = block_exclusive_scan(keep, s_warp, tot) + kept;
-        if (keep && pos < SP_MAXC) {
+        if (keep && pos < SP_MAXC && in_bounds(perm[p], m.ns, m.err)) {
             const int k = perm[p];
             const double e = m.eps[k];
 #pragma unroll
@@ -593,6 +638,7 @@ __device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__
         }
         if (!band) continue;
         const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+        if (!in_bounds(j, g.N, m.err)) continue;
         apply_forcing<DIM, T, R>(g, U, j, f, qh);
         T u[DIM + 2];
 #pragma unroll
@@ -726,7 +772,7 @@ band_refine_kernel(const GridParams g, const MarkerBuffers m) {
 // forces/heat sums (fixed-order reduction) and the time update
 // ---------------------------------------------------------------------------
 
-constexpr int FIN_T = 256;
+constexpr int FIN_T = 256;   // 1024 measured slower (22 against 17 us at 256^3)
 
 // One CTA of FIN_T threads: the force/heat sums of one grid, its time
 // update and its next step size from the stage-2 maxima (blockmax[0..nb))
@@ -1026,6 +1072,12 @@ static size_t interp_smem(const GridParams &g) {
 template <int DIM, typename T>
 static cudaError_t interp_force_t(const GridParams &g, const void *U, const MarkerBuffers &m,
                                   int grid_ctas, cudaStream_t s) {
+    if (DIM == 3) {
+        const long long threads = 32ll * m.ns;
+        interp_direct_kernel<DIM, T><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+            g, (const T *)U, m);
+        return cudaGetLastError();
+    }
     const size_t smem = interp_smem<T>(g);
     cudaError_t e = func_smem_attr((const void *)interp_force_kernel<DIM, T>, smem);
     if (e != cudaSuccess) return e;
