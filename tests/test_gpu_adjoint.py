@@ -240,6 +240,76 @@ def test_backward_matches_gpu_finite_differences():
         assert abs(gT[k] - fd) <= 1e-4 * abs(fd) + 1e-6 * np.abs(gT).max(), (k, gT[k], fd)
 
 
+def test_backward_at_the_benchmark_size_matches_central_differences():
+    """The 128^3 adjoint sphere (804 markers, 698 kept) in FP64, 20 recorded
+    steps with a checkpoint every 10 (two replayed segments): central
+    differences of the GPU's own J with the recorded step sizes held fixed,
+    on 16 seeded (marker, axis) draws that keep the marker in its owner cell
+    and 8 wall temperatures; gate 1e-4 relative with a floor of 1e-6 of the
+    largest entry.  J is only piecewise smooth here: 20 steps after the
+    impulsive start, limiter and Rusanov-max switches sit within 1e-6 of some
+    draws (at h = 1e-6 the one-sided differences of 2 of the 16 draws
+    disagree by ~1e-3), so the step is h = 1e-7, where the central
+    differences resolve the local branch and the FP64 rounding of J (~1e-13)
+    stays below 1e-5 of the entries.  The weights are solved to a residual
+    of 1e-14 (ibm_set_quadrature) to keep the solver's own noise out too."""
+    import dataclasses
+    c = C.adjoint_sphere()
+    g = dataclasses.replace(c.grid, fp_bytes=8)
+    a, b = 1.0, 0.5
+    tol = 1e-14
+    U0 = C.initial_state(g, c.seed)
+    grid = ibm.Grid(g, max_markers=len(c.X))
+    grid.set_quadrature(tol, 20000)
+    grid.set_markers(c.X, c.Tw)
+    grid.set_state(U0)
+    grid.record(20, 10)
+    dts = []
+    for _ in range(20):
+        grid.step(1)
+        dts.append(grid.time()[0])
+    Xk, _, idx = grid.markers()
+    Twk = np.asarray(c.Tw)[idx]
+    gX, gT = grid.backward(a, b)
+    grid.close()
+
+    def J_of(Xp, Twp):
+        gr = ibm.Grid(g, max_markers=len(Xp))
+        gr.set_quadrature(tol, 20000)
+        gr.set_markers(Xp, Twp, dedup=False)
+        gr.set_state(U0)
+        for dt in dts:
+            gr.step(1, dt_fixed=dt)
+        f = gr.forces()
+        gr.close()
+        return a * f["Cd"] + b * f["Nu"]
+
+    lo = np.array(g.lo[:3])
+    rng = np.random.default_rng(11)
+    d = 1e-7
+    done = 0
+    while done < 16:
+        k, ax = int(rng.integers(len(Xk))), int(rng.integers(3))
+        cell = np.floor((Xk[k, ax] - lo[ax]) / g.h)
+        if (np.floor((Xk[k, ax] + d - lo[ax]) / g.h) != cell or
+                np.floor((Xk[k, ax] - d - lo[ax]) / g.h) != cell):
+            continue
+        Xp, Xm = Xk.copy(), Xk.copy()
+        Xp[k, ax] += d
+        Xm[k, ax] -= d
+        fd = (J_of(Xp, Twk) - J_of(Xm, Twk)) / (2 * d)
+        assert abs(gX[k, ax] - fd) <= 1e-4 * abs(fd) + 1e-6 * np.abs(gX).max(), \
+            (k, ax, gX[k, ax], fd)
+        done += 1
+    for _ in range(8):
+        k = int(rng.integers(len(Xk)))
+        Tp, Tm = Twk.copy(), Twk.copy()
+        Tp[k] += d
+        Tm[k] -= d
+        fd = (J_of(Xk, Tp) - J_of(Xk, Tm)) / (2 * d)
+        assert abs(gT[k] - fd) <= 1e-4 * abs(fd) + 1e-6 * np.abs(gT).max(), (k, gT[k], fd)
+
+
 def test_autograd_function_returns_the_adjoint_gradient():
     g, X, Tw, seed = cylinder(8)
     U0 = C.initial_state(g, seed)
