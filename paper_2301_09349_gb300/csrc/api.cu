@@ -158,6 +158,12 @@ void layout(ibm_grid *g, const ibm_grid_desc &d, int cap, char *base, size_t *to
     m.counts = c.take<int>(4);
     m.sums = c.take<double>(16);
     m.bandmax = c.take<double>(kMaxPersistentCtas);
+    m.finpart = c.take<double>((size_t)kFinishCtas * 5);
+    m.gs = c.take<double>((size_t)cap * 4);
+    m.sp_cap = (dim == 3 ? 27 : 9) * (cap > 0 ? cap : 1);
+    m.sp_cell = c.take<SpreadCell>((size_t)m.sp_cap);
+    m.sp_k = c.take<int>((size_t)m.sp_cap);
+    m.sp_w = c.take<double>((size_t)m.sp_cap);
     m.band_bits = c.take<unsigned>((size_t)(gp.N / 32 + 1));
     m.t = c.take<double>(1);
     m.steps = c.take<long long>(1);
@@ -283,6 +289,13 @@ ibm_status rebuild_markers(ibm_grid *g, int warm, cudaStream_t s) {
     CU(launch_band_mask(g->gp, g->mb, persistent_ctas(g), s), "band mask");
     if (g->mb.ns > 0)
         CU(launch_quadrature(g->gp, g->mb, g->qb, g->cg_tol, g->cg_maxit, warm, s), "quadrature");
+    // static markers: their spreading operator, once per marker set
+    g->mb.sp_ready = 0;
+    if (!g->moving && g->mb.ns > 0) {
+        CU(launch_spread_build(g->gp, g->desc.fp_bytes, g->mb, persistent_ctas(g), s),
+           "spreading operator");
+        g->mb.sp_ready = 1;
+    }
     return IBM_OK;
 }
 ibm_status rebuild_markers(ibm_grid *g, int warm) { return rebuild_markers(g, warm, g->stream); }
@@ -551,9 +564,11 @@ ibm_status ibm_set_markers(ibm_grid *g, int n, const double *X0, const double *U
     g->moving = motion != nullptr;
     if (motion) g->motion = *motion;
     ibm_status st = rebuild_markers(g, 0);
-    if (st != IBM_OK) return st;
-    st = check_device(g);
-    if (st != IBM_OK) return st;
+    if (st == IBM_OK) st = check_device(g);
+    if (st != IBM_OK) {
+        g->mb.sp_ready = 0;
+        return st;
+    }
     if (n_kept) *n_kept = ns;
     return IBM_OK;
 }

@@ -27,7 +27,8 @@ cudaError_t func_smem_attr(const void *func, size_t smem, int carveout = -1);
 // state at the start of the step.
 struct FluidBuffers {
     double *blockmax;            // per-CTA maxima (stage 2, dt_init)
-    unsigned *counter;           // last-block ticket of dt_init (zero between launches)
+    unsigned *counter;           // last-block tickets (zero between launches): [0] dt_init,
+                                 // [1] the finish kernel
     double *dt;                  // device step size of the next step
     int *err;                    // device error word
     const unsigned *band_bits;   // one bit per cell changed by the forcing
@@ -127,6 +128,14 @@ __device__ __forceinline__ bool band_bit(const unsigned *bits, long long j) {
 }
 
 // ---- markers (markers.cu) --------------------------------------------------
+// One forced cell of the precomputed spreading operator of static markers:
+// its global index and its run [start, start + n) of (marker, weight)
+// entries.
+struct SpreadCell {
+    long long j;
+    int start, n;
+};
+
 struct MarkerBuffers {
     int ns;                  // kept markers
     double *X0, *X;          // ns*dim positions at t = 0 and now
@@ -144,10 +153,19 @@ struct MarkerBuffers {
     int *tile_off;           // n_tiles + 1
     int *occ_flag, *band_flag;  // n_tiles
     int *occ_list, *band_list;  // n_tiles
-    int *counts;             // [0] occupied tiles, [1] band tiles
+    int *counts;             // [0] occupied tiles, [1] band tiles, [2] operator cells,
+                             // [3] operator entries
     double *sums;            // [0..2] sum eps~ G, [3] sum eps~ H, [4] dt of those sums;
                              // [8..11] the first stage's sums (forcing per stage)
     double *bandmax;         // per-CTA step-size maxima of the spread kernel
+    double *finpart;         // kFinishCtas x 5 partials of the split finish kernel
+    void *gs;                // ns x 4 eps~-scaled forcing in the field precision: eps~ G_d
+                             // (d < dim), eps~ H at [3] (written by the interpolation)
+    SpreadCell *sp_cell;     // forced cells of the spreading operator (counts[2] of them)
+    int *sp_k;               // marker of each operator entry (counts[3] of them)
+    void *sp_w;              // weight of each entry, field precision
+    int sp_cap;              // capacity of cells and of entries: 3^dim x marker capacity
+    int sp_ready;            // the operator matches the current (static) markers
     unsigned *band_bits;     // one bit per cell inside some marker support
     double *t;               // simulated time
     long long *steps;        // step counter
@@ -161,12 +179,19 @@ cudaError_t launch_band_mask(const GridParams &g, const MarkerBuffers &m, int gr
 cudaError_t launch_bin(const GridParams &g, MarkerBuffers &m, cudaStream_t s);
 cudaError_t launch_interp_force(const GridParams &g, int fp_bytes, const void *U,
                                 const MarkerBuffers &m, int grid_ctas, cudaStream_t s);
+// spreading and forced update: through the precomputed operator when
+// m.sp_ready, else gathering straight from the binned markers
 cudaError_t launch_spread_apply(const GridParams &g, int fp_bytes, void *U,
                                 const MarkerBuffers &m, int grid_ctas, cudaStream_t s);
+// the spreading operator of the current (static) markers, from their bins
+cudaError_t launch_spread_build(const GridParams &g, int fp_bytes, const MarkerBuffers &m,
+                                int grid_ctas, cudaStream_t s);
 // sums[8..11] = sum eps~ G, sum eps~ H of the current G, H (fixed order)
 cudaError_t launch_partial_sums(const GridParams &g, const MarkerBuffers &m, cudaStream_t s);
 // force/heat sums, the time update and the next dt from the stage-2 and
-// band maxima (nbs = 0 when the spread kernel did not run)
+// band maxima (nbs = 0 when the spread kernel did not run), split over up to
+// kFinishCtas CTAs with a fixed-order combine
+constexpr int kFinishCtas = 32;
 cudaError_t launch_finish(const GridParams &g, const MarkerBuffers &m, const FluidBuffers &fb,
                           int nb, int nbs, double dt_fixed, cudaStream_t s);
 // cp[k] = (I[p]_k - p_inf) / (rho_inf U_inf^2 / 2) at every marker

@@ -265,11 +265,19 @@ template <int DIM, typename R>
 __device__ __forceinline__ void store_forcing(const GridParams &g, const MarkerBuffers &m, int k,
                                               const R (&acc)[DIM + 2]) {
     const double rk = (double)acc[0];
+    const double e = m.eps[k];
+    R *gs = reinterpret_cast<R *>(m.gs) + 4 * (long long)k;
     m.rhoL[k] = rk;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d)
-        m.G[(long long)k * DIM + d] = rk * m.Ub[(long long)k * DIM + d] - (double)acc[1 + d];
-    m.H[k] = rk * g.cv * m.Tw[k] - (double)acc[DIM + 1];
+    for (int d = 0; d < DIM; ++d) {
+        const double Gd = rk * m.Ub[(long long)k * DIM + d] - (double)acc[1 + d];
+        m.G[(long long)k * DIM + d] = Gd;
+        gs[d] = (R)(Gd * e);
+    }
+    if (DIM == 2) gs[2] = R(0);
+    const double H = rk * g.cv * m.Tw[k] - (double)acc[DIM + 1];
+    m.H[k] = H;
+    gs[3] = (R)(H * e);
 }
 
 // threads of the staged interpolation (one CTA per occupied tile; 3D tiles
@@ -445,7 +453,7 @@ constexpr int SP_MAXC = 1024;   // staged candidates per band tile
 template <typename R>
 size_t spread_smem_bytes(const GridParams &g) {
     const size_t bn = (size_t)(g.tile[0] + 2) * (g.tile[1] + 2) * (g.dim == 3 ? g.tile[2] + 2 : 1);
-    return SP_MAXC * (7 * sizeof(R) + sizeof(int)) + 2 * bn * sizeof(int);
+    return SP_MAXC * (7 * sizeof(R) + 2 * sizeof(int)) + 2 * bn * sizeof(int);
 }
 
 // Forced update of one band cell (App. B, Eqs. u_centralF2 and e_centralF2;
@@ -480,7 +488,8 @@ __device__ __forceinline__ void apply_forcing(const GridParams &g, T *__restrict
 template <typename R>
 struct SpreadSmem {
     R *fr, *g, *h;                // [3][SP_MAXC] offsets, [3][SP_MAXC] eps~ G, [SP_MAXC] eps~ H
-    int *cell, *head, *len;       // [SP_MAXC] owner cell in box, [bn], [bn]
+    int *cell, *k;                // [SP_MAXC] owner cell in box, [SP_MAXC] marker
+    int *head, *len;              // [bn], [bn]
     int *cnt, *start, *warp;      // [NT3 + 1], [NT3], [33]
 };
 
@@ -493,7 +502,8 @@ __device__ __forceinline__ SpreadSmem<R> spread_smem(unsigned char *raw, const G
     sm.g = sm.fr + 3 * SP_MAXC;
     sm.h = sm.g + 3 * SP_MAXC;
     sm.cell = reinterpret_cast<int *>(sm.h + SP_MAXC);
-    sm.head = sm.cell + SP_MAXC;
+    sm.k = sm.cell + SP_MAXC;
+    sm.head = sm.k + SP_MAXC;
     sm.len = sm.head + bn;
     sm.cnt = cnt;
     sm.start = start;
@@ -501,15 +511,17 @@ __device__ __forceinline__ SpreadSmem<R> spread_smem(unsigned char *raw, const G
     return sm;
 }
 
-// Spreading and the forced update of the cells of marker tile t; smax
-// collects the step-size rates of the forced cells.  Every thread calls it.
-template <int DIM, typename T>
-__device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__ U,
-                                            const MarkerBuffers &m,
-                                            const unsigned *__restrict__ keys,
-                                            const int *__restrict__ perm, int t,
-                                            const SpreadSmem<T> &sm, double &smax, bool &ok) {
-    using R = T;
+// Candidates of marker tile t: stage, in bin order, the markers whose owner
+// cell lies in the tile grown by one cell (their supports reach the tile),
+// then the runs of candidates per owner cell.  o receives the tile's first
+// cell; returns true when the candidates overflowed the staging area (the
+// caller then gathers from global memory).  Every thread calls it; it ends
+// with a barrier.
+template <int DIM, typename R>
+__device__ __forceinline__ bool spread_stage(const GridParams &g, const MarkerBuffers &m,
+                                             const unsigned *__restrict__ keys,
+                                             const int *__restrict__ perm, int t,
+                                             const SpreadSmem<R> &sm, int o[3]) {
     constexpr int NT3 = DIM == 3 ? 27 : 9;
     const int bx = g.tile[0] + 2, by = g.tile[1] + 2, bz = DIM == 3 ? g.tile[2] + 2 : 1;
     const int bn = bx * by * bz;
@@ -520,7 +532,9 @@ __device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__
     const int cpt = g.cells_per_tile;
     const int tx = t % g.ntile[0], ty = (t / g.ntile[0]) % g.ntile[1],
               tz = t / (g.ntile[0] * g.ntile[1]);
-    const int o[3] = {tx * g.tile[0], ty * g.tile[1], DIM == 3 ? tz * g.tile[2] : 0};
+    o[0] = tx * g.tile[0];
+    o[1] = ty * g.tile[1];
+    o[2] = DIM == 3 ? tz * g.tile[2] : 0;
     // 1. bin ranges of the neighbour tiles (z, y, x order)
     if (tid < NT3) {
         const int ux = tx + tid % 3 - 1, uy = ty + (tid / 3) % 3 - 1,
@@ -577,6 +591,7 @@ __device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__
             }
             s_h[pos] = (R)(m.H[k] * e);
             s_cell[pos] = lc;
+            sm.k[pos] = k;
         }
         kept += tot;
     }
@@ -596,6 +611,54 @@ __device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__
         }
     }
     __syncthreads();
+    return overflow;
+}
+
+// The staged candidates of local cell l of a tile (l in [0, tile)) in the
+// gather order - owner cells by z, y, x offset from -1 to +1, then bin order
+// - as visit(slot, w) with w the weight of that marker at the cell.  Returns
+// whether there was any.
+template <int DIM, typename R, typename F>
+__device__ __forceinline__ bool visit_staged(const GridParams &g, const SpreadSmem<R> &sm,
+                                             const int l[3], F &&visit) {
+    const int bx = g.tile[0] + 2, by = g.tile[1] + 2;
+    bool any = false;
+    const int zr = DIM == 3 ? 1 : 0;
+    for (int oz = -zr; oz <= zr; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+                const int lc = (l[0] + 1 + ox) +
+                               bx * ((l[1] + 1 + oy) + by * (DIM == 3 ? l[2] + 1 + oz : 0));
+                const int h0 = sm.head[lc];
+                if (h0 < 0) continue;
+                const int h1 = h0 + sm.len[lc];
+                const int oo[3] = {-ox, -oy, -oz};   // this cell seen from the owner cell
+                for (int i = h0; i < h1; ++i) {
+                    R w = R(1);
+#pragma unroll
+                    for (int d = 0; d < DIM; ++d)
+                        w *= phi_r<R>(cell_offset<R>(oo[d], sm.fr[d * SP_MAXC + i]));
+                    visit(i, w);
+                    any = true;
+                }
+            }
+    return any;
+}
+
+// Spreading and the forced update of the cells of marker tile t; smax
+// collects the step-size rates of the forced cells.  Every thread calls it.
+template <int DIM, typename T>
+__device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__ U,
+                                            const MarkerBuffers &m,
+                                            const unsigned *__restrict__ keys,
+                                            const int *__restrict__ perm, int t,
+                                            const SpreadSmem<T> &sm, double &smax, bool &ok) {
+    using R = T;
+    const R *s_g = sm.g, *s_h = sm.h;
+    const int tid = threadIdx.x;
+    const int cpt = g.cells_per_tile;
+    int o[3];
+    const bool overflow = spread_stage<DIM, R>(g, m, keys, perm, t, sm, o);
     // 4. gather per cell in the fixed order, then the forced update
     for (int q = tid; q < cpt; q += SP_T<DIM>) {
         const int l[3] = {q % g.tile[0], (q / g.tile[0]) % g.tile[1],
@@ -607,27 +670,11 @@ __device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__
         for (int d = 0; d < DIM; ++d) f[d] = R(0);
         bool band = false;
         if (!overflow) {
-            const int zr = DIM == 3 ? 1 : 0;
-            for (int oz = -zr; oz <= zr; ++oz)
-                for (int oy = -1; oy <= 1; ++oy)
-                    for (int ox = -1; ox <= 1; ++ox) {
-                        const int lc = (l[0] + 1 + ox) +
-                                       bx * ((l[1] + 1 + oy) + by * (DIM == 3 ? l[2] + 1 + oz : 0));
-                        const int h0 = s_head[lc];
-                        if (h0 < 0) continue;
-                        const int h1 = h0 + s_len[lc];
-                        const int oo[3] = {-ox, -oy, -oz};   // this cell seen from the owner cell
-                        for (int i = h0; i < h1; ++i) {
-                            R w = R(1);
+            band = visit_staged<DIM, R>(g, sm, l, [&](int i, R w) {
 #pragma unroll
-                            for (int d = 0; d < DIM; ++d)
-                                w *= phi_r<R>(cell_offset<R>(oo[d], s_fr[d * SP_MAXC + i]));
-#pragma unroll
-                            for (int d = 0; d < DIM; ++d) f[d] += s_g[d * SP_MAXC + i] * w;
-                            qh += s_h[i] * w;
-                            band = true;
-                        }
-                    }
+                for (int d = 0; d < DIM; ++d) f[d] += s_g[d * SP_MAXC + i] * w;
+                qh += s_h[i] * w;
+            });
         } else {
             band = gather_markers<DIM, R>(g, m, keys, perm, c, [&](int k, R w) {
                 const double e = m.eps[k];
@@ -676,6 +723,145 @@ spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m
     }
 }
 
+
+// The spreading operator of static markers, built once per marker set: for
+// every forced cell its (marker, weight) entries in the gather order of
+// spread_tile, so that the spreading of a step is a plain gather over them.
+// Cells and entry runs are allocated by atomics per block of cells, so their
+// placement varies between builds but no cell's run does.  counts[2..3]
+// must be zero on entry.  A marker reaches 3^dim cells, so 3^dim x markers
+// (sp_cap) bounds both the cells and the entries; a block that would pass
+// it records ERR_BOUNDS and writes nothing (its records stay empty).
+template <int DIM, typename T>
+__global__ void __launch_bounds__(SP_T<DIM>)
+spread_build_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__restrict__ keys,
+                    const int *__restrict__ perm) {
+    using R = T;
+    constexpr int NT3 = DIM == 3 ? 27 : 9;
+    extern __shared__ __align__(16) unsigned char smem_sp[];
+    __shared__ int s_cnt[NT3 + 1], s_start[NT3], s_warp[33];
+    __shared__ int s_base[2];
+    const SpreadSmem<R> sm = spread_smem<R>(smem_sp, g, s_cnt, s_start, s_warp);
+    const int tid = threadIdx.x;
+    const int cpt = g.cells_per_tile;
+    R *w_out = reinterpret_cast<R *>(m.sp_w);
+    const int n_band = m.counts[1];
+    for (int it = blockIdx.x; it < n_band; it += gridDim.x) {
+        int o[3];
+        const bool overflow = spread_stage<DIM, R>(g, m, keys, perm, m.band_list[it], sm, o);
+        for (int q0 = 0; q0 < cpt; q0 += SP_T<DIM>) {
+            const int q = q0 + tid;
+            const int l[3] = {q % g.tile[0], (q / g.tile[0]) % g.tile[1],
+                              DIM == 3 ? q / (g.tile[0] * g.tile[1]) : 0};
+            const int c[3] = {o[0] + l[0], o[1] + l[1], o[2] + l[2]};
+            const bool inside = q < cpt && c[0] < g.n[0] && c[1] < g.n[1] &&
+                                (DIM == 2 || c[2] < g.n[2]);
+            int n = 0;
+            if (inside) {
+                if (!overflow) visit_staged<DIM, R>(g, sm, l, [&](int, R) { ++n; });
+                else gather_markers<DIM, R>(g, m, keys, perm, c, [&](int, R) { ++n; });
+            }
+            int tot_c, tot_e;
+            const int co = block_exclusive_scan(n > 0 ? 1 : 0, s_warp, tot_c);
+            const int eo = block_exclusive_scan(n, s_warp, tot_e);
+            if (tid == 0) {
+                s_base[0] = tot_c > 0 ? atomicAdd(m.counts + 2, tot_c) : 0;
+                s_base[1] = tot_e > 0 ? atomicAdd(m.counts + 3, tot_e) : 0;
+            }
+            __syncthreads();
+            const long long bc = s_base[0], be = s_base[1];
+            if (bc + tot_c > m.sp_cap || be + tot_e > m.sp_cap) {
+                if (tid == 0) record_error(m.err, ERR_BOUNDS);
+            } else if (n > 0) {
+                const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+                int p = (int)be + eo;
+                m.sp_cell[bc + co] = SpreadCell{j, p, n};
+                if (!overflow) {
+                    visit_staged<DIM, R>(g, sm, l, [&](int i, R w) {
+                        m.sp_k[p] = sm.k[i];
+                        w_out[p] = w;
+                        ++p;
+                    });
+                } else {
+                    gather_markers<DIM, R>(g, m, keys, perm, c, [&](int k, R w) {
+                        m.sp_k[p] = k;
+                        w_out[p] = w;
+                        ++p;
+                    });
+                }
+            }
+            __syncthreads();   // s_base is taken again by the next block of cells
+        }
+    }
+}
+
+__device__ __forceinline__ void load4(const float *p, float v[4]) {
+    const float4 x = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+}
+__device__ __forceinline__ void load4(const double *p, double v[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+}
+
+// Spreading and forced update of static markers through their operator:
+// one thread per forced cell sums its entries in the stored order (the
+// terms and the order of spread_tile, so the results are bitwise the same),
+// then applies the forcing.  One step-size maximum per CTA in bandmax.
+constexpr int SPS_T = 256;
+template <int DIM, typename T>
+__global__ void __launch_bounds__(SPS_T)
+spread_static_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m) {
+    using R = T;
+    __shared__ double s_max[SPS_T / 32];
+    const int nc = min(m.counts[2], m.sp_cap);
+    const R *gs = reinterpret_cast<const R *>(m.gs);
+    const R *ew = reinterpret_cast<const R *>(m.sp_w);
+    double smax = 0.0;
+    bool ok = true;
+    for (int i = blockIdx.x * SPS_T + threadIdx.x; i < nc; i += gridDim.x * SPS_T) {
+        const SpreadCell rc = m.sp_cell[i];
+        if (rc.n <= 0) continue;
+        R f[DIM], qh = R(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) f[d] = R(0);
+        for (int p = rc.start; p < rc.start + rc.n; ++p) {
+            if (!in_bounds(p, m.sp_cap, m.err)) break;
+            const int k = __ldg(m.sp_k + p);
+            const R w = __ldg(ew + p);
+            if (!in_bounds(k, m.ns, m.err)) continue;
+            R v[4];
+            load4(gs + 4 * (long long)k, v);
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) f[d] += v[d] * w;
+            qh += v[3] * w;
+        }
+        if (!in_bounds(rc.j, g.N, m.err)) continue;
+        apply_forcing<DIM, T, R>(g, U, rc.j, f, qh);
+        T u[DIM + 2];
+#pragma unroll
+        for (int cc = 0; cc < DIM + 2; ++cc) u[cc] = U[cc * g.N + rc.j];
+        smax = fmax(smax, (double)step_rate<DIM, T>(g, u, ok));
+    }
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o2));
+    const int bad = __syncthreads_or(!ok);
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = smax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = s_max[0];
+        for (int w = 1; w < SPS_T / 32; ++w) mx = fmax(mx, s_max[w]);
+        m.bandmax[blockIdx.x] = mx;
+        if (bad) record_error(m.err, ERR_NONFINITE);
+    }
+}
 
 // Batched form: items are (case, position in the case's band list); one
 // step-size maximum per item.
@@ -774,28 +960,31 @@ band_refine_kernel(const GridParams g, const MarkerBuffers m) {
 
 constexpr int FIN_T = 256;   // 1024 measured slower (22 against 17 us at 256^3)
 
-// One CTA of FIN_T threads: the force/heat sums of one grid, its time
-// update and its next step size from the stage-2 maxima (blockmax[0..nb))
-// and the forced-cell maxima (bandmax[0..nbs)).
-__device__ __forceinline__ void finish_grid(const GridParams &g, int ns, const MarkerBuffers &m,
-                                            const double *__restrict__ blockmax, int nb,
-                                            const double *__restrict__ bandmax, int nbs,
-                                            double *__restrict__ dt_ptr, int *__restrict__ err,
-                                            double dt_fixed, double (*s)[FIN_T / 32]) {
+// Partial force/heat sums of markers [k0, k1) and the maxima of
+// blockmax[b0, b1) and bandmax[c0, c1) by one CTA: a[0..dim) = sum eps~ G,
+// a[3] = sum eps~ H, a[4] = max rate, valid in warp 0 on return.  The
+// markers are summed in a fixed order (thread stride, then a warp tree, then
+// a tree over the warps), so the result does not depend on timing.
+__device__ __forceinline__ void finish_partial(const GridParams &g, const MarkerBuffers &m,
+                                               int k0, int k1,
+                                               const double *__restrict__ blockmax, int b0, int b1,
+                                               const double *__restrict__ bandmax, int c0, int c1,
+                                               double (*s)[FIN_T / 32], double a[5]) {
     const int dim = g.dim;
-    double a[5] = {0, 0, 0, 0, 0};   // sums of eps~ G (dim), eps~ H; a[4] = max rate
-    // markers k = tid, tid + FIN_T, ... summed in that order; the loads of
-    // FIN_B of them are issued together, so the latency is paid once per
-    // batch rather than once per marker
+#pragma unroll
+    for (int i = 0; i < 5; ++i) a[i] = 0.0;
+    // markers k0 + tid, k0 + tid + FIN_T, ...; the loads of FIN_B of them
+    // are issued together, so the latency is paid once per batch rather
+    // than once per marker
     constexpr int FIN_B = 4;
-    for (int k0 = threadIdx.x; k0 < ns; k0 += FIN_B * FIN_T) {
+    for (int kb = k0 + (int)threadIdx.x; kb < k1; kb += FIN_B * FIN_T) {
         double e[FIN_B], gq[FIN_B][4];
 #pragma unroll
         for (int i = 0; i < FIN_B; ++i) {
-            const int k = k0 + i * FIN_T;
+            const int k = kb + i * FIN_T;
             e[i] = 0.0;
             gq[i][0] = gq[i][1] = gq[i][2] = gq[i][3] = 0.0;
-            if (k < ns) {
+            if (k < k1) {
                 e[i] = __ldg(m.eps + k);
 #pragma unroll
                 for (int d = 0; d < 3; ++d)
@@ -805,7 +994,7 @@ __device__ __forceinline__ void finish_grid(const GridParams &g, int ns, const M
         }
 #pragma unroll
         for (int i = 0; i < FIN_B; ++i) {
-            if (k0 + i * FIN_T >= ns) break;
+            if (kb + i * FIN_T >= k1) break;
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 if (d < dim) a[d] += e[i] * gq[i][d];
@@ -813,20 +1002,8 @@ __device__ __forceinline__ void finish_grid(const GridParams &g, int ns, const M
         }
     }
     // maxima: the order does not matter
-    for (int b = threadIdx.x; b < nb; b += FIN_B * FIN_T) {
-        double v[FIN_B];
-#pragma unroll
-        for (int i = 0; i < FIN_B; ++i) v[i] = b + i * FIN_T < nb ? __ldg(blockmax + b + i * FIN_T) : 0.0;
-#pragma unroll
-        for (int i = 0; i < FIN_B; ++i) a[4] = fmax(a[4], v[i]);
-    }
-    for (int b = threadIdx.x; b < nbs; b += FIN_B * FIN_T) {
-        double v[FIN_B];
-#pragma unroll
-        for (int i = 0; i < FIN_B; ++i) v[i] = b + i * FIN_T < nbs ? __ldg(bandmax + b + i * FIN_T) : 0.0;
-#pragma unroll
-        for (int i = 0; i < FIN_B; ++i) a[4] = fmax(a[4], v[i]);
-    }
+    for (int b = b0 + (int)threadIdx.x; b < b1; b += FIN_T) a[4] = fmax(a[4], __ldg(blockmax + b));
+    for (int b = c0 + (int)threadIdx.x; b < c1; b += FIN_T) a[4] = fmax(a[4], __ldg(bandmax + b));
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
 #pragma unroll
@@ -848,20 +1025,76 @@ __device__ __forceinline__ void finish_grid(const GridParams &g, int ns, const M
         for (int i = 0; i < 4; ++i) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
         a[4] = fmax(a[4], __shfl_xor_sync(0xffffffffu, a[4], o));
     }
-    if (lane == 0) {
-        for (int i = 0; i < 4; ++i) {
-            // forcing per stage: the first stage's sources count with weight 1/2
-            m.sums[i] = g.forcing_per_stage ? a[i] + 0.5 * m.sums[8 + i] : a[i];
-        }
-        const double mx = a[4];
-        const double dt_used = dt_fixed > 0.0 ? dt_fixed : *dt_ptr;
-        m.sums[4] = dt_used;
-        *m.t += dt_used;
-        *m.steps += 1;
-        const bool good = mx > 0.0 && mx <= DBL_MAX && !(*err & ERR_NONFINITE);
-        if (!good) record_error(err, ERR_NONFINITE);
-        *dt_ptr = good ? g.cfl / mx : 0.0;
+}
+
+// The sums of a step, its time update and the next step size from the
+// largest rate mx (one thread).
+__device__ __forceinline__ void finish_update(const GridParams &g, const MarkerBuffers &m,
+                                              const double a[5], double *__restrict__ dt_ptr,
+                                              int *__restrict__ err, double dt_fixed) {
+    for (int i = 0; i < 4; ++i) {
+        // forcing per stage: the first stage's sources count with weight 1/2
+        m.sums[i] = g.forcing_per_stage ? a[i] + 0.5 * m.sums[8 + i] : a[i];
     }
+    const double mx = a[4];
+    const double dt_used = dt_fixed > 0.0 ? dt_fixed : *dt_ptr;
+    m.sums[4] = dt_used;
+    *m.t += dt_used;
+    *m.steps += 1;
+    const bool good = mx > 0.0 && mx <= DBL_MAX && !(__ldcg(err) & ERR_NONFINITE);
+    if (!good) record_error(err, ERR_NONFINITE);
+    *dt_ptr = good ? g.cfl / mx : 0.0;
+}
+
+// The finish of a grid is split into C chunks of its markers (and of its
+// maxima): chunk c covers [n c / C, n (c+1) / C).  C depends on the marker
+// count alone, so the split kernel of one grid and the one-CTA finish of a
+// batch case add the same partials in the same tree.
+__host__ __device__ __forceinline__ int finish_chunks(int ns) {
+    const int c = (ns + FIN_T - 1) / FIN_T;
+    return c < 1 ? 1 : (c > kFinishCtas ? kFinishCtas : c);
+}
+__host__ __device__ __forceinline__ int finish_cut(int n, int c, int C) {
+    return (int)((long long)n * c / C);
+}
+
+// Warp 0: the C chunk partials (lane c holds chunk c's, zeros above C)
+// combined as a fixed shuffle tree; the result in every lane.
+__device__ __forceinline__ void finish_combine(double a[5]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
+        a[4] = fmax(a[4], __shfl_xor_sync(0xffffffffu, a[4], o));
+    }
+}
+
+// One CTA: the force/heat sums of one grid, its time update and its next
+// step size from the stage-2 maxima (blockmax[0..nb)) and the forced-cell
+// maxima (bandmax[0..nbs)); the chunks one after another.
+__device__ __forceinline__ void finish_grid(const GridParams &g, int ns, const MarkerBuffers &m,
+                                            const double *__restrict__ blockmax, int nb,
+                                            const double *__restrict__ bandmax, int nbs,
+                                            double *__restrict__ dt_ptr, int *__restrict__ err,
+                                            double dt_fixed, double (*s)[FIN_T / 32],
+                                            double (*part)[5]) {
+    const int C = finish_chunks(ns);
+    for (int c = 0; c < C; ++c) {
+        double a[5];
+        finish_partial(g, m, finish_cut(ns, c, C), finish_cut(ns, c + 1, C), blockmax,
+                       finish_cut(nb, c, C), finish_cut(nb, c + 1, C), bandmax,
+                       finish_cut(nbs, c, C), finish_cut(nbs, c + 1, C), s, a);
+        if (threadIdx.x == 0)
+            for (int i = 0; i < 5; ++i) part[c][i] = a[i];
+        __syncthreads();   // s is taken again by the next chunk
+    }
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    double a[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) a[i] = lane < C ? part[lane][i] : 0.0;
+    finish_combine(a);
+    if (lane == 0) finish_update(g, m, a, dt_ptr, err, dt_fixed);
 }
 
 // sum eps~ G and sum eps~ H of the current marker forcing into sums[8..11],
@@ -896,11 +1129,37 @@ partial_sums_kernel(const GridParams g, const MarkerBuffers m) {
         for (int i = 0; i < 4; ++i) m.sums[8 + i] = a[i];
 }
 
+// Split form: CTA c of C = finish_chunks(ns) sums chunk c of the markers
+// and of the maxima into part[c]; the last CTA to finish (ticket) combines
+// the C partials as the fixed tree of finish_combine, so the sums do not
+// depend on which CTA comes last, and resets the ticket for the next launch.
 __global__ void __launch_bounds__(FIN_T)
 finish_kernel(const GridParams g, int ns, const MarkerBuffers m, const double *__restrict__ blockmax,
-              int nb, int nbs, double *__restrict__ dt_ptr, int *__restrict__ err, double dt_fixed) {
+              int nb, int nbs, double *__restrict__ dt_ptr, int *__restrict__ err, double dt_fixed,
+              double *__restrict__ part, unsigned *__restrict__ ticket) {
     __shared__ double s[5][FIN_T / 32];
-    finish_grid(g, ns, m, blockmax, nb, m.bandmax, nbs, dt_ptr, err, dt_fixed, s);
+    __shared__ int s_last;
+    const int C = gridDim.x, c = blockIdx.x;
+    double a[5];
+    finish_partial(g, m, finish_cut(ns, c, C), finish_cut(ns, c + 1, C), blockmax,
+                   finish_cut(nb, c, C), finish_cut(nb, c + 1, C), m.bandmax,
+                   finish_cut(nbs, c, C), finish_cut(nbs, c + 1, C), s, a);
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 5; ++i) part[c * 5 + i] = a[i];
+        __threadfence();
+        s_last = atomicAdd(ticket, 1u) == (unsigned)C - 1;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x >= 32) return;
+    __threadfence();
+    const int lane = threadIdx.x;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) a[i] = lane < C ? __ldcg(part + lane * 5 + i) : 0.0;
+    finish_combine(a);
+    if (lane == 0) {
+        finish_update(g, m, a, dt_ptr, err, dt_fixed);
+        *ticket = 0u;
+    }
 }
 
 // Batched form: CTA c finishes case c over its own stage and band items.
@@ -908,9 +1167,10 @@ __global__ void __launch_bounds__(FIN_T)
 batch_finish_kernel(const BatchCase *__restrict__ cases, const double *__restrict__ item_max,
                     const double *__restrict__ band_max, double dt_fixed) {
     __shared__ double s[5][FIN_T / 32];
+    __shared__ double part[kFinishCtas][5];
     const BatchCase &bc = cases[blockIdx.x];
     finish_grid(bc.g, bc.m.ns, bc.m, item_max + bc.item0, bc.nitems, band_max + bc.band0,
-                bc.nband, bc.dt, bc.err, dt_fixed, s);
+                bc.nband, bc.dt, bc.err, dt_fixed, s, part);
 }
 
 // The force sums, the step size they belong to and the time of every case
@@ -1098,6 +1358,10 @@ cudaError_t launch_interp_force(const GridParams &g, int fp_bytes, const void *U
 template <int DIM, typename T>
 static cudaError_t spread_apply_t(const GridParams &g, void *U, const MarkerBuffers &m,
                                   int grid_ctas, cudaStream_t s) {
+    if (m.sp_ready) {
+        spread_static_kernel<DIM, T><<<grid_ctas, SPS_T, 0, s>>>(g, (T *)U, m);
+        return cudaGetLastError();
+    }
     const size_t smem = spread_smem_bytes<T>(g);
     cudaError_t e = func_smem_attr((const void *)spread_apply_kernel<DIM, T>, smem);
     if (e != cudaSuccess) return e;
@@ -1116,9 +1380,36 @@ cudaError_t launch_spread_apply(const GridParams &g, int fp_bytes, void *U,
                          : spread_apply_t<2, double>(g, U, m, grid_ctas, s);
 }
 
+template <int DIM, typename T>
+static cudaError_t spread_build_t(const GridParams &g, const MarkerBuffers &m, int grid_ctas,
+                                  cudaStream_t s) {
+    // counts to zero; every cell record empty (n = 0), so a record that a
+    // failed block reserved but did not write is skipped
+    cudaError_t e = cudaMemsetAsync(m.counts + 2, 0, 2 * sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m.sp_cell, 0, sizeof(SpreadCell) * m.sp_cap, s);
+    if (e != cudaSuccess) return e;
+    const size_t smem = spread_smem_bytes<T>(g);
+    e = func_smem_attr((const void *)spread_build_kernel<DIM, T>, smem);
+    if (e != cudaSuccess) return e;
+    spread_build_kernel<DIM, T><<<grid_ctas, SP_T<DIM>, smem, s>>>(g, m, m.keys[m.sorted],
+                                                                m.perm[m.sorted]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spread_build(const GridParams &g, int fp_bytes, const MarkerBuffers &m,
+                                int grid_ctas, cudaStream_t s) {
+    if (m.ns <= 0) return cudaSuccess;
+    if (g.dim == 3)
+        return fp_bytes == 4 ? spread_build_t<3, float>(g, m, grid_ctas, s)
+                             : spread_build_t<3, double>(g, m, grid_ctas, s);
+    return fp_bytes == 4 ? spread_build_t<2, float>(g, m, grid_ctas, s)
+                         : spread_build_t<2, double>(g, m, grid_ctas, s);
+}
+
 cudaError_t launch_finish(const GridParams &g, const MarkerBuffers &m, const FluidBuffers &fb,
                           int nb, int nbs, double dt_fixed, cudaStream_t s) {
-    finish_kernel<<<1, FIN_T, 0, s>>>(g, m.ns, m, fb.blockmax, nb, nbs, fb.dt, fb.err, dt_fixed);
+    finish_kernel<<<finish_chunks(m.ns), FIN_T, 0, s>>>(g, m.ns, m, fb.blockmax, nb, nbs, fb.dt, fb.err, dt_fixed,
+                                      m.finpart, fb.counter + 1);
     return cudaGetLastError();
 }
 

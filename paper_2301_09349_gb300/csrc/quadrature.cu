@@ -265,39 +265,41 @@ size_t chol_smem(int ns) {
 // Cholesky of the diagonal block [c0, c0 + w) in place, by one warp: lane r
 // holds row c0 + r of the block in registers, and step k hands the pivot
 // column L_lk to the lanes by shuffles; 1 / L_kk into dinv, *bad set on a
-// pivot that is not positive
+// pivot that is not positive.  The row shifts left by one column per step
+// (a[l] holds column k + l at step k), so the pivot column is always a[0]
+// and every step runs the same loop body: a compact loop that stays in the
+// instruction cache, where the fully unrolled form (528 distinct
+// shuffle-update pairs, fetched once per solve) spent most of its time on
+// instruction fetch.  Same operations in the same order as the unrolled form.
 __device__ __forceinline__ void chol_diag_block(float *__restrict__ F, int ld, int c0, int w,
                                                 float *__restrict__ dinv, int lane, int *bad) {
     float a[CHOL_PB];
 #pragma unroll
     for (int l = 0; l < CHOL_PB; ++l)
         a[l] = (lane < w && l <= lane) ? F[(size_t)(c0 + lane) * ld + c0 + l] : 0.0f;
-#pragma unroll
-    for (int k = 0; k < CHOL_PB; ++k) {
-        if (k < w) {
-            const float d = __shfl_sync(0xffffffffu, a[k], k);
-            const bool good = d > 0.0f;
-            const float sd = good ? sqrtf(d) : 1.0f;
-            const float inv = 1.0f / sd;
-            if (lane == k) {
-                a[k] = sd;
-                dinv[c0 + k] = inv;
-                if (!good) *bad = 1;
-            } else if (lane > k) {
-                a[k] *= inv;
-            }
-            const float lk = a[k];
-#pragma unroll
-            for (int l = k + 1; l < CHOL_PB; ++l) {
-                const float llk = __shfl_sync(0xffffffffu, lk, l);
-                if (lane >= l) a[l] -= lk * llk;
-            }
+#pragma unroll 1
+    for (int k = 0; k < w; ++k) {
+        const float d = __shfl_sync(0xffffffffu, a[0], k);
+        const bool good = d > 0.0f;
+        const float sd = good ? sqrtf(d) : 1.0f;
+        const float inv = 1.0f / sd;
+        float lk = a[0];   // zero on the lanes above the diagonal
+        if (lane == k) {
+            lk = sd;
+            dinv[c0 + k] = inv;
+            if (!good) *bad = 1;
+        } else if (lane > k) {
+            lk = a[0] * inv;
         }
-    }
-    if (lane < w) {
+        if (lane >= k && lane < w) F[(size_t)(c0 + lane) * ld + c0 + k] = lk;
 #pragma unroll
-        for (int l = 0; l < CHOL_PB; ++l)
-            if (l <= lane) F[(size_t)(c0 + lane) * ld + c0 + l] = a[l];
+        for (int l = 1; l < CHOL_PB; ++l) {
+            const float llk = __shfl_sync(0xffffffffu, lk, (k + l) & 31);
+            if (lane >= k + l) a[l] -= lk * llk;
+        }
+#pragma unroll
+        for (int l = 0; l < CHOL_PB - 1; ++l) a[l] = a[l + 1];
+        a[CHOL_PB - 1] = 0.0f;
     }
 }
 
