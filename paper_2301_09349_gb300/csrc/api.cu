@@ -142,6 +142,7 @@ void layout(ibm_grid *g, const ibm_grid_desc &d, int cap, char *base, size_t *to
     m.cell = c.take<int>((size_t)cap * 3);
     m.frac_d = c.take<double>((size_t)cap * 3);
     m.frac_f = c.take<float>((size_t)cap * 3);
+    m.wphi = c.take<double>((size_t)cap * 9);
     m.rhoL = c.take<double>(cap);
     m.G = c.take<double>((size_t)cap * dim);
     m.H = c.take<double>(cap);
@@ -286,7 +287,7 @@ cudaError_t prof_collect(ibm_grid *g) {
 // Marker pipeline on the device: bins, then quadrature (warm start if asked).
 ibm_status rebuild_markers(ibm_grid *g, int warm, cudaStream_t s) {
     CU(launch_bin(g->gp, g->mb, s), "bin markers");
-    CU(launch_band_mask(g->gp, g->mb, persistent_ctas(g), s), "band mask");
+    CU(launch_band_mask(g->gp, g->mb, s), "band mask");
     if (g->mb.ns > 0)
         CU(launch_quadrature(g->gp, g->mb, g->qb, g->cg_tol, g->cg_maxit, warm, s), "quadrature");
     // static markers: their spreading operator, once per marker set
@@ -405,7 +406,7 @@ ibm_status ibm_create_grid(const ibm_grid_desc *desc, int max_markers, void *dev
     if (e == cudaSuccess) e = cudaMemsetAsync(g->mb.steps, 0, sizeof(long long), g->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->mb.counts, 0, 4 * sizeof(int), g->stream);
     if (e == cudaSuccess) e = launch_bin(g->gp, g->mb, g->stream);  // empty bins
-    if (e == cudaSuccess) e = launch_band_mask(g->gp, g->mb, 1, g->stream);
+    if (e == cudaSuccess) e = launch_band_mask(g->gp, g->mb, g->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
     if (e != cudaSuccess) {
         g_create_error = std::string("CUDA: ") + cudaGetErrorString(e);
@@ -620,12 +621,23 @@ ibm_status run_steps(ibm_grid *g, int nsteps, double dt_fixed, cudaStream_t s) {
         CU(launch_stage1(g->gp, fpb, Un, U1, g->fb, dt_fixed, s), "stage 1");
         CU(prof_end(g, rec), "profile");
         if (g->moving && g->mb.ns > 0) {
-            CU(prof_begin(g, IBM_PROF_MARKERS, 8, &rec), "profile");
-            CU(launch_motion(g->gp, g->mb, g->motion.amp, g->motion.freq, g->motion.axis, g->fb.dt,
-                             dt_fixed, s),
-               "motion");
-            ibm_status st = rebuild_markers(g, 1, s);
-            if (st != IBM_OK) return st;
+            if (g->mb.ns <= kSmallRebuildNs) {
+                // small body: motion, bins, forced cells and tile lists in one
+                // launch, then the quadrature (warm start)
+                CU(prof_begin(g, IBM_PROF_MARKERS, 4, &rec), "profile");
+                CU(launch_small_rebuild(g->gp, g->mb, g->motion.amp, g->motion.freq,
+                                        g->motion.axis, g->fb.dt, dt_fixed, s),
+                   "motion + bins");
+                CU(launch_quadrature(g->gp, g->mb, g->qb, g->cg_tol, g->cg_maxit, 1, s),
+                   "quadrature");
+            } else {
+                CU(prof_begin(g, IBM_PROF_MARKERS, 9, &rec), "profile");
+                CU(launch_motion(g->gp, g->mb, g->motion.amp, g->motion.freq, g->motion.axis,
+                                 g->fb.dt, dt_fixed, s),
+                   "motion");
+                ibm_status st = rebuild_markers(g, 1, s);
+                if (st != IBM_OK) return st;
+            }
             CU(prof_end(g, rec), "profile");
         }
         if (g->desc.forcing_per_stage && g->mb.ns > 0) {

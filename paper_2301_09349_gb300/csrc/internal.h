@@ -145,6 +145,8 @@ struct MarkerBuffers {
     int *cell;               // ns*3 owner cells floor((X - lo)/h) (bins kernel)
     double *frac_d;          // ns*3 offsets (X - lo)/h - cell, in [0, 1)
     float *frac_f;           // the same offsets in single precision
+    double *wphi;            // ns*9: phi((i - 1) + 1/2 - frac_d) for i = 0..2 per axis, the
+                             // marker's 1D weights at its owner cell and the two beside it
     double *rhoL, *G, *H;    // last forcing: rho_L, dt*F (ns*dim), dt*Q
     double *cp;              // ns surface pressure coefficients (ibm_surface_pressure)
     unsigned *keys[2];       // radix-sort ping-pong
@@ -174,8 +176,15 @@ struct MarkerBuffers {
 
 cudaError_t launch_motion(const GridParams &g, const MarkerBuffers &m, double amp, double freq,
                           int axis, const double *dt, double dt_fixed, cudaStream_t s);
-cudaError_t launch_band_mask(const GridParams &g, const MarkerBuffers &m, int grid_ctas,
-                             cudaStream_t s);
+// the per-step marker pipeline of a moving body with at most kSmallRebuildNs
+// markers in one launch (motion, bins, forced cells, tile lists); the
+// quadrature follows separately
+constexpr int kSmallRebuildNs = 512;
+cudaError_t launch_small_rebuild(const GridParams &g, MarkerBuffers &m, double amp, double freq,
+                                 int axis, const double *dt, double dt_fixed, cudaStream_t s);
+// forced-cell bits and band-tile flags scattered from the markers' supports,
+// then the ordered occupied and band tile lists (after launch_bin)
+cudaError_t launch_band_mask(const GridParams &g, const MarkerBuffers &m, cudaStream_t s);
 cudaError_t launch_bin(const GridParams &g, MarkerBuffers &m, cudaStream_t s);
 cudaError_t launch_interp_force(const GridParams &g, int fp_bytes, const void *U,
                                 const MarkerBuffers &m, int grid_ctas, cudaStream_t s);

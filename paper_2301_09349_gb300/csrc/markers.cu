@@ -63,6 +63,34 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int *s_warp, int &tot
 // bins
 // ---------------------------------------------------------------------------
 
+// Owner cell floor(xi) and offset xi - cell of marker k, xi = (X - lo)/h with
+// IEEE subtraction and division (they feed every weight evaluation); its
+// sort key.  A marker closer than two cells to the grid's edge sets bad.
+__device__ __forceinline__ unsigned owner_cell(const GridParams &g, const double *__restrict__ X,
+                                               int k, int *__restrict__ cell_out,
+                                               double *__restrict__ frac_d,
+                                               float *__restrict__ frac_f, int &bad) {
+    int c[3] = {0, 0, 0};
+    for (int d = 0; d < 3; ++d) {
+        double fr = 0.0;
+        if (d < g.dim) {
+            const double xi = __ddiv_rn(__dsub_rn(X[(long long)k * g.dim + d], g.lo[d]), g.h);
+            int cd = (int)floor(xi);
+            fr = xi - (double)cd;
+            if (!(cd >= 2 && cd <= g.n[d] - 3)) {
+                bad = 1;
+                cd = cd < 0 ? 0 : (cd >= g.n[d] ? g.n[d] - 1 : cd);
+                fr = 0.5;
+            }
+            c[d] = cd;
+        }
+        cell_out[(long long)k * 3 + d] = c[d];
+        frac_d[(long long)k * 3 + d] = fr;
+        frac_f[(long long)k * 3 + d] = (float)fr;
+    }
+    return cell_key(g, c[0], c[1], c[2]);
+}
+
 __global__ void __launch_bounds__(SORT_T)
 bin_sort_kernel(const GridParams g, int ns, const double *__restrict__ X, unsigned *keys0,
                 int *vals0, unsigned *keys1, int *vals1, int passes, int *err,
@@ -72,27 +100,7 @@ bin_sort_kernel(const GridParams g, int ns, const double *__restrict__ X, unsign
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     int bad = 0;
     for (int k = tid; k < ns; k += SORT_T) {
-        int c[3] = {0, 0, 0};
-        for (int d = 0; d < 3; ++d) {
-            double fr = 0.0;
-            if (d < g.dim) {
-                // xi = (X - lo)/h with IEEE subtraction and division; owner cell
-                // floor(xi) and the offset xi - cell feed every weight evaluation
-                const double xi = __ddiv_rn(__dsub_rn(X[(long long)k * g.dim + d], g.lo[d]), g.h);
-                int cd = (int)floor(xi);
-                fr = xi - (double)cd;
-                if (!(cd >= 2 && cd <= g.n[d] - 3)) {
-                    bad = 1;
-                    cd = cd < 0 ? 0 : (cd >= g.n[d] ? g.n[d] - 1 : cd);
-                    fr = 0.5;
-                }
-                c[d] = cd;
-            }
-            cell_out[(long long)k * 3 + d] = c[d];
-            frac_d[(long long)k * 3 + d] = fr;
-            frac_f[(long long)k * 3 + d] = (float)fr;
-        }
-        keys0[k] = cell_key(g, c[0], c[1], c[2]);
+        keys0[k] = owner_cell(g, X, k, cell_out, frac_d, frac_f, bad);
         vals0[k] = k;
     }
     if (bad) record_error(err, ERR_MARKER_RANGE);
@@ -171,32 +179,21 @@ __global__ void tile_offsets_kernel(const GridParams g, int ns, const unsigned *
     tile_off[t] = lo;
 }
 
+// occ[t] = tile t holds an owner cell; band[t] cleared for the scatter of
+// the forced cells
 __global__ void tile_flags_kernel(const GridParams g, const int *__restrict__ tile_off,
                                   int *__restrict__ occ, int *__restrict__ band) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= g.n_tiles) return;
-    const int tx = t % g.ntile[0], ty = (t / g.ntile[0]) % g.ntile[1],
-              tz = t / (g.ntile[0] * g.ntile[1]);
     occ[t] = tile_off[t + 1] > tile_off[t];
-    int b = 0;
-    const int zr = g.dim == 3 ? 1 : 0;
-    for (int oz = -zr; oz <= zr; ++oz)
-        for (int oy = -1; oy <= 1; ++oy)
-            for (int ox = -1; ox <= 1; ++ox) {
-                const int x = tx + ox, y = ty + oy, z = tz + oz;
-                if (x < 0 || y < 0 || z < 0 || x >= g.ntile[0] || y >= g.ntile[1] || z >= g.ntile[2])
-                    continue;
-                const int u = x + g.ntile[0] * (y + g.ntile[1] * z);
-                b |= tile_off[u + 1] > tile_off[u];
-            }
-    band[t] = b;
+    band[t] = 0;
 }
 
-// ordered compaction of the two flag arrays (single CTA)
-__global__ void __launch_bounds__(SORT_T)
-tile_lists_kernel(int n_tiles, const int *__restrict__ occ, const int *__restrict__ band,
-                  int *__restrict__ occ_list, int *__restrict__ band_list, int *__restrict__ counts) {
-    __shared__ int s_warp[33];
+// ordered compaction of the two flag arrays by one CTA of SORT_T threads
+__device__ __forceinline__ void tile_lists(int n_tiles, const int *__restrict__ occ,
+                                           const int *__restrict__ band, int *__restrict__ occ_list,
+                                           int *__restrict__ band_list, int *__restrict__ counts,
+                                           int *s_warp) {
     const int chunk = (n_tiles + SORT_T - 1) / SORT_T;
     const int t0 = threadIdx.x * chunk, t1 = min(n_tiles, t0 + chunk);
     int co = 0, cb = 0;
@@ -217,9 +214,28 @@ tile_lists_kernel(int n_tiles, const int *__restrict__ occ, const int *__restric
     }
 }
 
+__global__ void __launch_bounds__(SORT_T)
+tile_lists_kernel(int n_tiles, const int *__restrict__ occ, const int *__restrict__ band,
+                  int *__restrict__ occ_list, int *__restrict__ band_list, int *__restrict__ counts) {
+    __shared__ int s_warp[33];
+    tile_lists(n_tiles, occ, band, occ_list, band_list, counts, s_warp);
+}
+
 // ---------------------------------------------------------------------------
 // motion (Sec. 5): positions and body velocity at t^{n+1} = t^n + dt
 // ---------------------------------------------------------------------------
+
+// body offset and velocity along the motion axis at t^{n+1} (rigid
+// transverse or streamwise oscillation X = X0 + A sin(2 pi f t))
+__device__ __forceinline__ void motion_offset(double amp, double freq,
+                                              const double *__restrict__ t,
+                                              const double *__restrict__ dt, double dt_fixed,
+                                              double &sv, double &vv) {
+    const double pi = 3.14159265358979323846;
+    const double tn = *t + (dt_fixed > 0.0 ? dt_fixed : *dt);
+    sv = amp * sin(2.0 * pi * freq * tn);
+    vv = amp * 2.0 * pi * freq * cos(2.0 * pi * freq * tn);
+}
 
 __global__ void motion_kernel(const GridParams g, int ns, const double *__restrict__ X0,
                               const double *__restrict__ Ub0, double *__restrict__ X,
@@ -228,15 +244,97 @@ __global__ void motion_kernel(const GridParams g, int ns, const double *__restri
                               double dt_fixed) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= ns) return;
-    const double pi = 3.14159265358979323846;
-    const double tn = *t + (dt_fixed > 0.0 ? dt_fixed : *dt);
-    const double sv = amp * sin(2.0 * pi * freq * tn);
-    const double vv = amp * 2.0 * pi * freq * cos(2.0 * pi * freq * tn);
+    double sv, vv;
+    motion_offset(amp, freq, t, dt, dt_fixed, sv, vv);
     for (int d = 0; d < g.dim; ++d) {
         const long long q = (long long)k * g.dim + d;
         X[q] = X0[q] + (d == axis ? sv : 0.0);
         Ub[q] = Ub0[q] + (d == axis ? vv : 0.0);
     }
+}
+
+// The per-step marker pipeline of a small moving body (ns <= SMALL_NS) in one
+// CTA: the motion, owner cells and keys, a stable sort by key (rank of each
+// key: the keys below it plus the equal keys before it, the order a stable
+// radix sort gives), tile offsets and occupancy, the forced-cell scatter and
+// the tile lists - the work of motion_kernel, bin_sort_kernel,
+// tile_offsets_kernel, tile_flags_kernel, band_scatter_kernel and
+// tile_lists_kernel, with barriers in place of six launches.  band_bits must
+// be clear on entry; the sorted order goes to keys[0] / perm[0].
+constexpr int SMALL_NS = kSmallRebuildNs;
+static_assert(SMALL_NS <= SORT_T, "one marker per thread");
+__global__ void __launch_bounds__(SORT_T)
+small_rebuild_kernel(const GridParams g, const MarkerBuffers m, double amp, double freq, int axis,
+                     const double *__restrict__ dt, double dt_fixed) {
+    __shared__ unsigned s_key[SMALL_NS];
+    __shared__ unsigned s_sorted[SMALL_NS];
+    __shared__ int s_warp[33];
+    __shared__ double s_mv[2];
+    const int tid = threadIdx.x, ns = m.ns;
+    if (tid == 0) motion_offset(amp, freq, m.t, dt, dt_fixed, s_mv[0], s_mv[1]);
+    __syncthreads();
+    int bad = 0;
+    if (tid < ns) {
+        const int k = tid;
+        for (int d = 0; d < g.dim; ++d) {
+            const long long q = (long long)k * g.dim + d;
+            m.X[q] = m.X0[q] + (d == axis ? s_mv[0] : 0.0);
+            m.Ub[q] = m.Ub0[q] + (d == axis ? s_mv[1] : 0.0);
+        }
+        s_key[k] = owner_cell(g, m.X, k, m.cell, m.frac_d, m.frac_f, bad);
+    }
+    if (bad) record_error(m.err, ERR_MARKER_RANGE);
+    __syncthreads();
+    if (tid < ns) {
+        const unsigned key = s_key[tid];
+        int r = 0;
+        for (int j = 0; j < ns; ++j) {
+            const unsigned kj = s_key[j];
+            r += kj < key || (kj == key && j < tid);
+        }
+        s_sorted[r] = key;
+        m.keys[0][r] = key;
+        m.perm[0][r] = tid;
+    }
+    __syncthreads();
+    // tile offsets (lower bounds in the sorted keys), occupancy; band flags
+    // cleared for the scatter
+    const unsigned cpt = (unsigned)g.cells_per_tile;
+    for (int t = tid; t <= g.n_tiles; t += SORT_T) {
+        const unsigned target = (unsigned)t * cpt;
+        int lo = 0, hi = ns;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (s_sorted[mid] < target) lo = mid + 1;
+            else hi = mid;
+        }
+        m.tile_off[t] = lo;
+        if (t < g.n_tiles) {
+            // occupied: some key in [t cpt, (t+1) cpt)
+            m.occ_flag[t] = lo < ns && s_sorted[lo] < target + cpt;
+            m.band_flag[t] = 0;
+        }
+    }
+    __syncthreads();
+    // forced cells: the 3^d support cells of every marker
+    const int nsc = g.dim == 3 ? 27 : 9;
+    for (int i = tid; i < ns * nsc; i += SORT_T) {
+        const int k = i / nsc, sc = i - k * nsc;
+        const int o[3] = {sc % 3 - 1, (sc / 3) % 3 - 1, g.dim == 3 ? sc / 9 - 1 : 0};
+        int c[3] = {0, 0, 0};
+        bool in = true;
+        for (int d = 0; d < g.dim; ++d) {
+            c[d] = m.cell[(long long)k * 3 + d] + o[d];
+            in = in && c[d] >= 0 && c[d] < g.n[d];
+        }
+        if (!in) continue;
+        const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+        if (!in_bounds(j, g.N, m.err)) continue;
+        atomicOr(m.band_bits + (j >> 5), 1u << (j & 31));
+        m.band_flag[cell_key(g, c[0], c[1], c[2]) / cpt] = 1;
+    }
+    __syncthreads();
+    tile_lists(g.n_tiles, m.occ_flag, m.band_flag, m.occ_list, m.band_list, m.counts, s_warp);
 }
 
 // ---------------------------------------------------------------------------
@@ -462,25 +560,34 @@ size_t spread_smem_bytes(const GridParams &g) {
 // sum_d f_d (m0_d + m1_d) (no cancellation).  The heat source is capped at
 // kHeatSourceCap of the cell's internal energy (positivity reading).  In the
 // spreading precision R (the field precision).
+template <int DIM, typename R>
+__device__ __forceinline__ void force_cell(const GridParams &g, R (&u)[DIM + 2], const R *f, R qh) {
+    const R rho = u[0];
+    R dke = R(0), ke0 = R(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const R m0 = u[1 + d];
+        const R m1 = m0 + f[d];
+        dke += f[d] * (m0 + m1);
+        ke0 += m0 * m0;
+        u[1 + d] = m1;
+    }
+    const R E = u[DIM + 1];
+    const R qmin = -(R)kHeatSourceCap * (E - R(0.5) * ke0 / rho);
+    if (qh < qmin) qh = qmin;
+    u[DIM + 1] = g.energy_reading == 1 ? E + qh : E + (qh + R(0.5) * dke / rho);
+}
+
 template <int DIM, typename T, typename R>
 __device__ __forceinline__ void apply_forcing(const GridParams &g, T *__restrict__ U, long long j,
                                               const R *f, R qh) {
     const long long N = g.N;
-    const R rho = (R)U[j];
-    R dke = R(0), ke0 = R(0);
+    R u[DIM + 2];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        const R m0 = (R)U[(1 + d) * N + j];
-        const R m1 = m0 + f[d];
-        dke += f[d] * (m0 + m1);
-        ke0 += m0 * m0;
-        U[(1 + d) * N + j] = (T)m1;
-    }
-    const R E = (R)U[(DIM + 1) * N + j];
-    const R qmin = -(R)kHeatSourceCap * (E - R(0.5) * ke0 / rho);
-    if (qh < qmin) qh = qmin;
-    const R En = g.energy_reading == 1 ? E + qh : E + (qh + R(0.5) * dke / rho);
-    U[(DIM + 1) * N + j] = (T)En;
+    for (int c = 0; c < DIM + 2; ++c) u[c] = (R)U[c * N + j];
+    force_cell<DIM, R>(g, u, f, qh);
+#pragma unroll
+    for (int c = 1; c < DIM + 2; ++c) U[c * N + j] = (T)u[c];
 }
 
 // Shared memory of the spreading kernels: staged candidate markers (dynamic)
@@ -652,7 +759,7 @@ __device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__
                                             const MarkerBuffers &m,
                                             const unsigned *__restrict__ keys,
                                             const int *__restrict__ perm, int t,
-                                            const SpreadSmem<T> &sm, double &smax, bool &ok) {
+                                            const SpreadSmem<T> &sm, T &smax, bool &ok) {
     using R = T;
     const R *s_g = sm.g, *s_h = sm.h;
     const int tid = threadIdx.x;
@@ -690,7 +797,7 @@ __device__ __forceinline__ void spread_tile(const GridParams &g, T *__restrict__
         T u[DIM + 2];
 #pragma unroll
         for (int cc = 0; cc < DIM + 2; ++cc) u[cc] = U[cc * g.N + j];
-        smax = fmax(smax, (double)step_rate<DIM, T>(g, u, ok));
+        smax = fmax(smax, step_rate<DIM, T>(g, u, ok));
     }
     __syncthreads();
 }
@@ -706,18 +813,18 @@ spread_apply_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m
     const SpreadSmem<T> sm = spread_smem<T>(smem_sp, g, s_cnt, s_start, s_warp);
     const int tid = threadIdx.x;
     const int n_band = m.counts[1];
-    double smax = 0.0;   // step-size rate of the forced cells, for the next dt
+    T smax = T(0);   // step-size rate of the forced cells, for the next dt
     bool ok = true;
     for (int it = blockIdx.x; it < n_band; it += gridDim.x)
         spread_tile<DIM, T>(g, U, m, keys, perm, m.band_list[it], sm, smax, ok);
 #pragma unroll
     for (int o2 = 16; o2 > 0; o2 >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o2));
     const int bad = __syncthreads_or(!ok);
-    if ((tid & 31) == 0) s_max[tid >> 5] = smax;
+    if ((tid & 31) == 0) s_max[tid >> 5] = (double)smax;
     __syncthreads();
     if (tid == 0) {
         double mx = s_max[0];
-        for (int w = 1; w < SP_T<DIM> / 32; ++w) mx = fmax(mx, s_max[w]);
+        for (int w = 1; w < SP_T<DIM> / 32; ++w) mx = dmax_nonneg(mx, s_max[w]);
         m.bandmax[blockIdx.x] = mx;
         if (bad) record_error(m.err, ERR_NONFINITE);
     }
@@ -816,6 +923,7 @@ __device__ __forceinline__ void load4(const double *p, double v[4]) {
 // terms and the order of spread_tile, so the results are bitwise the same),
 // then applies the forcing.  One step-size maximum per CTA in bandmax.
 constexpr int SPS_T = 256;
+constexpr int SPS_B = 8;   // operator entries whose loads issue together
 template <int DIM, typename T>
 __global__ void __launch_bounds__(SPS_T)
 spread_static_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m) {
@@ -824,40 +932,62 @@ spread_static_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers 
     const int nc = min(m.counts[2], m.sp_cap);
     const R *gs = reinterpret_cast<const R *>(m.gs);
     const R *ew = reinterpret_cast<const R *>(m.sp_w);
-    double smax = 0.0;
+    T smax = T(0);
     bool ok = true;
     for (int i = blockIdx.x * SPS_T + threadIdx.x; i < nc; i += gridDim.x * SPS_T) {
         const SpreadCell rc = m.sp_cell[i];
-        if (rc.n <= 0) continue;
-        R f[DIM], qh = R(0);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) f[d] = R(0);
-        for (int p = rc.start; p < rc.start + rc.n; ++p) {
-            if (!in_bounds(p, m.sp_cap, m.err)) break;
-            const int k = __ldg(m.sp_k + p);
-            const R w = __ldg(ew + p);
-            if (!in_bounds(k, m.ns, m.err)) continue;
-            R v[4];
-            load4(gs + 4 * (long long)k, v);
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) f[d] += v[d] * w;
-            qh += v[3] * w;
-        }
-        if (!in_bounds(rc.j, g.N, m.err)) continue;
-        apply_forcing<DIM, T, R>(g, U, rc.j, f, qh);
+        if (rc.n <= 0 || !in_bounds(rc.j, g.N, m.err)) continue;
+        // the cell's state is loaded ahead of its entries
         T u[DIM + 2];
 #pragma unroll
         for (int cc = 0; cc < DIM + 2; ++cc) u[cc] = U[cc * g.N + rc.j];
-        smax = fmax(smax, (double)step_rate<DIM, T>(g, u, ok));
+        R f[DIM], qh = R(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) f[d] = R(0);
+        // entries in batches of SPS_B: their loads issue together, then
+        // the terms in the stored order
+        const int pe = rc.start + rc.n;
+        for (int p0 = rc.start; p0 < pe; p0 += SPS_B) {
+            int k[SPS_B];
+            R w[SPS_B], v[SPS_B][4];
+#pragma unroll
+            for (int b = 0; b < SPS_B; ++b) {
+                const int p = p0 + b;
+                const bool in = p < pe && in_bounds(p, m.sp_cap, m.err);
+                k[b] = in ? __ldg(m.sp_k + p) : -1;
+                w[b] = in ? __ldg(ew + p) : R(0);
+            }
+#pragma unroll
+            for (int b = 0; b < SPS_B; ++b) {
+                if (k[b] >= 0 && in_bounds(k[b], m.ns, m.err)) {
+                    load4(gs + 4 * (long long)k[b], v[b]);
+                } else {
+                    k[b] = -1;
+                    v[b][0] = v[b][1] = v[b][2] = v[b][3] = R(0);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < SPS_B; ++b) {
+                if (k[b] < 0) continue;
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) f[d] += v[b][d] * w[b];
+                qh += v[b][3] * w[b];
+            }
+        }
+        // the forced update (as apply_forcing), the rate from the new state
+        force_cell<DIM, T>(g, u, f, qh);
+#pragma unroll
+        for (int cc = 1; cc < DIM + 2; ++cc) U[cc * g.N + rc.j] = u[cc];
+        smax = fmax(smax, step_rate<DIM, T>(g, u, ok));
     }
 #pragma unroll
     for (int o2 = 16; o2 > 0; o2 >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o2));
     const int bad = __syncthreads_or(!ok);
-    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = smax;
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = (double)smax;
     __syncthreads();
     if (threadIdx.x == 0) {
         double mx = s_max[0];
-        for (int w = 1; w < SPS_T / 32; ++w) mx = fmax(mx, s_max[w]);
+        for (int w = 1; w < SPS_T / 32; ++w) mx = dmax_nonneg(mx, s_max[w]);
         m.bandmax[blockIdx.x] = mx;
         if (bad) record_error(m.err, ERR_NONFINITE);
     }
@@ -880,108 +1010,103 @@ batch_spread_kernel(const BatchCase *__restrict__ cases, const int2 *__restrict_
         const GridParams g = bc.g;
         const MarkerBuffers m = bc.m;
         const SpreadSmem<T> sm = spread_smem<T>(smem_sp, g, s_cnt, s_start, s_warp);
-        double smax = 0.0;
+        T smax = T(0);
         bool ok = true;
         spread_tile<DIM, T>(g, (T *)bc.Us, m, m.keys[m.sorted], m.perm[m.sorted],
                             m.band_list[w.y], sm, smax, ok);
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o2));
         const int bad = __syncthreads_or(!ok);
-        if ((tid & 31) == 0) s_max[tid >> 5] = smax;
+        if ((tid & 31) == 0) s_max[tid >> 5] = (double)smax;
         __syncthreads();
         if (tid == 0) {
             double mx = s_max[0];
-            for (int w2 = 1; w2 < SP_T<DIM> / 32; ++w2) mx = fmax(mx, s_max[w2]);
+            for (int w2 = 1; w2 < SP_T<DIM> / 32; ++w2) mx = dmax_nonneg(mx, s_max[w2]);
             band_max[it] = mx;
             if (bad) record_error(bc.err, ERR_NONFINITE);
         }
     }
 }
 
-// One bit per cell lying in the support of some marker (the cells the
-// forcing changes).  The bits must be clear on entry.
+// The forced cells, scattered from the markers: the support of marker k is
+// the 3^d cells around its owner cell (per axis the owner and its two
+// neighbours; the 3-point delta vanishes beyond), so one thread per (marker,
+// support cell) sets that cell's bit in band_bits and the flag of its tile in
+// band_flag - the set the spreading's cell-centric gather visits, with bit
+// OR and flag stores that do not depend on order.  Both must be clear on
+// entry.
 template <int DIM>
 __global__ void __launch_bounds__(256)
-band_mask_kernel(const GridParams g, const MarkerBuffers m, const unsigned *__restrict__ keys,
-                 const int *__restrict__ perm) {
-    const int n_band = m.counts[1];
-    const int cpt = g.cells_per_tile;
-    for (int it = blockIdx.x; it < n_band; it += gridDim.x) {
-        const int t = m.band_list[it];
-        const int tx = t % g.ntile[0], ty = (t / g.ntile[0]) % g.ntile[1],
-                  tz = t / (g.ntile[0] * g.ntile[1]);
-        for (int q = threadIdx.x; q < cpt; q += blockDim.x) {
-            const int c[3] = {tx * g.tile[0] + q % g.tile[0],
-                              ty * g.tile[1] + (q / g.tile[0]) % g.tile[1],
-                              DIM == 3 ? tz * g.tile[2] + q / (g.tile[0] * g.tile[1]) : 0};
-            if (c[0] >= g.n[0] || c[1] >= g.n[1] || (DIM == 3 && c[2] >= g.n[2])) continue;
-            const bool band = gather_markers<DIM, float>(g, m, keys, perm, c, [&](int, float) {});
-            if (band) {
-                const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
-                atomicOr(m.band_bits + (j >> 5), 1u << (j & 31));
-            }
-        }
+band_scatter_kernel(const GridParams g, const MarkerBuffers m) {
+    constexpr int NSC = DIM == 3 ? 27 : 9;
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const int k = (int)(t / NSC), sc = (int)(t - (long long)k * NSC);
+    if (k >= m.ns) return;
+    const int o[3] = {sc % 3 - 1, (sc / 3) % 3 - 1, DIM == 3 ? sc / 9 - 1 : 0};
+    int c[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        c[d] = m.cell[(long long)k * 3 + d] + o[d];
+        if (c[d] < 0 || c[d] >= g.n[d]) return;
     }
-}
-
-// Keep in the band list only the tiles that hold a band cell: a tile next to
-// an occupied one is reached by a marker's support only where that marker's
-// owner cell lies on the shared tile face, and the spreading kernels would
-// otherwise pay a full pass over each of the others for nothing.  One warp
-// per band tile clears band_flag where no bit is set; the lists are then
-// rebuilt.
-template <int DIM>
-__global__ void __launch_bounds__(256)
-band_refine_kernel(const GridParams g, const MarkerBuffers m) {
-    const int n_band = m.counts[1];
-    const int lane = threadIdx.x & 31;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
-    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_band; it += nw) {
-        const int t = m.band_list[it];
-        const int tx = t % g.ntile[0], ty = (t / g.ntile[0]) % g.ntile[1],
-                  tz = t / (g.ntile[0] * g.ntile[1]);
-        bool any = false;
-        for (int q = lane; q < g.cells_per_tile && !any; q += 32) {
-            const int c[3] = {tx * g.tile[0] + q % g.tile[0],
-                              ty * g.tile[1] + (q / g.tile[0]) % g.tile[1],
-                              DIM == 3 ? tz * g.tile[2] + q / (g.tile[0] * g.tile[1]) : 0};
-            if (c[0] >= g.n[0] || c[1] >= g.n[1] || (DIM == 3 && c[2] >= g.n[2])) continue;
-            const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
-            any = (m.band_bits[j >> 5] >> (j & 31)) & 1u;
-        }
-        any = __any_sync(0xffffffffu, any);
-        if (lane == 0 && !any) m.band_flag[t] = 0;
-    }
+    const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+    if (!in_bounds(j, g.N, m.err)) return;
+    atomicOr(m.band_bits + (j >> 5), 1u << (j & 31));
+    m.band_flag[cell_key(g, c[0], c[1], c[2]) / (unsigned)g.cells_per_tile] = 1;
 }
 
 // ---------------------------------------------------------------------------
 // forces/heat sums (fixed-order reduction) and the time update
 // ---------------------------------------------------------------------------
 
-constexpr int FIN_T = 256;   // 1024 measured slower (22 against 17 us at 256^3)
+constexpr int FIN_T = 256;   // threads of the batch finish and of the stage-1 sums
 
-// Partial force/heat sums of markers [k0, k1) and the maxima of
-// blockmax[b0, b1) and bandmax[c0, c1) by one CTA: a[0..dim) = sum eps~ G,
-// a[3] = sum eps~ H, a[4] = max rate, valid in warp 0 on return.  The
-// markers are summed in a fixed order (thread stride, then a warp tree, then
-// a tree over the warps), so the result does not depend on timing.
-__device__ __forceinline__ void finish_partial(const GridParams &g, const MarkerBuffers &m,
-                                               int k0, int k1,
-                                               const double *__restrict__ blockmax, int b0, int b1,
-                                               const double *__restrict__ bandmax, int c0, int c1,
-                                               double (*s)[FIN_T / 32], double a[5]) {
+// A warp's five partials (sums 0..3, maximum 4) combined as a fixed
+// shuffle tree; the result in every lane.
+__device__ __forceinline__ void finish_combine(double a[5]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
+        a[4] = dmax_nonneg(a[4], __shfl_xor_sync(0xffffffffu, a[4], o));
+    }
+}
+
+// The finish of a grid splits its markers (and its maxima) into C chunks,
+// chunk c covering [n c / C, n (c+1) / C), C = ceil(n_s / FIN_CHUNK) <= 32.
+// One warp forms a chunk's partial: lane l sums markers k0 + l, k0 + l + 32,
+// ... in order, then a shuffle tree; the C partials are combined by a second
+// fixed tree.  FP64 is the limiter here (this GPU's FP64 pipe retires about
+// two operations per SM cycle), so the chunks run on separate SMs with one
+// warp each, and C depends on the marker count alone: the split kernel of
+// one grid and the one-CTA finish of a batch case add the same partials in
+// the same trees.
+constexpr int FIN_CHUNK = 128;
+__host__ __device__ __forceinline__ int finish_chunks(int ns) {
+    const int c = (ns + FIN_CHUNK - 1) / FIN_CHUNK;
+    return c < 1 ? 1 : (c > kFinishCtas ? kFinishCtas : c);
+}
+__host__ __device__ __forceinline__ int finish_cut(int n, int c, int C) {
+    return (int)((long long)n * c / C);
+}
+
+// One warp: a[0..dim) = sum eps~ G, a[3] = sum eps~ H over markers [k0, k1)
+// and a[4] = the largest of blockmax[b0, b1) and bandmax[c0, c1), in every
+// lane on return.
+__device__ __forceinline__ void finish_chunk(const GridParams &g, const MarkerBuffers &m, int k0,
+                                             int k1, const double *__restrict__ blockmax, int b0,
+                                             int b1, const double *__restrict__ bandmax, int c0,
+                                             int c1, int lane, double a[5]) {
     const int dim = g.dim;
 #pragma unroll
     for (int i = 0; i < 5; ++i) a[i] = 0.0;
-    // markers k0 + tid, k0 + tid + FIN_T, ...; the loads of FIN_B of them
-    // are issued together, so the latency is paid once per batch rather
-    // than once per marker
+    // the loads of FIN_B markers issue together, then their terms in order
     constexpr int FIN_B = 4;
-    for (int kb = k0 + (int)threadIdx.x; kb < k1; kb += FIN_B * FIN_T) {
+    for (int kb = k0 + lane; kb < k1; kb += FIN_B * 32) {
         double e[FIN_B], gq[FIN_B][4];
 #pragma unroll
         for (int i = 0; i < FIN_B; ++i) {
-            const int k = kb + i * FIN_T;
+            const int k = kb + i * 32;
             e[i] = 0.0;
             gq[i][0] = gq[i][1] = gq[i][2] = gq[i][3] = 0.0;
             if (k < k1) {
@@ -994,37 +1119,29 @@ __device__ __forceinline__ void finish_partial(const GridParams &g, const Marker
         }
 #pragma unroll
         for (int i = 0; i < FIN_B; ++i) {
-            if (kb + i * FIN_T >= k1) break;
+            if (kb + i * 32 >= k1) break;
 #pragma unroll
             for (int d = 0; d < 3; ++d)
                 if (d < dim) a[d] += e[i] * gq[i][d];
             a[3] += e[i] * gq[i][3];
         }
     }
-    // maxima: the order does not matter
-    for (int b = b0 + (int)threadIdx.x; b < b1; b += FIN_T) a[4] = fmax(a[4], __ldg(blockmax + b));
-    for (int b = c0 + (int)threadIdx.x; b < c1; b += FIN_T) a[4] = fmax(a[4], __ldg(bandmax + b));
+    // maxima (the order does not matter), eight loads issued together
+    for (int b = b0 + lane; b < b1; b += 8 * 32) {
+        double v[8];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < 8; ++i) v[i] = b + i * 32 < b1 ? __ldg(blockmax + b + i * 32) : 0.0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
+        for (int i = 0; i < 8; ++i) a[4] = dmax_nonneg(a[4], v[i]);
     }
+    for (int b = c0 + lane; b < c1; b += 8 * 32) {
+        double v[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a[4] = fmax(a[4], __shfl_xor_sync(0xffffffffu, a[4], o));
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (lane == 0)
-        for (int i = 0; i < 5; ++i) s[i][w] = a[i];
-    __syncthreads();
-    if (w != 0) return;
-    // warp 0 combines the warp partials as a fixed tree
+        for (int i = 0; i < 8; ++i) v[i] = b + i * 32 < c1 ? __ldg(bandmax + b + i * 32) : 0.0;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) a[i] = lane < FIN_T / 32 ? s[i][lane] : 0.0;
-#pragma unroll
-    for (int o = FIN_T / 64; o > 0; o >>= 1) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
-        a[4] = fmax(a[4], __shfl_xor_sync(0xffffffffu, a[4], o));
+        for (int i = 0; i < 8; ++i) a[4] = dmax_nonneg(a[4], v[i]);
     }
+    finish_combine(a);
 }
 
 // The sums of a step, its time update and the next step size from the
@@ -1046,50 +1163,26 @@ __device__ __forceinline__ void finish_update(const GridParams &g, const MarkerB
     *dt_ptr = good ? g.cfl / mx : 0.0;
 }
 
-// The finish of a grid is split into C chunks of its markers (and of its
-// maxima): chunk c covers [n c / C, n (c+1) / C).  C depends on the marker
-// count alone, so the split kernel of one grid and the one-CTA finish of a
-// batch case add the same partials in the same tree.
-__host__ __device__ __forceinline__ int finish_chunks(int ns) {
-    const int c = (ns + FIN_T - 1) / FIN_T;
-    return c < 1 ? 1 : (c > kFinishCtas ? kFinishCtas : c);
-}
-__host__ __device__ __forceinline__ int finish_cut(int n, int c, int C) {
-    return (int)((long long)n * c / C);
-}
-
-// Warp 0: the C chunk partials (lane c holds chunk c's, zeros above C)
-// combined as a fixed shuffle tree; the result in every lane.
-__device__ __forceinline__ void finish_combine(double a[5]) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) a[i] += __shfl_xor_sync(0xffffffffu, a[i], o);
-        a[4] = fmax(a[4], __shfl_xor_sync(0xffffffffu, a[4], o));
-    }
-}
-
-// One CTA: the force/heat sums of one grid, its time update and its next
-// step size from the stage-2 maxima (blockmax[0..nb)) and the forced-cell
-// maxima (bandmax[0..nbs)); the chunks one after another.
+// One CTA of FIN_T threads: the force/heat sums of one grid, its time update
+// and its next step size from the stage-2 maxima (blockmax[0..nb)) and the
+// forced-cell maxima (bandmax[0..nbs)); warp w forms chunks w, w + 8, ...
 __device__ __forceinline__ void finish_grid(const GridParams &g, int ns, const MarkerBuffers &m,
                                             const double *__restrict__ blockmax, int nb,
                                             const double *__restrict__ bandmax, int nbs,
                                             double *__restrict__ dt_ptr, int *__restrict__ err,
-                                            double dt_fixed, double (*s)[FIN_T / 32],
-                                            double (*part)[5]) {
+                                            double dt_fixed, double (*part)[5]) {
     const int C = finish_chunks(ns);
-    for (int c = 0; c < C; ++c) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int c = w; c < C; c += FIN_T / 32) {
         double a[5];
-        finish_partial(g, m, finish_cut(ns, c, C), finish_cut(ns, c + 1, C), blockmax,
-                       finish_cut(nb, c, C), finish_cut(nb, c + 1, C), bandmax,
-                       finish_cut(nbs, c, C), finish_cut(nbs, c + 1, C), s, a);
-        if (threadIdx.x == 0)
+        finish_chunk(g, m, finish_cut(ns, c, C), finish_cut(ns, c + 1, C), blockmax,
+                     finish_cut(nb, c, C), finish_cut(nb, c + 1, C), bandmax,
+                     finish_cut(nbs, c, C), finish_cut(nbs, c + 1, C), lane, a);
+        if (lane == 0)
             for (int i = 0; i < 5; ++i) part[c][i] = a[i];
-        __syncthreads();   // s is taken again by the next chunk
     }
-    if (threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
+    __syncthreads();
+    if (w != 0) return;
     double a[5];
 #pragma unroll
     for (int i = 0; i < 5; ++i) a[i] = lane < C ? part[lane][i] : 0.0;
@@ -1129,30 +1222,27 @@ partial_sums_kernel(const GridParams g, const MarkerBuffers m) {
         for (int i = 0; i < 4; ++i) m.sums[8 + i] = a[i];
 }
 
-// Split form: CTA c of C = finish_chunks(ns) sums chunk c of the markers
-// and of the maxima into part[c]; the last CTA to finish (ticket) combines
-// the C partials as the fixed tree of finish_combine, so the sums do not
-// depend on which CTA comes last, and resets the ticket for the next launch.
-__global__ void __launch_bounds__(FIN_T)
+// Split form: one warp per chunk (CTA c forms chunk c's partial into
+// part[c]); the last CTA to finish (ticket) combines the C partials as the
+// fixed tree of finish_combine, so the sums do not depend on which CTA comes
+// last, and resets the ticket for the next launch.
+__global__ void __launch_bounds__(32)
 finish_kernel(const GridParams g, int ns, const MarkerBuffers m, const double *__restrict__ blockmax,
               int nb, int nbs, double *__restrict__ dt_ptr, int *__restrict__ err, double dt_fixed,
               double *__restrict__ part, unsigned *__restrict__ ticket) {
-    __shared__ double s[5][FIN_T / 32];
-    __shared__ int s_last;
-    const int C = gridDim.x, c = blockIdx.x;
+    const int C = gridDim.x, c = blockIdx.x, lane = threadIdx.x;
     double a[5];
-    finish_partial(g, m, finish_cut(ns, c, C), finish_cut(ns, c + 1, C), blockmax,
-                   finish_cut(nb, c, C), finish_cut(nb, c + 1, C), m.bandmax,
-                   finish_cut(nbs, c, C), finish_cut(nbs, c + 1, C), s, a);
-    if (threadIdx.x == 0) {
+    finish_chunk(g, m, finish_cut(ns, c, C), finish_cut(ns, c + 1, C), blockmax,
+                 finish_cut(nb, c, C), finish_cut(nb, c + 1, C), m.bandmax,
+                 finish_cut(nbs, c, C), finish_cut(nbs, c + 1, C), lane, a);
+    unsigned last = 0;
+    if (lane == 0) {
         for (int i = 0; i < 5; ++i) part[c * 5 + i] = a[i];
         __threadfence();
-        s_last = atomicAdd(ticket, 1u) == (unsigned)C - 1;
+        last = atomicAdd(ticket, 1u) == (unsigned)C - 1;
     }
-    __syncthreads();
-    if (!s_last || threadIdx.x >= 32) return;
+    if (!__shfl_sync(0xffffffffu, last, 0)) return;
     __threadfence();
-    const int lane = threadIdx.x;
 #pragma unroll
     for (int i = 0; i < 5; ++i) a[i] = lane < C ? __ldcg(part + lane * 5 + i) : 0.0;
     finish_combine(a);
@@ -1166,11 +1256,10 @@ finish_kernel(const GridParams g, int ns, const MarkerBuffers m, const double *_
 __global__ void __launch_bounds__(FIN_T)
 batch_finish_kernel(const BatchCase *__restrict__ cases, const double *__restrict__ item_max,
                     const double *__restrict__ band_max, double dt_fixed) {
-    __shared__ double s[5][FIN_T / 32];
     __shared__ double part[kFinishCtas][5];
     const BatchCase &bc = cases[blockIdx.x];
     finish_grid(bc.g, bc.m.ns, bc.m, item_max + bc.item0, bc.nitems, band_max + bc.band0,
-                bc.nband, bc.dt, bc.err, dt_fixed, s, part);
+                bc.nband, bc.dt, bc.err, dt_fixed, part);
 }
 
 // The force sums, the step size they belong to and the time of every case
@@ -1297,6 +1386,16 @@ cudaError_t launch_motion(const GridParams &g, const MarkerBuffers &m, double am
     return cudaGetLastError();
 }
 
+cudaError_t launch_small_rebuild(const GridParams &g, MarkerBuffers &m, double amp, double freq,
+                                 int axis, const double *dt, double dt_fixed, cudaStream_t s) {
+    if (m.ns <= 0 || m.ns > SMALL_NS) return cudaErrorInvalidValue;
+    m.sorted = 0;
+    cudaError_t e = cudaMemsetAsync(m.band_bits, 0, sizeof(unsigned) * (size_t)(g.N / 32 + 1), s);
+    if (e != cudaSuccess) return e;
+    small_rebuild_kernel<<<1, SORT_T, 0, s>>>(g, m, amp, freq, axis, dt, dt_fixed);
+    return cudaGetLastError();
+}
+
 static int radix_passes(const GridParams &g) {
     unsigned long long maxkey = (unsigned long long)g.n_tiles * g.cells_per_tile - 1ull;
     int bits = 0;
@@ -1318,8 +1417,6 @@ cudaError_t launch_bin(const GridParams &g, MarkerBuffers &m, cudaStream_t s) {
                                                                      m.tile_off);
     tile_flags_kernel<<<(g.n_tiles + 255) / 256, 256, 0, s>>>(g, m.tile_off, m.occ_flag,
                                                               m.band_flag);
-    tile_lists_kernel<<<1, SORT_T, 0, s>>>(g.n_tiles, m.occ_flag, m.band_flag, m.occ_list,
-                                           m.band_list, m.counts);
     return cudaGetLastError();
 }
 
@@ -1408,7 +1505,7 @@ cudaError_t launch_spread_build(const GridParams &g, int fp_bytes, const MarkerB
 
 cudaError_t launch_finish(const GridParams &g, const MarkerBuffers &m, const FluidBuffers &fb,
                           int nb, int nbs, double dt_fixed, cudaStream_t s) {
-    finish_kernel<<<finish_chunks(m.ns), FIN_T, 0, s>>>(g, m.ns, m, fb.blockmax, nb, nbs, fb.dt, fb.err, dt_fixed,
+    finish_kernel<<<finish_chunks(m.ns), 32, 0, s>>>(g, m.ns, m, fb.blockmax, nb, nbs, fb.dt, fb.err, dt_fixed,
                                       m.finpart, fb.counter + 1);
     return cudaGetLastError();
 }
@@ -1474,19 +1571,17 @@ cudaError_t launch_batch_tw(const BatchTwSlot *slots, int ncases, const double *
     return cudaGetLastError();
 }
 
-cudaError_t launch_band_mask(const GridParams &g, const MarkerBuffers &m, int grid_ctas,
-                             cudaStream_t s) {
+cudaError_t launch_band_mask(const GridParams &g, const MarkerBuffers &m, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(m.band_bits, 0, sizeof(unsigned) * (size_t)(g.N / 32 + 1), s);
-    if (e != cudaSuccess || m.ns <= 0) return e;
-    if (g.dim == 3) {
-        band_mask_kernel<3><<<grid_ctas, 256, 0, s>>>(g, m, m.keys[m.sorted], m.perm[m.sorted]);
-        band_refine_kernel<3><<<grid_ctas, 256, 0, s>>>(g, m);
-    } else {
-        band_mask_kernel<2><<<grid_ctas, 256, 0, s>>>(g, m, m.keys[m.sorted], m.perm[m.sorted]);
-        band_refine_kernel<2><<<grid_ctas, 256, 0, s>>>(g, m);
-    }
-    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (m.ns > 0) {
+        const long long threads = (long long)m.ns * (g.dim == 3 ? 27 : 9);
+        const unsigned nb = (unsigned)((threads + 255) / 256);
+        if (g.dim == 3) band_scatter_kernel<3><<<nb, 256, 0, s>>>(g, m);
+        else band_scatter_kernel<2><<<nb, 256, 0, s>>>(g, m);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     tile_lists_kernel<<<1, SORT_T, 0, s>>>(g.n_tiles, m.occ_flag, m.band_flag, m.occ_list,
                                            m.band_list, m.counts);
     return cudaGetLastError();

@@ -17,11 +17,29 @@
 namespace ibmk {
 namespace {
 
+// The 1D weights of every marker at its owner cell and the two beside it,
+// per axis: wphi[k][d][i] = phi((i - 1) + 1/2 - frac_d[k][d]) (Eq. 3-point
+// delta), one thread per (marker, axis).  FP64 runs at a small fraction of
+// the FP32 rate on this GPU, so the assembly multiplies these tabulated
+// weights instead of evaluating phi for every pair of markers.
+__global__ void support_weights_kernel(const MarkerBuffers m, int dim) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = t / 3, d = t - 3 * k;
+    if (k >= m.ns || d >= dim) return;
+    const double fk = m.frac_d[(long long)k * 3 + d];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) m.wphi[(long long)k * 9 + d * 3 + i] = phi_d(((double)(i - 1) + 0.5) - fk);
+}
+
 // Row k of A~: one warp per marker, one lane per neighbour cell of its owner
 // cell (the 5^d cells whose markers can overlap its support), visited in
 // (z, y, x) order and bin order within a cell; a warp scan of the per-cell
 // counts places every entry where a serial walk would, so the rows are the
-// same whatever the warp size.
+// same whatever the warp size.  A~_kl = prod_d sum_i phi_k,d(i) phi_l,d(i)
+// over the cells of both supports, from the tabulated weights: cell
+// ck - 1 + i of marker k is cell j = ck - cl + i of marker l, and the terms
+// with j outside [0, 2] are zero (|r| >= 3/2), so skipping them leaves every
+// sum as it was with phi evaluated per pair.
 template <int DIM>
 __global__ void __launch_bounds__(128)
 assemble_kernel(const GridParams g, const MarkerBuffers m, const QuadBuffers q,
@@ -34,8 +52,7 @@ assemble_kernel(const GridParams g, const MarkerBuffers m, const QuadBuffers q,
     double wk[3][3];
     for (int d = 0; d < DIM; ++d) {
         ck[d] = m.cell[(long long)k * 3 + d];
-        const double fk = m.frac_d[(long long)k * 3 + d];
-        for (int i = 0; i < 3; ++i) wk[d][i] = phi_d(((double)(i - 1) + 0.5) - fk);
+        for (int i = 0; i < 3; ++i) wk[d][i] = m.wphi[(long long)k * 9 + d * 3 + i];
     }
     int base = 0;
     bool overflow = false;
@@ -75,11 +92,13 @@ assemble_kernel(const GridParams g, const MarkerBuffers m, const QuadBuffers q,
             const int l = perm[p];
             double a = 1.0;
             for (int d = 0; d < DIM; ++d) {
-                const int cl = m.cell[(long long)l * 3 + d];
-                const double fl = m.frac_d[(long long)l * 3 + d];
+                const int off = ck[d] - m.cell[(long long)l * 3 + d];
+                const double *wl = m.wphi + (long long)l * 9 + d * 3;
                 double sum = 0.0;
-                for (int i = 0; i < 3; ++i)
-                    sum += wk[d][i] * phi_d(((double)(ck[d] - 1 + i - cl) + 0.5) - fl);
+                for (int i = 0; i < 3; ++i) {
+                    const int j = off + i;
+                    if (j >= 0 && j <= 2) sum += wk[d][i] * wl[j];
+                }
                 a *= sum;
             }
             if (l == k) q.diag[k] = a;
@@ -116,14 +135,14 @@ __device__ __forceinline__ double block_sum(double v, double *s_red) {
 template <int NTH>
 __device__ __forceinline__ double block_max(double v, double *s_red) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = 16; o > 0; o >>= 1) v = dmax_nonneg(v, __shfl_xor_sync(0xffffffffu, v, o));
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) s_red[w] = v;
     __syncthreads();
     double r = lane < NTH / 32 ? s_red[lane] : 0.0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    for (int o = 16; o > 0; o >>= 1) r = dmax_nonneg(r, __shfl_xor_sync(0xffffffffu, r, o));
     return r;
 }
 
@@ -161,7 +180,7 @@ __device__ bool pcg_solve(int ns, const QuadBuffers &q, double *x, const double 
         double lm = 0.0;
         for (int k = threadIdx.x; k < ns; k += NTH) {
             r[k] = (rhs ? rhs[k] : 1.0) - qv[k];
-            lm = fmax(lm, fabs(r[k]));
+            lm = dmax_nonneg(lm, fabs(r[k]));
         }
         rmax = block_max<NTH>(lm, s_red);
         if (rmax <= tol) { converged = true; break; }
@@ -183,7 +202,7 @@ __device__ bool pcg_solve(int ns, const QuadBuffers &q, double *x, const double 
             for (int k = threadIdx.x; k < ns; k += NTH) {
                 x[k] += alpha * p[k];
                 r[k] -= alpha * qv[k];
-                lr = fmax(lr, fabs(r[k]));
+                lr = dmax_nonneg(lr, fabs(r[k]));
             }
             const double rm = block_max<NTH>(lr, s_red);
             ++it;
@@ -205,7 +224,7 @@ __device__ bool pcg_solve(int ns, const QuadBuffers &q, double *x, const double 
         spmv<NTH>(ns, q, x, qv, err);
         __syncthreads();
         double lm = 0.0;
-        for (int k = threadIdx.x; k < ns; k += NTH) lm = fmax(lm, fabs((rhs ? rhs[k] : 1.0) - qv[k]));
+        for (int k = threadIdx.x; k < ns; k += NTH) lm = dmax_nonneg(lm, fabs((rhs ? rhs[k] : 1.0) - qv[k]));
         rmax = block_max<NTH>(lm, s_red);
         converged = rmax <= tol;
     }
@@ -257,22 +276,33 @@ constexpr int CHOL_PB = 32;                                  // panel width
 static_assert((CHOL_MAX + CHOL_PB - 1) / CHOL_PB <= CHOL_W, "one warp per diagonal block");
 constexpr int CHOL_REFINE_MAX = 40;
 
-// x [ns] in FP64, then the FP32 factors [ns][ns | 1], 1/L_jj, r and t
+// the first CHOL_EC entries of every row of A~ are kept in shared memory for
+// the residuals of the refinement (rows hold ~10-60 entries; the rest are
+// read from the ELL arrays in global memory)
+constexpr int CHOL_EC = 32;
+
+// x [ns] and the cached row values [CHOL_EC][ns] in FP64, then the FP32
+// factors [ns][ns | 1], 1/L_jj, r and t, then the cached columns [CHOL_EC][ns]
+// and the row lengths [ns]
 size_t chol_smem(int ns) {
-    return sizeof(double) * (size_t)ns + sizeof(float) * ((size_t)ns * (ns | 1) + 3 * (size_t)ns);
+    return sizeof(double) * (size_t)ns * (1 + CHOL_EC) +
+           sizeof(float) * ((size_t)ns * (ns | 1) + 3 * (size_t)ns) +
+           sizeof(int) * (size_t)ns * (CHOL_EC + 1);
 }
 
 // Cholesky of the diagonal block [c0, c0 + w) in place, by one warp: lane r
-// holds row c0 + r of the block in registers, and step k hands the pivot
-// column L_lk to the lanes by shuffles; 1 / L_kk into dinv, *bad set on a
-// pivot that is not positive.  The row shifts left by one column per step
-// (a[l] holds column k + l at step k), so the pivot column is always a[0]
-// and every step runs the same loop body: a compact loop that stays in the
-// instruction cache, where the fully unrolled form (528 distinct
-// shuffle-update pairs, fetched once per solve) spent most of its time on
-// instruction fetch.  Same operations in the same order as the unrolled form.
+// holds row c0 + r of the block in registers; 1 / L_kk into dinv, *bad set
+// on a pivot that is not positive.  The row shifts left by one column per
+// step (a[l] holds column k + l at step k), so the pivot column is always
+// a[0] and every step runs the same compact loop body.  Step k hands the
+// pivot column L_{k+l,k} to the lanes through col (32 floats, 16-byte
+// aligned, this warp's alone): each lane stores its entry at l = lane - k
+// and reads the column back as eight 16-byte broadcast loads, where 31
+// shuffles (one per entry) set the step's latency.  Same operations in the
+// same order as a shuffle form.
 __device__ __forceinline__ void chol_diag_block(float *__restrict__ F, int ld, int c0, int w,
-                                                float *__restrict__ dinv, int lane, int *bad) {
+                                                float *__restrict__ dinv, int lane, int *bad,
+                                                float *__restrict__ col) {
     float a[CHOL_PB];
 #pragma unroll
     for (int l = 0; l < CHOL_PB; ++l)
@@ -292,11 +322,22 @@ __device__ __forceinline__ void chol_diag_block(float *__restrict__ F, int ld, i
             lk = a[0] * inv;
         }
         if (lane >= k && lane < w) F[(size_t)(c0 + lane) * ld + c0 + k] = lk;
+        // col[l] = L_{k+l,k}; the entries past 31 - k are stale and unused
+        if (lane >= k) col[lane - k] = lk;
+        __syncwarp();
+        float c[CHOL_PB];
 #pragma unroll
-        for (int l = 1; l < CHOL_PB; ++l) {
-            const float llk = __shfl_sync(0xffffffffu, lk, (k + l) & 31);
-            if (lane >= k + l) a[l] -= lk * llk;
+        for (int v = 0; v < CHOL_PB / 4; ++v) {
+            const float4 q = reinterpret_cast<const float4 *>(col)[v];
+            c[4 * v] = q.x;
+            c[4 * v + 1] = q.y;
+            c[4 * v + 2] = q.z;
+            c[4 * v + 3] = q.w;
         }
+        __syncwarp();   // every lane has read col before the next step writes it
+#pragma unroll
+        for (int l = 1; l < CHOL_PB; ++l)
+            if (lane >= k + l) a[l] -= lk * c[l];
 #pragma unroll
         for (int l = 0; l < CHOL_PB - 1; ++l) a[l] = a[l + 1];
         a[CHOL_PB - 1] = 0.0f;
@@ -401,24 +442,36 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
     const int ld = ns | 1;
     extern __shared__ __align__(16) double sD[];
     double *sx = sD;                                 // [ns] solution
-    float *F = reinterpret_cast<float *>(sx + ns);   // [ns][ld]: L on and below the diagonal,
+    double *ev = sx + ns;                            // [CHOL_EC][ns] cached row values
+    float *F = reinterpret_cast<float *>(ev + (size_t)CHOL_EC * ns);
+                                                     // [ns][ld]: L on and below the diagonal,
                                                      // the inverses X_II of its 32 x 32
                                                      // diagonal blocks transposed above it
     float *dinv = F + (size_t)ns * ld;               // [ns] 1 / L_jj, the diagonal of X_II
     float *r32 = dinv + ns;                          // [ns] residual in FP32
     float *st = r32 + ns;                            // [ns] the triangular solves' vector
+    int *ec = reinterpret_cast<int *>(st + ns);      // [CHOL_EC][ns] cached row columns
+    int *ecnt = ec + (size_t)CHOL_EC * ns;           // [ns] row lengths
     __shared__ double s_red[CHOL_T / 32];
     __shared__ int s_bad;
+    __shared__ __align__(16) float s_col[CHOL_PB];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < ns * ld; i += CHOL_T) F[i] = 0.0f;
     if (tid == 0) s_bad = 0;
     __syncthreads();
-    // lower triangle of A~ (the upper triangle stays zero)
+    // lower triangle of A~ (the upper triangle stays zero); the rows' first
+    // CHOL_EC entries and their lengths kept for the residuals
     for (int k = tid; k < ns; k += CHOL_T) {
         const int c = q.cnt[k];
+        ecnt[k] = c;
         for (int i = 0; i < c; ++i) {
             const int l = q.col[(long long)i * q.cap + k];
-            if (in_bounds(l, ns, err) && l <= k) F[(size_t)k * ld + l] = (float)q.val[(long long)i * q.cap + k];
+            const double v = q.val[(long long)i * q.cap + k];
+            if (i < CHOL_EC) {
+                ec[(size_t)i * ns + k] = l;
+                ev[(size_t)i * ns + k] = v;
+            }
+            if (in_bounds(l, ns, err) && l <= k) F[(size_t)k * ld + l] = (float)v;
         }
         sx[k] = warm ? x[k] : 0.0;
     }
@@ -426,7 +479,7 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
     // blocked Cholesky over 32-column panels, then the diagonal blocks' inverses
     for (int c0 = 0; c0 < ns; c0 += CHOL_PB) {
         const int w = min(CHOL_PB, ns - c0);
-        if (warp == 0) chol_diag_block(F, ld, c0, w, dinv, lane, &s_bad);
+        if (warp == 0) chol_diag_block(F, ld, c0, w, dinv, lane, &s_bad, s_col);
         __syncthreads();
         if (c0 + w < ns) {
             chol_panel_rows(F, ld, c0, w, ns, dinv, tid);
@@ -445,15 +498,31 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
     for (;; ++it) {
         double lm = 0.0;
         for (int k = tid; k < ns; k += CHOL_T) {
-            const int c = q.cnt[k];
+            const int c = ecnt[k];
+            const int cc = min(c, CHOL_EC);
             double sum = 0.0;
-            for (int i = 0; i < c; ++i) {
+            // the cached entries in batches of four (loads first, then the
+            // terms in row order), the rest from the ELL arrays
+            for (int i0 = 0; i0 < cc; i0 += 4) {
+                int l[4];
+                double v[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const bool in = i0 + u < cc;
+                    l[u] = in ? ec[(size_t)(i0 + u) * ns + k] : 0;
+                    v[u] = in ? ev[(size_t)(i0 + u) * ns + k] : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (i0 + u < cc && in_bounds(l[u], ns, err)) sum += v[u] * sx[l[u]];
+            }
+            for (int i = CHOL_EC; i < c; ++i) {
                 const int l = q.col[(long long)i * q.cap + k];
                 if (in_bounds(l, ns, err)) sum += q.val[(long long)i * q.cap + k] * sx[l];
             }
             const double r = (rhs ? rhs[k] : 1.0) - sum;
             r32[k] = (float)r;
-            lm = fmax(lm, fabs(r));
+            lm = dmax_nonneg(lm, fabs(r));
         }
         rmax = block_max<CHOL_T>(lm, s_red);   // synchronizes
         if (!(rmax > 0.0) || (it > 0 && !(rmax < 0.5 * rprev)) || it == CHOL_REFINE_MAX) break;
@@ -464,12 +533,19 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
         __syncthreads();
         for (int b0 = 0; b0 < ns; b0 += CHOL_PB) {
             const int b1 = min(b0 + CHOL_PB, ns);
+            // (loops of the panel width with predicated terms: the loads of
+            // every term issue together; same terms in the same order as
+            // loops that stop at the ragged end)
             if (warp == 0) {
                 const int i = b0 + lane;
                 float y = 0.0f;
                 if (i < b1) {
                     y = dinv[i] * st[i];
-                    for (int cq = b0; cq < i; ++cq) y += F[(size_t)cq * ld + i] * st[cq];
+#pragma unroll
+                    for (int j = 0; j < CHOL_PB - 1; ++j) {
+                        const int cq = b0 + j;
+                        if (cq < i) y += F[(size_t)cq * ld + i] * st[cq];
+                    }
                 }
                 __syncwarp();
                 if (i < b1) st[i] = y;
@@ -478,12 +554,16 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
             for (int i = b1 + tid; i < ns; i += CHOL_T) {
                 const float *row = F + (size_t)i * ld;
                 float a0 = st[i], a1 = 0.0f;
-                int cq = b0;
-                for (; cq + 2 <= b1; cq += 2) {
-                    a0 -= row[cq] * st[cq];
-                    a1 -= row[cq + 1] * st[cq + 1];
+#pragma unroll
+                for (int j = 0; j < CHOL_PB / 2; ++j) {
+                    const int cq = b0 + 2 * j;
+                    if (cq + 2 <= b1) {
+                        a0 -= row[cq] * st[cq];
+                        a1 -= row[cq + 1] * st[cq + 1];
+                    } else if (cq < b1) {
+                        a0 -= row[cq] * st[cq];
+                    }
                 }
-                if (cq < b1) a0 -= row[cq] * st[cq];
                 st[i] = a0 + a1;
             }
             __syncthreads();
@@ -498,7 +578,11 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
                 if (c < b1) {
                     const float *row = F + (size_t)c * ld;
                     z = dinv[c] * st[c];
-                    for (int i = c + 1; i < b1; ++i) z += row[i] * st[i];
+#pragma unroll
+                    for (int j = 1; j < CHOL_PB; ++j) {
+                        const int i = b0 + j;
+                        if (i > c && i < b1) z += row[i] * st[i];
+                    }
                 }
                 __syncwarp();
                 if (c < b1) st[c] = z;
@@ -506,12 +590,16 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
             __syncthreads();
             for (int c = tid; c < b0; c += CHOL_T) {
                 float a0 = st[c], a1 = 0.0f;
-                int i = b0;
-                for (; i + 2 <= b1; i += 2) {
-                    a0 -= F[(size_t)i * ld + c] * st[i];
-                    a1 -= F[(size_t)(i + 1) * ld + c] * st[i + 1];
+#pragma unroll
+                for (int j = 0; j < CHOL_PB / 2; ++j) {
+                    const int i = b0 + 2 * j;
+                    if (i + 2 <= b1) {
+                        a0 -= F[(size_t)i * ld + c] * st[i];
+                        a1 -= F[(size_t)(i + 1) * ld + c] * st[i + 1];
+                    } else if (i < b1) {
+                        a0 -= F[(size_t)i * ld + c] * st[i];
+                    }
                 }
-                if (i < b1) a0 -= F[(size_t)i * ld + c] * st[i];
                 st[c] = a0 + a1;
             }
             __syncthreads();
@@ -563,6 +651,7 @@ cudaError_t launch_quadrature(const GridParams &g, const MarkerBuffers &m, const
     if (m.ns <= 0) return cudaSuccess;
     const unsigned *keys = m.keys[m.sorted];
     const int *perm = m.perm[m.sorted];
+    support_weights_kernel<<<(m.ns * 3 + 127) / 128, 128, 0, s>>>(m, g.dim);
     const int nb = (m.ns * 32 + 127) / 128;   // one warp per marker
     if (g.dim == 3) assemble_kernel<3><<<nb, 128, 0, s>>>(g, m, qb, keys, perm);
     else assemble_kernel<2><<<nb, 128, 0, s>>>(g, m, qb, keys, perm);
