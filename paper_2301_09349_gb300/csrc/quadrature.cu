@@ -261,8 +261,10 @@ pcg_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ rh
 // ELL rows (only their nonzeros) and the two triangular solves blocked by
 // the same panels (each diagonal block applied through its inverse); it
 // contracts by about cond(A~) times the FP32 rounding per pass and stops
-// when the FP64 residual stops falling (its rounding floor) or reaches
-// zero.  Fixed order throughout, so the result is bitwise reproducible.
+// at the FP64 residual's rounding floor: when the residual is within
+// CHOL_FLOOR of the right-hand side's size, stops falling, or reaches zero
+// (the first test saves the pass that would only confirm the floor).  Fixed
+// order throughout, so the result is bitwise reproducible.
 // If the refinement stops above tol or a pivot is not positive (a system
 // too ill-conditioned for the FP32 factor), the same CTA runs the FP64
 // Jacobi-PCG instead; ERR_NOCONV only if that fails too.
@@ -275,6 +277,7 @@ constexpr int CHOL_MAX = IBM_CHOL_MAX;
 constexpr int CHOL_PB = 32;                                  // panel width
 static_assert((CHOL_MAX + CHOL_PB - 1) / CHOL_PB <= CHOL_W, "one warp per diagonal block");
 constexpr int CHOL_REFINE_MAX = 40;
+constexpr double CHOL_FLOOR = 4.0 * 2.220446049250313e-16;   // 4 ulp of 1
 
 // the first CHOL_EC entries of every row of A~ are kept in shared memory for
 // the residuals of the refinement (rows hold ~10-60 entries; the rest are
@@ -478,6 +481,13 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
         }
         sx[k] = warm ? x[k] : 0.0;
     }
+    // the right-hand side's size, the scale of the residual's floor
+    double rscale = 1.0;
+    if (rhs) {
+        double lr = 0.0;
+        for (int k = tid; k < ns; k += CHOL_T) lr = dmax_nonneg(lr, fabs(rhs[k]));
+        rscale = block_max<CHOL_T>(lr, s_red);   // synchronizes
+    }
     __syncthreads();
     // blocked Cholesky over 32-column panels, then the diagonal blocks' inverses
     for (int c0 = 0; c0 < ns; c0 += CHOL_PB) {
@@ -528,7 +538,9 @@ chol_kernel(int ns, const QuadBuffers q, double *x, const double *__restrict__ r
             lm = dmax_nonneg(lm, fabs(r));
         }
         rmax = block_max<CHOL_T>(lm, s_red);   // synchronizes
-        if (!(rmax > 0.0) || (it > 0 && !(rmax < 0.5 * rprev)) || it == CHOL_REFINE_MAX) break;
+        if (!(rmax > 0.0) || rmax <= CHOL_FLOOR * rscale || (it > 0 && !(rmax < 0.5 * rprev)) ||
+            it == CHOL_REFINE_MAX)
+            break;
         rprev = rmax;
         // t = L^-1 r: per panel, t_I = X_II t_I (warp 0), then the rows
         // below take -L_iI t_I
