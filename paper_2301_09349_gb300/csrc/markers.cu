@@ -19,6 +19,8 @@
 //    the same thread.
 #include <float.h>
 
+#include <algorithm>
+
 #include "internal.h"
 #include "marker_ops.cuh"
 
@@ -259,8 +261,24 @@ __global__ void motion_kernel(const GridParams g, int ns, const double *__restri
 // radix sort gives), tile offsets and occupancy, the forced-cell scatter and
 // the tile lists - the work of motion_kernel, bin_sort_kernel,
 // tile_offsets_kernel, tile_flags_kernel, band_scatter_kernel and
-// tile_lists_kernel, with barriers in place of six launches.  band_bits must
-// be clear on entry; the sorted order goes to keys[0] / perm[0].
+// tile_lists_kernel, with barriers in place of six launches.  band_bits
+// must hold exactly the previous marker set's forced cells on entry (it
+// clears them first, from the previous owner cells, instead of a memset of
+// the whole mask); the sorted order goes to keys[0] / perm[0].
+// Support cell sc (0 .. 3^d - 1, x fastest) of marker k from its owner cell:
+// its index in j, false when it lies outside the grid.
+__device__ __forceinline__ bool support_cell(const GridParams &g, const MarkerBuffers &m, int k,
+                                             int sc, long long &j) {
+    const int o[3] = {sc % 3 - 1, (sc / 3) % 3 - 1, g.dim == 3 ? sc / 9 - 1 : 0};
+    int c[3] = {0, 0, 0};
+    for (int d = 0; d < g.dim; ++d) {
+        c[d] = m.cell[(long long)k * 3 + d] + o[d];
+        if (c[d] < 0 || c[d] >= g.n[d]) return false;
+    }
+    j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
+    return in_bounds(j, g.N, m.err);
+}
+
 constexpr int SMALL_NS = kSmallRebuildNs;
 static_assert(SMALL_NS <= SORT_T, "one marker per thread");
 __global__ void __launch_bounds__(SORT_T)
@@ -271,7 +289,14 @@ small_rebuild_kernel(const GridParams g, const MarkerBuffers m, double amp, doub
     __shared__ int s_warp[33];
     __shared__ double s_mv[2];
     const int tid = threadIdx.x, ns = m.ns;
+    const int nsc = g.dim == 3 ? 27 : 9;
     if (tid == 0) motion_offset(amp, freq, m.t, dt, dt_fixed, s_mv[0], s_mv[1]);
+    // the previous forced cells off (the same support cells the scatter
+    // below sets, from the owner cells of the previous step)
+    for (int i = tid; i < ns * nsc; i += SORT_T) {
+        long long j;
+        if (support_cell(g, m, i / nsc, i % nsc, j)) atomicAnd(m.band_bits + (j >> 5), ~(1u << (j & 31)));
+    }
     __syncthreads();
     int bad = 0;
     if (tid < ns) {
@@ -317,21 +342,13 @@ small_rebuild_kernel(const GridParams g, const MarkerBuffers m, double amp, doub
     }
     __syncthreads();
     // forced cells: the 3^d support cells of every marker
-    const int nsc = g.dim == 3 ? 27 : 9;
     for (int i = tid; i < ns * nsc; i += SORT_T) {
-        const int k = i / nsc, sc = i - k * nsc;
-        const int o[3] = {sc % 3 - 1, (sc / 3) % 3 - 1, g.dim == 3 ? sc / 9 - 1 : 0};
-        int c[3] = {0, 0, 0};
-        bool in = true;
-        for (int d = 0; d < g.dim; ++d) {
-            c[d] = m.cell[(long long)k * 3 + d] + o[d];
-            in = in && c[d] >= 0 && c[d] < g.n[d];
-        }
-        if (!in) continue;
-        const long long j = c[0] + (long long)g.n[0] * (c[1] + (long long)g.n[1] * c[2]);
-        if (!in_bounds(j, g.N, m.err)) continue;
+        long long j;
+        if (!support_cell(g, m, i / nsc, i % nsc, j)) continue;
         atomicOr(m.band_bits + (j >> 5), 1u << (j & 31));
-        m.band_flag[cell_key(g, c[0], c[1], c[2]) / cpt] = 1;
+        const int cx = (int)(j % g.n[0]), cy = (int)((j / g.n[0]) % g.n[1]),
+                  cz = (int)(j / ((long long)g.n[0] * g.n[1]));
+        m.band_flag[cell_key(g, cx, cy, cz) / cpt] = 1;
     }
     __syncthreads();
     tile_lists(g.n_tiles, m.occ_flag, m.band_flag, m.occ_list, m.band_list, m.counts, s_warp);
@@ -1230,10 +1247,14 @@ __global__ void __launch_bounds__(32)
 finish_kernel(const GridParams g, int ns, const MarkerBuffers m, const double *__restrict__ blockmax,
               int nb, int nbs, double *__restrict__ dt_ptr, int *__restrict__ err, double dt_fixed,
               double *__restrict__ part, unsigned *__restrict__ ticket) {
+    // CTAs c < Cm form the marker chunks (as the batch finish does); the
+    // maxima are shared over all C >= Cm CTAs, and CTAs past Cm add exact
+    // zeros to the sums, as the empty lanes of the batch's combine do
     const int C = gridDim.x, c = blockIdx.x, lane = threadIdx.x;
+    const int Cm = finish_chunks(ns);
+    const int k0 = c < Cm ? finish_cut(ns, c, Cm) : ns, k1 = c < Cm ? finish_cut(ns, c + 1, Cm) : ns;
     double a[5];
-    finish_chunk(g, m, finish_cut(ns, c, C), finish_cut(ns, c + 1, C), blockmax,
-                 finish_cut(nb, c, C), finish_cut(nb, c + 1, C), m.bandmax,
+    finish_chunk(g, m, k0, k1, blockmax, finish_cut(nb, c, C), finish_cut(nb, c + 1, C), m.bandmax,
                  finish_cut(nbs, c, C), finish_cut(nbs, c + 1, C), lane, a);
     unsigned last = 0;
     if (lane == 0) {
@@ -1390,8 +1411,6 @@ cudaError_t launch_small_rebuild(const GridParams &g, MarkerBuffers &m, double a
                                  int axis, const double *dt, double dt_fixed, cudaStream_t s) {
     if (m.ns <= 0 || m.ns > SMALL_NS) return cudaErrorInvalidValue;
     m.sorted = 0;
-    cudaError_t e = cudaMemsetAsync(m.band_bits, 0, sizeof(unsigned) * (size_t)(g.N / 32 + 1), s);
-    if (e != cudaSuccess) return e;
     small_rebuild_kernel<<<1, SORT_T, 0, s>>>(g, m, amp, freq, axis, dt, dt_fixed);
     return cudaGetLastError();
 }
@@ -1505,7 +1524,9 @@ cudaError_t launch_spread_build(const GridParams &g, int fp_bytes, const MarkerB
 
 cudaError_t launch_finish(const GridParams &g, const MarkerBuffers &m, const FluidBuffers &fb,
                           int nb, int nbs, double dt_fixed, cudaStream_t s) {
-    finish_kernel<<<finish_chunks(m.ns), 32, 0, s>>>(g, m.ns, m, fb.blockmax, nb, nbs, fb.dt, fb.err, dt_fixed,
+    // the marker chunks, and at least one CTA per 512 maxima (up to kFinishCtas)
+    const int C = std::max(finish_chunks(m.ns), std::min(kFinishCtas, (nb + nbs + 511) / 512));
+    finish_kernel<<<C, 32, 0, s>>>(g, m.ns, m, fb.blockmax, nb, nbs, fb.dt, fb.err, dt_fixed,
                                       m.finpart, fb.counter + 1);
     return cudaGetLastError();
 }
