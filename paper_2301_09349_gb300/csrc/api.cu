@@ -246,7 +246,8 @@ const char *const kProfNames[IBM_PROF_GROUPS] = {"ibm: fluid stage 1", "ibm: flu
                                                  "ibm: spreading + forced update",
                                                  "ibm: force sums, next dt"};
 
-cudaError_t prof_begin(ibm_grid *g, int group, int launches, long *rec) {
+cudaError_t prof_begin(ibm_grid *g, int group, int launches, long *rec,
+                       cudaStream_t on = nullptr) {
     *rec = -1;
     if (!g->prof) return cudaSuccess;
     nvtxRangePushA(kProfNames[group]);
@@ -260,12 +261,12 @@ cudaError_t prof_begin(ibm_grid *g, int group, int launches, long *rec) {
     g->ev_used += 2;
     g->recs.push_back({group, launches, i});
     *rec = (long)g->recs.size() - 1;
-    return cudaEventRecord(g->ev_pool[i], g->stream);
+    return cudaEventRecord(g->ev_pool[i], on ? on : g->stream);
 }
 
-cudaError_t prof_end(ibm_grid *g, long rec) {
+cudaError_t prof_end(ibm_grid *g, long rec, cudaStream_t on = nullptr) {
     if (rec < 0) return cudaSuccess;
-    const cudaError_t e = cudaEventRecord(g->ev_pool[g->recs[rec].ev + 1], g->stream);
+    const cudaError_t e = cudaEventRecord(g->ev_pool[g->recs[rec].ev + 1], on ? on : g->stream);
     nvtxRangePop();
     return e;
 }
@@ -601,6 +602,15 @@ ibm_status ibm_set_wall_temperature(ibm_grid *g, const double *Tw) {
 }  // extern "C"
 
 namespace {
+// the side stream and fork/join events of the small-body marker pipeline
+cudaError_t ensure_side(ibm_grid *g) {
+    cudaError_t e = cudaSuccess;
+    if (!g->side) e = cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&g->ev_fork, &g->ev_bins, &g->ev_quad})
+        if (e == cudaSuccess && !*ev) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    return e;
+}
+
 // nsteps IBM steps launched on stream s (the handle's stream, or the private
 // stream a graph is captured on)
 ibm_status run_steps(ibm_grid *g, int nsteps, double dt_fixed, cudaStream_t s) {
@@ -617,30 +627,46 @@ ibm_status run_steps(ibm_grid *g, int nsteps, double dt_fixed, cudaStream_t s) {
                                    (size_t)(g->rec_steps / g->adj.every) * align_up(state_bytes(g->desc), 256),
                                Un, state_bytes(g->desc), cudaMemcpyDeviceToDevice, s),
                "checkpoint");
+        // A small moving body's marker pipeline (positions at t^{n+1}, bins,
+        // forced cells, weights) depends only on the time and the step
+        // size: it runs on a side stream beside stage 1; stage 2 (which
+        // skips the forced cells) waits for the bins, the interpolation for
+        // the weights.
+        const bool fork = g->moving && g->mb.ns > 0 && g->mb.ns <= kSmallRebuildNs;
+        if (fork) {
+            CU(ensure_side(g), "side stream");
+            CU(cudaEventRecord(g->ev_fork, s), "fork");
+            CU(cudaStreamWaitEvent(g->side, g->ev_fork, 0), "fork");
+            CU(prof_begin(g, IBM_PROF_MARKERS, 3, &rec, g->side), "profile");
+            CU(launch_small_rebuild(g->gp, g->mb, g->motion.amp, g->motion.freq, g->motion.axis,
+                                    g->fb.dt, dt_fixed, g->side),
+               "motion + bins");
+            CU(cudaEventRecord(g->ev_bins, g->side), "bins");
+            CU(launch_quadrature(g->gp, g->mb, g->qb, g->cg_tol, g->cg_maxit, 1, g->side, 1),
+               "quadrature");
+            CU(prof_end(g, rec, g->side), "profile");
+            CU(cudaEventRecord(g->ev_quad, g->side), "weights");
+        }
         CU(prof_begin(g, IBM_PROF_STAGE1, 1, &rec), "profile");
         CU(launch_stage1(g->gp, fpb, Un, U1, g->fb, dt_fixed, s), "stage 1");
         CU(prof_end(g, rec), "profile");
-        if (g->moving && g->mb.ns > 0) {
-            if (g->mb.ns <= kSmallRebuildNs) {
-                // small body: motion, bins, forced cells and tile lists in one
-                // launch, then the quadrature (warm start)
-                CU(prof_begin(g, IBM_PROF_MARKERS, 4, &rec), "profile");
-                CU(launch_small_rebuild(g->gp, g->mb, g->motion.amp, g->motion.freq,
-                                        g->motion.axis, g->fb.dt, dt_fixed, s),
-                   "motion + bins");
-                CU(launch_quadrature(g->gp, g->mb, g->qb, g->cg_tol, g->cg_maxit, 1, s),
-                   "quadrature");
-            } else {
-                CU(prof_begin(g, IBM_PROF_MARKERS, 9, &rec), "profile");
-                CU(launch_motion(g->gp, g->mb, g->motion.amp, g->motion.freq, g->motion.axis,
-                                 g->fb.dt, dt_fixed, s),
-                   "motion");
-                ibm_status st = rebuild_markers(g, 1, s);
-                if (st != IBM_OK) return st;
-            }
+        if (fork) {
+            CU(cudaStreamWaitEvent(s, g->ev_bins, 0), "join bins");
+        } else if (g->moving && g->mb.ns > 0) {
+            CU(prof_begin(g, IBM_PROF_MARKERS, 9, &rec), "profile");
+            CU(launch_motion(g->gp, g->mb, g->motion.amp, g->motion.freq, g->motion.axis,
+                             g->fb.dt, dt_fixed, s),
+               "motion");
+            ibm_status st = rebuild_markers(g, 1, s);
+            if (st != IBM_OK) return st;
             CU(prof_end(g, rec), "profile");
         }
+        bool joined = !fork;
         if (g->desc.forcing_per_stage && g->mb.ns > 0) {
+            if (!joined) {
+                CU(cudaStreamWaitEvent(s, g->ev_quad, 0), "join weights");
+                joined = true;
+            }
             // variant: the first stage is forced too; its sources are summed now
             CU(prof_begin(g, IBM_PROF_INTERP, 2, &rec), "profile");
             CU(launch_interp_force(g->gp, fpb, U1, g->mb, ctas, s), "interp/force (stage 1)");
@@ -653,6 +679,7 @@ ibm_status run_steps(ibm_grid *g, int nsteps, double dt_fixed, cudaStream_t s) {
         CU(prof_begin(g, IBM_PROF_STAGE2, 1, &rec), "profile");
         CU(launch_stage2(g->gp, fpb, Un, U1, Us, g->fb, dt_fixed, s), "stage 2");
         CU(prof_end(g, rec), "profile");
+        if (!joined) CU(cudaStreamWaitEvent(s, g->ev_quad, 0), "join weights");
         if (g->mb.ns > 0) {
             CU(prof_begin(g, IBM_PROF_INTERP, 1, &rec), "profile");
             CU(launch_interp_force(g->gp, fpb, Us, g->mb, ctas, s), "interp/force");

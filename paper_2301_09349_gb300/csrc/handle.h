@@ -63,6 +63,11 @@ struct ibm_grid {
     int graph_steps = 0;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+
+    // small moving bodies: the marker pipeline runs on a side stream beside
+    // fluid stage 1 (forked and joined by events, also inside a capture)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_bins = nullptr, ev_quad = nullptr;
     double gexec_dt[2] = {0.0, 0.0};
 
     void drop_graphs() {
@@ -74,6 +79,9 @@ struct ibm_grid {
     ~ibm_grid() {
         drop_graphs();
         if (cap) cudaStreamDestroy(cap);
+        if (side) cudaStreamDestroy(side);
+        for (cudaEvent_t e : {ev_fork, ev_bins, ev_quad})
+            if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     }
 };

@@ -310,8 +310,10 @@ struct QuadBuffers {
 };
 
 int quad_row_width(int dim);
+// A~ assembly and the solve A~ eps~ = 1 (warm: start from the current eps~;
+// have_weights: m.wphi already holds the current positions' support weights)
 cudaError_t launch_quadrature(const GridParams &g, const MarkerBuffers &m, const QuadBuffers &qb,
-                              double tol, int maxit, int warm, cudaStream_t s);
+                              double tol, int maxit, int warm, cudaStream_t s, int have_weights = 0);
 cudaError_t launch_quadrature_solve(int ns, const QuadBuffers &qb, const double *rhs, double *x,
                                     double tol, int maxit, int *err, cudaStream_t s);
 

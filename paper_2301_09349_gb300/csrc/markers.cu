@@ -261,7 +261,8 @@ __global__ void motion_kernel(const GridParams g, int ns, const double *__restri
 // radix sort gives), tile offsets and occupancy, the forced-cell scatter and
 // the tile lists - the work of motion_kernel, bin_sort_kernel,
 // tile_offsets_kernel, tile_flags_kernel, band_scatter_kernel and
-// tile_lists_kernel, with barriers in place of six launches.  band_bits
+// tile_lists_kernel, and the support weights of support_weights_kernel, with
+// barriers in place of seven launches.  band_bits
 // must hold exactly the previous marker set's forced cells on entry (it
 // clears them first, from the previous owner cells, instead of a memset of
 // the whole mask); the sorted order goes to keys[0] / perm[0].
@@ -307,6 +308,14 @@ small_rebuild_kernel(const GridParams g, const MarkerBuffers m, double amp, doub
             m.Ub[q] = m.Ub0[q] + (d == axis ? s_mv[1] : 0.0);
         }
         s_key[k] = owner_cell(g, m.X, k, m.cell, m.frac_d, m.frac_f, bad);
+        // the marker's 1D support weights for the assembly (those of
+        // support_weights_kernel, which the quadrature then skips)
+        for (int d = 0; d < g.dim; ++d) {
+            const double fk = m.frac_d[(long long)k * 3 + d];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                m.wphi[(long long)k * 9 + d * 3 + i] = phi_d(((double)(i - 1) + 0.5) - fk);
+        }
     }
     if (bad) record_error(m.err, ERR_MARKER_RANGE);
     __syncthreads();
