@@ -60,6 +60,7 @@ struct ibm_batch {
     std::vector<long long> tbl_gen;
     int n_stage = 0, n_band = 0, n_mk = 0;
     size_t spread_smem = 0;
+    bool spread_op = false;   // spreading through the cases' operators
     ibm_batch_tuning tune{0, 4, 1};
 
     // kernel timing (ibm_batch_profile): event pairs around each group;
@@ -173,7 +174,8 @@ BatchLayout batch_layout(int ncases, const ibm_grid_desc *descs, const int *max_
         int most = 0;
         for (int s = 0; s < kBatchShapes; ++s) most = std::max(most, tiles_of_shape(descs[c], s));
         L.stage_cap += most;
-        L.band_cap += marker_tiles(descs[c]);
+        // band items: band tiles, or runs of 32 forced cells (at most 3^2 per marker)
+        L.band_cap += std::max(marker_tiles(descs[c]), (9 * mm + 31) / 32);
         L.mk_cap += mm;
     }
     auto take = [&](size_t bytes) {
@@ -207,6 +209,11 @@ ibm_status build_tables(ibm_batch *b) {
     BCU(cudaStreamSynchronize(b->stream), "stream synchronize");
 
     const int shape = b->tune.tile_shape;
+    // every case's spreading operator built (static markers): the batch
+    // spreads through them, in runs of 32 forced cells
+    bool use_op = true;
+    for (int c = 0; c < nc; ++c)
+        if (b->grids[c]->mb.ns > 0 && !b->grids[c]->mb.sp_ready) use_op = false;
     std::vector<int2> st, bd, mk;
     std::vector<BatchCase> tb((size_t)2 * nc);
     size_t smem = 0;
@@ -223,10 +230,11 @@ ibm_status build_tables(ibm_batch *b) {
         bc.nitems = tiles_of_shape(g->desc, shape);
         for (int t = 0; t < bc.nitems; ++t) st.push_back(make_int2(c, t));
         const int ns = g->mb.ns;
-        const int nband = ns > 0 ? counts[(size_t)c * 4 + 1] : 0;
+        const int ncell = ns > 0 ? counts[(size_t)c * 4 + 2] : 0;
+        const int nband = ns <= 0 ? 0 : use_op ? (ncell + 31) / 32 : counts[(size_t)c * 4 + 1];
         bc.band0 = (int)bd.size();
         bc.nband = nband;
-        for (int i = 0; i < nband; ++i) bd.push_back(make_int2(c, i));
+        for (int i = 0; i < nband; ++i) bd.push_back(make_int2(c, use_op ? 32 * i : i));
         for (int k = 0; k < ns; ++k) mk.push_back(make_int2(c, k));
         if (ns > 0) smem = std::max(smem, batch_spread_smem(g->gp, b->fp_bytes));
         for (int p = 0; p < 2; ++p) {
@@ -259,6 +267,7 @@ ibm_status build_tables(ibm_batch *b) {
     b->n_band = (int)bd.size();
     b->n_mk = (int)mk.size();
     b->spread_smem = smem;
+    b->spread_op = use_op;
     b->tbl_cur.resize(nc);
     b->tbl_gen.resize(nc);
     for (int c = 0; c < nc; ++c) {
@@ -309,6 +318,8 @@ cudaError_t launch_group(ibm_batch *b, int p, int group, double dt_fixed, cudaSt
     case IBM_PROF_INTERP:
         return launch_batch_interp(fp, t, b->mk_items, b->n_mk, b->tune.markers_per_block, s);
     case IBM_PROF_SPREAD:
+        if (b->spread_op)
+            return launch_batch_spread_static(fp, t, b->band_items, b->n_band, b->band_max, s);
         return launch_batch_spread(fp, b->spread_smem, t, b->band_items, b->n_band, b->band_max,
                                    b->n_sm, s);
     case IBM_PROF_FINISH:

@@ -239,6 +239,10 @@ cudaError_t launch_batch_interp(int fp_bytes, const BatchCase *cases, const int2
                                 int n_items, int warps, cudaStream_t s);
 // spreading + forced update: items are (case, index into the case's band
 // list); band_max[item] receives the step-size maximum of the forced cells
+// the spreading of a batch through its cases' operators (static markers):
+// items (case, first of 32 forced cells)
+cudaError_t launch_batch_spread_static(int fp_bytes, const BatchCase *cases, const int2 *items,
+                                       int n_items, double *band_max, cudaStream_t s);
 cudaError_t launch_batch_spread(int fp_bytes, size_t smem, const BatchCase *cases,
                                 const int2 *items, int n_items, double *band_max, int n_sm,
                                 cudaStream_t s);

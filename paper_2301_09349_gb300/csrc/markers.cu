@@ -944,68 +944,77 @@ __device__ __forceinline__ void load4(const double *p, double v[4]) {
     v[3] = b.y;
 }
 
+constexpr int SPS_B = 8;   // operator entries whose loads issue together
+
+// Forced cell i of the spreading operator: its entries summed in the stored
+// order, the forced update, its step-size rate into smax.
+template <int DIM, typename T>
+__device__ __forceinline__ void spread_static_cell(const GridParams &g, T *__restrict__ U,
+                                                   const MarkerBuffers &m, int i, T &smax,
+                                                   bool &ok) {
+    using R = T;
+    const R *gs = reinterpret_cast<const R *>(m.gs);
+    const R *ew = reinterpret_cast<const R *>(m.sp_w);
+    const SpreadCell rc = m.sp_cell[i];
+    if (rc.n <= 0 || !in_bounds(rc.j, g.N, m.err)) return;
+    // the cell's state is loaded ahead of its entries
+    T u[DIM + 2];
+#pragma unroll
+    for (int cc = 0; cc < DIM + 2; ++cc) u[cc] = U[cc * g.N + rc.j];
+    R f[DIM], qh = R(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) f[d] = R(0);
+    // entries in batches of SPS_B: their loads issue together, then
+    // the terms in the stored order
+    const int pe = rc.start + rc.n;
+    for (int p0 = rc.start; p0 < pe; p0 += SPS_B) {
+        int k[SPS_B];
+        R w[SPS_B], v[SPS_B][4];
+#pragma unroll
+        for (int b = 0; b < SPS_B; ++b) {
+            const int p = p0 + b;
+            const bool in = p < pe && in_bounds(p, m.sp_cap, m.err);
+            k[b] = in ? __ldg(m.sp_k + p) : -1;
+            w[b] = in ? __ldg(ew + p) : R(0);
+        }
+#pragma unroll
+        for (int b = 0; b < SPS_B; ++b) {
+            if (k[b] >= 0 && in_bounds(k[b], m.ns, m.err)) {
+                load4(gs + 4 * (long long)k[b], v[b]);
+            } else {
+                k[b] = -1;
+                v[b][0] = v[b][1] = v[b][2] = v[b][3] = R(0);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < SPS_B; ++b) {
+            if (k[b] < 0) continue;
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) f[d] += v[b][d] * w[b];
+            qh += v[b][3] * w[b];
+        }
+    }
+    // the forced update (as apply_forcing), the rate from the new state
+    force_cell<DIM, T>(g, u, f, qh);
+#pragma unroll
+    for (int cc = 1; cc < DIM + 2; ++cc) U[cc * g.N + rc.j] = u[cc];
+    smax = fmax(smax, step_rate<DIM, T>(g, u, ok));
+}
+
 // Spreading and forced update of static markers through their operator:
 // one thread per forced cell sums its entries in the stored order (the
 // terms and the order of spread_tile, so the results are bitwise the same),
 // then applies the forcing.  One step-size maximum per CTA in bandmax.
 constexpr int SPS_T = 256;
-constexpr int SPS_B = 8;   // operator entries whose loads issue together
 template <int DIM, typename T>
 __global__ void __launch_bounds__(SPS_T)
 spread_static_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m) {
-    using R = T;
     __shared__ double s_max[SPS_T / 32];
     const int nc = min(m.counts[2], m.sp_cap);
-    const R *gs = reinterpret_cast<const R *>(m.gs);
-    const R *ew = reinterpret_cast<const R *>(m.sp_w);
     T smax = T(0);
     bool ok = true;
-    for (int i = blockIdx.x * SPS_T + threadIdx.x; i < nc; i += gridDim.x * SPS_T) {
-        const SpreadCell rc = m.sp_cell[i];
-        if (rc.n <= 0 || !in_bounds(rc.j, g.N, m.err)) continue;
-        // the cell's state is loaded ahead of its entries
-        T u[DIM + 2];
-#pragma unroll
-        for (int cc = 0; cc < DIM + 2; ++cc) u[cc] = U[cc * g.N + rc.j];
-        R f[DIM], qh = R(0);
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) f[d] = R(0);
-        // entries in batches of SPS_B: their loads issue together, then
-        // the terms in the stored order
-        const int pe = rc.start + rc.n;
-        for (int p0 = rc.start; p0 < pe; p0 += SPS_B) {
-            int k[SPS_B];
-            R w[SPS_B], v[SPS_B][4];
-#pragma unroll
-            for (int b = 0; b < SPS_B; ++b) {
-                const int p = p0 + b;
-                const bool in = p < pe && in_bounds(p, m.sp_cap, m.err);
-                k[b] = in ? __ldg(m.sp_k + p) : -1;
-                w[b] = in ? __ldg(ew + p) : R(0);
-            }
-#pragma unroll
-            for (int b = 0; b < SPS_B; ++b) {
-                if (k[b] >= 0 && in_bounds(k[b], m.ns, m.err)) {
-                    load4(gs + 4 * (long long)k[b], v[b]);
-                } else {
-                    k[b] = -1;
-                    v[b][0] = v[b][1] = v[b][2] = v[b][3] = R(0);
-                }
-            }
-#pragma unroll
-            for (int b = 0; b < SPS_B; ++b) {
-                if (k[b] < 0) continue;
-#pragma unroll
-                for (int d = 0; d < DIM; ++d) f[d] += v[b][d] * w[b];
-                qh += v[b][3] * w[b];
-            }
-        }
-        // the forced update (as apply_forcing), the rate from the new state
-        force_cell<DIM, T>(g, u, f, qh);
-#pragma unroll
-        for (int cc = 1; cc < DIM + 2; ++cc) U[cc * g.N + rc.j] = u[cc];
-        smax = fmax(smax, step_rate<DIM, T>(g, u, ok));
-    }
+    for (int i = blockIdx.x * SPS_T + threadIdx.x; i < nc; i += gridDim.x * SPS_T)
+        spread_static_cell<DIM, T>(g, U, m, i, smax, ok);
 #pragma unroll
     for (int o2 = 16; o2 > 0; o2 >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o2));
     const int bad = __syncthreads_or(!ok);
@@ -1016,6 +1025,33 @@ spread_static_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers 
         for (int w = 1; w < SPS_T / 32; ++w) mx = dmax_nonneg(mx, s_max[w]);
         m.bandmax[blockIdx.x] = mx;
         if (bad) record_error(m.err, ERR_NONFINITE);
+    }
+}
+
+// Batched form of the operator spreading (static markers): items are (case,
+// first of a run of 32 of the case's forced cells), one warp each; one
+// step-size maximum per item.  The cells are formed as in
+// spread_static_kernel, so a batch step stays bitwise the per-case step.
+template <typename T>
+__global__ void __launch_bounds__(256)
+batch_spread_static_kernel(const BatchCase *__restrict__ cases, const int2 *__restrict__ items,
+                           int n_items, double *__restrict__ band_max) {
+    const int lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < n_items; it += nw) {
+        const int2 w = items[it];
+        const BatchCase &bc = cases[w.x];
+        const int nc = min(bc.m.counts[2], bc.m.sp_cap);
+        T smax = T(0);
+        bool ok = true;
+        if (w.y + lane < nc) spread_static_cell<2, T>(bc.g, (T *)bc.Us, bc.m, w.y + lane, smax, ok);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+        const bool bad = __any_sync(0xffffffffu, !ok);
+        if (lane == 0) {
+            band_max[it] = (double)smax;
+            if (bad) record_error(bc.err, ERR_NONFINITE);
+        }
     }
 }
 
@@ -1562,6 +1598,15 @@ static cudaError_t batch_spread_t(size_t smem, const BatchCase *cases, const int
     cudaError_t e = func_smem_attr((const void *)batch_spread_kernel<2, T>, smem);
     if (e != cudaSuccess) return e;
     batch_spread_kernel<2, T><<<ctas, SP_T<2>, smem, s>>>(cases, items, n_items, band_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_spread_static(int fp_bytes, const BatchCase *cases, const int2 *items,
+                                       int n_items, double *band_max, cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    const unsigned nb = (unsigned)((n_items + 7) / 8);   // eight warps per CTA
+    if (fp_bytes == 4) batch_spread_static_kernel<float><<<nb, 256, 0, s>>>(cases, items, n_items, band_max);
+    else batch_spread_static_kernel<double><<<nb, 256, 0, s>>>(cases, items, n_items, band_max);
     return cudaGetLastError();
 }
 
