@@ -680,18 +680,24 @@ ibm_status run_steps(ibm_grid *g, int nsteps, double dt_fixed, cudaStream_t s) {
         CU(launch_stage2(g->gp, fpb, Un, U1, Us, g->fb, dt_fixed, s), "stage 2");
         CU(prof_end(g, rec), "profile");
         if (!joined) CU(cudaStreamWaitEvent(s, g->ev_quad, 0), "join weights");
+        // static markers: the finish runs inside the spreading launch
+        const bool fused_finish = g->mb.ns > 0 && g->mb.sp_ready;
         if (g->mb.ns > 0) {
             CU(prof_begin(g, IBM_PROF_INTERP, 1, &rec), "profile");
             CU(launch_interp_force(g->gp, fpb, Us, g->mb, ctas, s), "interp/force");
             CU(prof_end(g, rec), "profile");
+            const FinishArgs fa = finish_args(g->mb, g->fb, nb, dt_fixed);
             CU(prof_begin(g, IBM_PROF_SPREAD, 1, &rec), "profile");
-            CU(launch_spread_apply(g->gp, fpb, Us, g->mb, ctas, s), "spread/apply");
+            CU(launch_spread_apply(g->gp, fpb, Us, g->mb, ctas, s, fused_finish ? &fa : nullptr),
+               "spread/apply");
             CU(prof_end(g, rec), "profile");
         }
-        CU(prof_begin(g, IBM_PROF_FINISH, 1, &rec), "profile");
-        CU(launch_finish(g->gp, g->mb, g->fb, nb, g->mb.ns > 0 ? ctas : 0, dt_fixed, s),
-           "finish");
-        CU(prof_end(g, rec), "profile");
+        if (!fused_finish) {
+            CU(prof_begin(g, IBM_PROF_FINISH, 1, &rec), "profile");
+            CU(launch_finish(g->gp, g->mb, g->fb, nb, g->mb.ns > 0 ? ctas : 0, dt_fixed, s),
+               "finish");
+            CU(prof_end(g, rec), "profile");
+        }
         if (g->recording) {
             CU(cudaMemcpyAsync(g->adj.dt_hist + g->rec_steps, g->mb.sums + 4, sizeof(double),
                                cudaMemcpyDeviceToDevice, s),

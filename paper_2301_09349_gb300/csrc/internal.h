@@ -188,10 +188,24 @@ cudaError_t launch_band_mask(const GridParams &g, const MarkerBuffers &m, cudaSt
 cudaError_t launch_bin(const GridParams &g, MarkerBuffers &m, cudaStream_t s);
 cudaError_t launch_interp_force(const GridParams &g, int fp_bytes, const void *U,
                                 const MarkerBuffers &m, int grid_ctas, cudaStream_t s);
+// What the step's finish needs when it runs inside the spreading launch.
+struct FinishArgs {
+    const double *blockmax;   // stage-2 per-CTA maxima
+    int nb;                   // their count
+    double *dt;               // the next step size (device)
+    int *err;                 // the device error word
+    double dt_fixed;          // > 0: the step size used
+    double *part;             // kFinishCtas x 5 chunk partials
+    unsigned *ticket;         // last-CTA ticket (zero between launches)
+};
+FinishArgs finish_args(const MarkerBuffers &m, const FluidBuffers &fb, int nb, double dt_fixed);
+
 // spreading and forced update: through the precomputed operator when
-// m.sp_ready, else gathering straight from the binned markers
+// m.sp_ready, else gathering straight from the binned markers; with fin
+// (operator path only) the step's finish runs in the same launch
 cudaError_t launch_spread_apply(const GridParams &g, int fp_bytes, void *U,
-                                const MarkerBuffers &m, int grid_ctas, cudaStream_t s);
+                                const MarkerBuffers &m, int grid_ctas, cudaStream_t s,
+                                const FinishArgs *fin = nullptr);
 // the spreading operator of the current (static) markers, from their bins
 cudaError_t launch_spread_build(const GridParams &g, int fp_bytes, const MarkerBuffers &m,
                                 int grid_ctas, cudaStream_t s);

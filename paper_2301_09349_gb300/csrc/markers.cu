@@ -1284,6 +1284,71 @@ partial_sums_kernel(const GridParams g, const MarkerBuffers m) {
         for (int i = 0; i < 4; ++i) m.sums[8 + i] = a[i];
 }
 
+// The forced update of static markers with the step's finish in the same
+// launch (one kernel less per step): CTAs c < C_m also form marker chunk c's
+// force/heat partial (one warp, as finish_kernel's CTA c does), every CTA
+// its forced cells' step-size maximum; the last CTA to finish (ticket)
+// combines the partials in finish_kernel's tree (so the sums are bitwise
+// those of the separate finish), takes the largest rate over the stage-2
+// and forced-cell maxima, updates the time and the next step size, and
+// resets the ticket.
+template <int DIM, typename T>
+__global__ void __launch_bounds__(SPS_T)
+spread_static_finish_kernel(const GridParams g, T *__restrict__ U, const MarkerBuffers m,
+                            const FinishArgs f) {
+    __shared__ double s_max[SPS_T / 32];
+    __shared__ int s_last;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int ns = m.ns, Cm = finish_chunks(ns);
+    if ((int)blockIdx.x < Cm && w == 0) {
+        double a[5];
+        finish_chunk(g, m, finish_cut(ns, blockIdx.x, Cm), finish_cut(ns, blockIdx.x + 1, Cm),
+                     f.blockmax, 0, 0, m.bandmax, 0, 0, lane, a);
+        if (lane == 0)
+            for (int i = 0; i < 5; ++i) f.part[blockIdx.x * 5 + i] = a[i];
+    }
+    const int nc = min(m.counts[2], m.sp_cap);
+    T smax = T(0);
+    bool ok = true;
+    for (int i = blockIdx.x * SPS_T + tid; i < nc; i += gridDim.x * SPS_T)
+        spread_static_cell<DIM, T>(g, U, m, i, smax, ok);
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o2));
+    const int bad = __syncthreads_or(!ok);
+    if (lane == 0) s_max[w] = (double)smax;
+    __syncthreads();
+    if (tid == 0) {
+        double mx = s_max[0];
+        for (int v = 1; v < SPS_T / 32; ++v) mx = dmax_nonneg(mx, s_max[v]);
+        m.bandmax[blockIdx.x] = mx;
+        if (bad) record_error(m.err, ERR_NONFINITE);
+        __threadfence();
+        s_last = atomicAdd(f.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // the largest rate: the stage-2 block maxima and every CTA's forced cells
+    double mx = 0.0;
+    for (int b = tid; b < f.nb; b += SPS_T) mx = dmax_nonneg(mx, __ldcg(f.blockmax + b));
+    for (int b = tid; b < (int)gridDim.x; b += SPS_T) mx = dmax_nonneg(mx, __ldcg(m.bandmax + b));
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) mx = dmax_nonneg(mx, __shfl_xor_sync(0xffffffffu, mx, o2));
+    if (lane == 0) s_max[w] = mx;
+    __syncthreads();
+    if (w != 0) return;
+    double a[5];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) a[i] = lane < Cm ? __ldcg(f.part + lane * 5 + i) : 0.0;
+    a[4] = 0.0;
+    finish_combine(a);
+    if (lane == 0) {
+        for (int v = 0; v < SPS_T / 32; ++v) a[4] = dmax_nonneg(a[4], s_max[v]);
+        finish_update(g, m, a, f.dt, f.err, f.dt_fixed);
+        *f.ticket = 0u;
+    }
+}
+
 // Split form: one warp per chunk (CTA c forms chunk c's partial into
 // part[c]); the last CTA to finish (ticket) combines the C partials as the
 // fixed tree of finish_combine, so the sums do not depend on which CTA comes
@@ -1518,11 +1583,15 @@ cudaError_t launch_interp_force(const GridParams &g, int fp_bytes, const void *U
 
 template <int DIM, typename T>
 static cudaError_t spread_apply_t(const GridParams &g, void *U, const MarkerBuffers &m,
-                                  int grid_ctas, cudaStream_t s) {
+                                  int grid_ctas, cudaStream_t s, const FinishArgs *fin) {
     if (m.sp_ready) {
-        spread_static_kernel<DIM, T><<<grid_ctas, SPS_T, 0, s>>>(g, (T *)U, m);
+        if (fin)
+            spread_static_finish_kernel<DIM, T><<<grid_ctas, SPS_T, 0, s>>>(g, (T *)U, m, *fin);
+        else
+            spread_static_kernel<DIM, T><<<grid_ctas, SPS_T, 0, s>>>(g, (T *)U, m);
         return cudaGetLastError();
     }
+    if (fin) return cudaErrorInvalidValue;
     const size_t smem = spread_smem_bytes<T>(g);
     cudaError_t e = func_smem_attr((const void *)spread_apply_kernel<DIM, T>, smem);
     if (e != cudaSuccess) return e;
@@ -1532,13 +1601,18 @@ static cudaError_t spread_apply_t(const GridParams &g, void *U, const MarkerBuff
 }
 
 cudaError_t launch_spread_apply(const GridParams &g, int fp_bytes, void *U,
-                                const MarkerBuffers &m, int grid_ctas, cudaStream_t s) {
+                                const MarkerBuffers &m, int grid_ctas, cudaStream_t s,
+                                const FinishArgs *fin) {
     if (m.ns <= 0) return cudaSuccess;
     if (g.dim == 3)
-        return fp_bytes == 4 ? spread_apply_t<3, float>(g, U, m, grid_ctas, s)
-                             : spread_apply_t<3, double>(g, U, m, grid_ctas, s);
-    return fp_bytes == 4 ? spread_apply_t<2, float>(g, U, m, grid_ctas, s)
-                         : spread_apply_t<2, double>(g, U, m, grid_ctas, s);
+        return fp_bytes == 4 ? spread_apply_t<3, float>(g, U, m, grid_ctas, s, fin)
+                             : spread_apply_t<3, double>(g, U, m, grid_ctas, s, fin);
+    return fp_bytes == 4 ? spread_apply_t<2, float>(g, U, m, grid_ctas, s, fin)
+                         : spread_apply_t<2, double>(g, U, m, grid_ctas, s, fin);
+}
+
+FinishArgs finish_args(const MarkerBuffers &m, const FluidBuffers &fb, int nb, double dt_fixed) {
+    return FinishArgs{fb.blockmax, nb, fb.dt, fb.err, dt_fixed, m.finpart, fb.counter + 1};
 }
 
 template <int DIM, typename T>
