@@ -5,18 +5,20 @@
 //  - Bins: markers sorted by key = (tile id, cell in tile) and input index
 //    with a stable LSD radix sort in one CTA (warp __match_any_sync ranks and
 //    a block-wide scan of the digit histograms), then tile_off[] by binary
-//    search, then the lists of occupied tiles and of "band" tiles (tiles
-//    within one tile of an occupied one).  Integer work only: bit-exact.
-//  - Interpolation (Eq. interp): one CTA per occupied tile stages the tile
-//    plus a one-cell halo of (rho, rho u, rho e) in shared memory; one warp
-//    per marker, one lane per support cell, warp butterfly sum.
+//    search; the forced cells scattered from the markers' supports, and the
+//    lists of occupied tiles and of "band" tiles (tiles holding a forced
+//    cell).  Integer work only: bit-exact.  Small moving bodies do all of
+//    it in one launch (small_rebuild_kernel).
+//  - Interpolation (Eq. interp): one warp per marker, one lane per support
+//    cell read straight from the state, warp butterfly sum.
 //  - Forcing (Eqs. forceMomentum, corr3.8, a = 1/dt): G = dt F =
 //    rho_L U_b - I[rho u], H = dt Q = rho_L c_v T_w - I[rho e].
 //  - Spreading (Eq. force2) as a gather: each cell of a band tile visits its
 //    3^d neighbour cells in a fixed order and the markers binned there in
-//    sorted order, so the sum order is fixed and no float atomics are used.
-//    The forced update (App. B, Eqs. u_centralF2 and e_centralF2) follows in
-//    the same thread.
+//    sorted order, so the sum order is fixed and no float atomics are used;
+//    static markers keep that per-cell list of (marker, weight) entries as
+//    their spreading operator and gather through it.  The forced update
+//    (App. B, Eqs. u_centralF2 and e_centralF2) follows in the same thread.
 #include <float.h>
 
 #include <algorithm>
@@ -404,82 +406,9 @@ __device__ __forceinline__ void store_forcing(const GridParams &g, const MarkerB
     gs[3] = (R)(H * e);
 }
 
-// threads of the staged interpolation (one CTA per occupied tile; 3D tiles
-// hold more markers, served by more warps)
-template <int DIM> constexpr int IF_T = DIM == 3 ? 512 : 256;
-
-
-template <int DIM, typename T>
-__global__ void __launch_bounds__(IF_T<DIM>)
-interp_force_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuffers m,
-                    const int *__restrict__ perm) {
-    using R = T;
-    constexpr int NF = DIM + 2;   // rho, rho u.., rho e
-    constexpr int NS = DIM == 3 ? 27 : 9;
-    extern __shared__ __align__(16) unsigned char smem_if[];
-    R *sS = reinterpret_cast<R *>(smem_if);
-    const int bx = g.tile[0] + 2, by = g.tile[1] + 2, bz = DIM == 3 ? g.tile[2] + 2 : 1;
-    const int bn = bx * by * bz;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const long long N = g.N;
-    const int n_occ = m.counts[0];
-    for (int it = blockIdx.x; it < n_occ; it += gridDim.x) {
-        const int t = m.occ_list[it];
-        const int tx = t % g.ntile[0], ty = (t / g.ntile[0]) % g.ntile[1],
-                  tz = t / (g.ntile[0] * g.ntile[1]);
-        const int ox = tx * g.tile[0] - 1, oy = ty * g.tile[1] - 1,
-                  oz = DIM == 3 ? tz * g.tile[2] - 1 : 0;
-        // stage rho, rho u.., rho e of the tile grown by one cell
-        for (int q = threadIdx.x; q < bn; q += blockDim.x) {
-            const int lx = q % bx, ly = (q / bx) % by, lz = q / (bx * by);
-            const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
-            const bool in = gx >= 0 && gy >= 0 && gz >= 0 && gx < g.n[0] && gy < g.n[1] &&
-                            (DIM == 2 || gz < g.n[2]);
-            R v[NF];
-            const long long j = gx + (long long)g.n[0] * (gy + (long long)g.n[1] * gz);
-            if (in && in_bounds(j, N, m.err)) {
-                interp_fields<DIM, R>(U, N, j, v);
-            } else {
-#pragma unroll
-                for (int f = 0; f < NF; ++f) v[f] = R(0);
-            }
-#pragma unroll
-            for (int f = 0; f < NF; ++f) sS[f * bn + q] = v[f];
-        }
-        __syncthreads();
-        const int p0 = m.tile_off[t], p1 = m.tile_off[t + 1];
-        for (int p = p0 + warp; p < p1; p += nwarps) {
-            const int k = perm[p];
-            if (!in_bounds(k, m.ns, m.err)) continue;
-            R fr[3] = {R(0), R(0), R(0)};
-            int ck[3] = {0, 0, 0};
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                ck[d] = m.cell[(long long)k * 3 + d];
-                fr[d] = marker_frac<R>(m, k, d);
-            }
-            R acc[NF];
-#pragma unroll
-            for (int f = 0; f < NF; ++f) acc[f] = R(0);
-            if (lane < NS) {
-                int cell[3];
-                const R w = lane_weight<DIM, R>(fr, ck, lane, cell);
-                const int li = (cell[0] - ox) + bx * ((cell[1] - oy) + by * (cell[2] - oz));
-#pragma unroll
-                for (int f = 0; f < NF; ++f) acc[f] = w * sS[f * bn + li];
-            }
-#pragma unroll
-            for (int f = 0; f < NF; ++f) acc[f] = warp_sum_r<R>(acc[f]);
-            if (lane == 0) store_forcing<DIM, R>(g, m, k, acc);
-        }
-        __syncthreads();
-    }
-}
-
 // Batched form: one warp per (case, marker) item, the 3^DIM support cells
-// read straight from the case's state.  The support lies inside the grid, so
-// each term equals the staged kernel's and the warp sums run in the same
-// order: the results are bitwise those of interp_force_kernel.
+// read straight from the case's state; the terms and warp sums of
+// interp_direct_kernel, so the results are bitwise the per-case step's.
 template <int DIM, typename T>
 __global__ void __launch_bounds__(512)
 batch_interp_kernel(const BatchCase *__restrict__ cases, const int2 *__restrict__ items,
@@ -523,12 +452,13 @@ batch_interp_kernel(const BatchCase *__restrict__ cases, const int2 *__restrict_
     }
 }
 
-// Interpolation and forcing of one grid with one warp per marker, the
-// support cells read straight from the state (L2): every SM gets markers at
-// once, where the tile-staged form runs one CTA per occupied tile in a single
-// short wave (3D sphere at 256^3: 18.6 -> 10.5 us; the small 2D marker sets
-// keep the staged form, 1 % faster there).  The terms and the warp sums are
-// those of interp_force_kernel, so the results are bitwise the same.
+// Interpolation and forcing of one grid (Eqs. interp, forceMomentum,
+// corr3.8) with one warp per marker, lane l on support cell l, the cells read
+// straight from the state (L2): every SM gets markers at once, where a form
+// staging each occupied tile in shared memory ran one CTA per tile in a
+// single short wave (3D sphere at 256^3: 18.6 -> 10.5 us; moving cylinder
+// 12.5 -> 8.3 us, heated cylinder 18.6 -> 12.4 us per step, results bitwise
+// the same).  The warp sums run in a fixed order.
 template <int DIM, typename T>
 __global__ void __launch_bounds__(256)
 interp_direct_kernel(const GridParams g, const T *__restrict__ U, const MarkerBuffers m) {
@@ -1549,25 +1479,13 @@ cudaError_t launch_bin(const GridParams &g, MarkerBuffers &m, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-template <typename T>
-static size_t interp_smem(const GridParams &g) {
-    size_t bn = (size_t)(g.tile[0] + 2) * (g.tile[1] + 2) * (g.dim == 3 ? g.tile[2] + 2 : 1);
-    return bn * (g.dim + 2) * sizeof(T);
-}
-
 template <int DIM, typename T>
 static cudaError_t interp_force_t(const GridParams &g, const void *U, const MarkerBuffers &m,
                                   int grid_ctas, cudaStream_t s) {
-    if (DIM == 3) {
-        const long long threads = 32ll * m.ns;
-        interp_direct_kernel<DIM, T><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
-            g, (const T *)U, m);
-        return cudaGetLastError();
-    }
-    const size_t smem = interp_smem<T>(g);
-    cudaError_t e = func_smem_attr((const void *)interp_force_kernel<DIM, T>, smem);
-    if (e != cudaSuccess) return e;
-    interp_force_kernel<DIM, T><<<grid_ctas, IF_T<DIM>, smem, s>>>(g, (const T *)U, m, m.perm[m.sorted]);
+    (void)grid_ctas;
+    const long long threads = 32ll * m.ns;
+    interp_direct_kernel<DIM, T><<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
+        g, (const T *)U, m);
     return cudaGetLastError();
 }
 
