@@ -2,12 +2,19 @@
 """Benchmark of the IBM step (3D heated sphere, 256^3 FP32).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--workload sphere|batched]
+                [--workload sphere|batched|cylinders|adjoint]
 
 One step = the whole hot path: fluid stage 1 (L(U^n), dt), fluid stage 2
 (SSP-RK2 predictor), interpolation + direct forcing at the markers,
 spreading + forced update, force/heat sums.  The markers are at rest, so the
-bins and the quadrature weights are built once at set-up.
+bins, the quadrature weights and the spreading operator are built once at
+set-up, and the force/heat sums run inside the spreading launch (the kernel
+split reports them under "spread_apply").
+
+--workload cylinders times the small L2-resident 2D cases (the heated
+cylinder, FP64, static; the transversely oscillating cylinder, FP32, with
+its markers, bins and weights rebuilt every step) with direct launches and
+with step graphs, and the kernel split of the direct launches.
 
 With N > 1 (torchrun, one process per GPU) every rank runs its own
 independent sphere case (Mach x wall-temperature variants): weak scaling,
