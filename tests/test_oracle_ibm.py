@@ -324,3 +324,29 @@ def test_per_stage_forcing_reported_force_is_the_momentum_given(oracle):
     hd = g.h ** 2
     dmom = hd * (Un.reshape(4, -1)[1:3] - U.reshape(4, -1)[1:3]).sum(1) / dt
     np.testing.assert_allclose(f[:2], -dmom, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_band_is_the_union_of_the_marker_supports(oracle, dim):
+    """The forced cells (the oracle's cell-centric band mask: cells with a
+    marker whose owner cell is within one cell per axis) are exactly the
+    union of the markers' 3^d support cells around their owner cells - the
+    marker-centric set the GPU scatters - and every marker reaches 3^d cells
+    (the bound that sizes the spreading operator)."""
+    n = (40, 36, 28)[:dim]
+    g = C.small_grid(dim, n, h=0.1, fp_bytes=8)
+    X = C.random_markers(g, 60, seed=71)
+    cnt, mask = oracle.band_mask(g, X)
+    lo = np.array(g.lo[:dim])
+    owner = np.floor((X - lo) / g.h).astype(int)
+    ref = np.zeros(tuple(reversed(n)), dtype=np.uint8)
+    pairs = 0
+    for c in owner:
+        for off in np.ndindex(*(3,) * dim):
+            cell = c + np.array(off) - 1
+            if np.all(cell >= 0) and np.all(cell < np.array(n)):
+                ref[tuple(reversed(cell))] = 1
+                pairs += 1
+    np.testing.assert_array_equal(mask, ref.reshape(-1))
+    assert cnt == ref.sum()
+    assert pairs == len(X) * 3 ** dim      # markers lie at least two cells inside
